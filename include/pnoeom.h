@@ -1,0 +1,168 @@
+/*
+ * pnoeom.h -- C ABI of the GB300 state-averaged PNO-EOM-CCSD engine.
+ *
+ * What the library computes (Peng, Clement, Valeev, arXiv:1802.06738):
+ *   * the closed-shell EOM-CCSD eigenproblem  Hbar R|0> = E R|0>,
+ *     Hbar = exp(-T) H exp(T), R = R1 + R2 (Sec. 2, the EOM paragraph);
+ *   * with R2 stored per occupied pair ij in the pair's state-averaged PNO
+ *     space and R1 per occupied i in its OSV space (Sec. 2, Eq. eom:sa_density
+ *     and the OSV definition that follows it);
+ *   * PNOs are eigenvectors of the CIS(D) pair densities (Eq. cis_d and the
+ *     pair-density formula after it) averaged over the N target states,
+ *     truncated at T_CutPNO; OSVs are those of the diagonal pairs truncated at
+ *     T_CutOSV (default T_CutPNO / 10, Sec. 3);
+ *   * eigenvalues are found by a Davidson solver whose residuals are
+ *     preconditioned in the semicanonical PNO/OSV bases (Sec. 2, the
+ *     PNO-EOM-CCSD Davidson steps 1-4).
+ *
+ * Conventions
+ *   * Orbitals p = 0..o-1 occupied, o..o+v-1 virtual, canonical RHF (Fock
+ *     diagonal = eps).  Two-electron integrals enter only through
+ *     density-fitting factors B[Q][p][q], (pq|rs) = sum_Q B[Q][p][q] B[Q][r][s]
+ *     (Sec. 3: density fitting is used for all calculations).
+ *   * Amplitudes: t1[i][a] = t^i_a, t2[i][j][a][b] = t^{ij}_{ab} (row-major,
+ *     t2[i][j][a][b] = t2[j][i][b][a]).  T2 = 1/2 t^{ij}_{ab} E^a_i E^b_j.
+ *   * Packed PNO vector (one root): [R1: i = 0..o-1, n_i entries each]
+ *     [R2: pairs i <= j in lexicographic order, n_ij x n_ij row-major, the row
+ *     index in the ij PNO space belonging to orbital i].  Offsets come from
+ *     pno_query().  A batch of nvec vectors is nvec such vectors back to back.
+ *   * PNO/OSV sign convention: every kept semicanonical vector has its entry
+ *     of largest magnitude (the first, on ties) positive.
+ *
+ * Errors: every int-returning call returns PNOEOM_OK (0) or a negative code;
+ * pnoeom_last_error() gives a message for the calling thread.  No call
+ * aborts the process.  Ownership: inputs are caller-owned and copied in;
+ * handles are library-owned until the matching *_destroy.
+ */
+#ifndef PNOEOM_H
+#define PNOEOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PNOEOM_OK = 0,
+  PNOEOM_ERR_INVALID_ARG = -1,
+  PNOEOM_ERR_NOMEM = -2,          /* device allocation failed or footprint over budget */
+  PNOEOM_ERR_CUDA = -3,           /* a CUDA / cuSOLVER call failed */
+  PNOEOM_ERR_NOT_CONVERGED = -4,  /* Davidson hit max_iter; best values returned */
+  PNOEOM_ERR_TIMEOUT = -5,        /* a bounded device wait expired */
+  PNOEOM_ERR_UNSUPPORTED = -6
+};
+
+enum { PNOEOM_HOST = 0, PNOEOM_DEVICE = 1 };            /* memory space of pointers */
+enum { PNOEOM_FP64 = 0, PNOEOM_FP32 = 1 };              /* sigma arithmetic */
+
+typedef struct pnoeom_ctx pnoeom_ctx;
+typedef struct pnoeom_pno pnoeom_pno;
+
+/* One closed-shell system.  eps: float64[o+v]; B: float64[naux][o+v][o+v];
+ * t1: float64[o][v] or NULL (T1 = 0); t2: float64[o][o][v][v] or NULL, in
+ * which case the first-order amplitudes of Eq. T1 are used,
+ * t^{ij}_{ab} = (ai|bj) / (eps_i + eps_j - eps_a - eps_b).
+ * mem_space says whether the pointers are host or device memory. */
+typedef struct {
+  int o, v, naux;
+  const double* eps;
+  const double* B;
+  const double* t1;
+  const double* t2;
+  int mem_space;
+} pnoeom_system;
+
+/* t_pno: T_CutPNO (occupations >= t_pno kept; 0 keeps the full virtual space);
+ * t_osv: T_CutOSV, < 0 means t_pno / 10 (Sec. 3).  nroots_sa: N of the state
+ * average (Eq. eom:sa_density); nroots_solve: roots returned by the solver
+ * (<= nroots_sa).  precision: PNOEOM_FP64 or PNOEOM_FP32 sigma;
+ * refine_fp64: after an FP32 solve, continue with FP64 sigma until the FP64
+ * tolerances hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
+ * change between iterations; max_subspace <= 0 means 8 * nroots_solve. */
+typedef struct {
+  double t_pno, t_osv;
+  int nroots_sa, nroots_solve;
+  int precision;
+  int refine_fp64;
+  int max_iter, max_subspace;
+  double res_tol, e_tol;
+} pnoeom_opts;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no
+ * budget; otherwise pno_build refuses (PNOEOM_ERR_NOMEM) a system whose
+ * estimated footprint exceeds it. */
+int pnoeom_create(pnoeom_ctx** ctx, int device, size_t hbm_budget_bytes);
+void pnoeom_destroy(pnoeom_ctx* ctx);
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char* pnoeom_last_error(void);
+
+/* Setup (Sec. 2): dress the Hamiltonian with T1 (if any), form T2 (Eq. T1 if
+ * not supplied), CIS roots, CIS(D) doubles and state-averaged pair densities,
+ * PNO/OSV eigendecompositions with truncation and semicanonicalisation, and
+ * the R-independent PNO-space operator blocks sigma needs.  Runs on
+ * `cuda_stream` (NULL = default stream) and returns when done.  Inputs are
+ * copied; *out owns all device state. */
+int pno_build(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts,
+              void* cuda_stream, pnoeom_pno** out);
+void pno_destroy(pnoeom_pno* pno);
+
+/* Sizes of the packed PNO vector.  Arrays stay valid until pno_destroy.
+ * n_ij has npairs = o(o+1)/2 entries, n_i has o entries. */
+int pno_query(const pnoeom_pno* pno, int* npairs, const int** n_ij, const int** n_i,
+              size_t* vec_len, size_t* footprint_bytes);
+
+/* PNO bases on the host: U (float64[v][n_ij], row-major) of pair p (i <= j,
+ * lexicographic index), or of OSV set i when pair < 0 (index -pair-1).  The
+ * caller provides v * n doubles.  fbar (n doubles, may be NULL) receives the
+ * semicanonical orbital energies. */
+int pno_get_basis(const pnoeom_pno* pno, int pair, double* U, double* fbar);
+
+/* sigma = Hbar R projected into the PNO/OSV spaces (Sec. 2) for nvec packed
+ * vectors.  r_dev, s_dev: caller-owned device buffers of nvec * vec_len
+ * elements of the chosen precision (double for FP64, float for FP32).
+ * Asynchronous on cuda_stream. */
+int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
+          int precision, void* cuda_stream);
+
+/* Davidson solve (Sec. 2, PNO-EOM-CCSD Davidson): projected CIS guesses,
+ * semicanonical preconditioner omega + f_ii (+ f_jj) - fbar_a (- fbar_b),
+ * FP64 orthogonalisation and subspace diagonalisation.  energies and
+ * res_norms: host arrays of nroots_solve doubles; iters: host int.  Blocking.
+ * Returns PNOEOM_ERR_NOT_CONVERGED with the best values after max_iter. */
+int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, void* cuda_stream,
+                   double* energies, double* res_norms, int* iters);
+
+/* Eigenvectors of the last davidson_solve on this handle, as packed FP64
+ * vectors on the host (nroots_solve * vec_len doubles). */
+int pno_get_eigenvectors(const pnoeom_pno* pno, double* X);
+
+/* All eigenvalues (ascending) of every state-averaged pair density D^{ij}
+ * (Eq. eom:sa_density): npairs x v doubles on the host, pair-major.  The PNO
+ * occupation numbers whose truncation at T_CutPNO defines n_ij. */
+int pno_get_occupations(const pnoeom_pno* pno, double* occ);
+
+/* CIS singles amplitudes b^i_a(k) (Sec. 2, CIS(D) paragraph), nroots_sa x o x v
+ * doubles on the host, normalised so that R1|0> is a unit vector
+ * (2 sum b^2 = 1), largest-magnitude entry positive. */
+int pno_get_cis_vectors(const pnoeom_pno* pno, double* b);
+
+int pno_get_cis(const pnoeom_pno* pno, double* omega);
+
+/* Eigenpairs of a small dense non-symmetric matrix on the host (the Davidson
+ * subspace step, Sec. 2).  A: row-major n x n; wr, wi: real and imaginary
+ * parts of the eigenvalues (unsorted); VR[i*n + k]: component i of the right
+ * eigenvector of eigenvalue k, rotated so its largest component is real,
+ * real part kept, unit 2-norm.  Host memory only, no GPU needed.  Returns 0,
+ * PNOEOM_ERR_INVALID_ARG, or PNOEOM_ERR_NOT_CONVERGED. */
+int pnoeom_small_eig(int n, const double* A, double* wr, double* wi, double* VR);
+
+/* Seconds spent in the last pno_build of this handle (setup time). */
+double pno_build_seconds(const pnoeom_pno* pno);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

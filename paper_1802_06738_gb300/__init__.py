@@ -1,0 +1,229 @@
+"""GB300 engine for state-averaged PNO-EOM-CCSD (arXiv:1802.06738).
+
+A thin ctypes binding over ``libpnoeom.so`` (C ABI in ``include/pnoeom.h``).
+Every step of setup, sigma and the Davidson solve runs inside the library on
+the GPU; this module only marshals arguments.  ``build()`` compiles the CUDA
+sources in-tree for sm_103a.  Importing never falls back to anything: when
+the library is missing the entry points raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import build, LIB_PATH  # noqa: F401
+
+OK = 0
+ERR_INVALID_ARG, ERR_NOMEM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+HOST, DEVICE = 0, 1
+FP64, FP32 = 0, 1
+
+
+class PnoeomError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pnoeom error {code}: {msg}")
+        self.code = code
+
+
+class System(ctypes.Structure):
+    _fields_ = [("o", ctypes.c_int), ("v", ctypes.c_int), ("naux", ctypes.c_int),
+                ("eps", ctypes.c_void_p), ("B", ctypes.c_void_p), ("t1", ctypes.c_void_p),
+                ("t2", ctypes.c_void_p), ("mem_space", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("t_pno", ctypes.c_double), ("t_osv", ctypes.c_double),
+                ("nroots_sa", ctypes.c_int), ("nroots_solve", ctypes.c_int),
+                ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("max_subspace", ctypes.c_int),
+                ("res_tol", ctypes.c_double), ("e_tol", ctypes.c_double)]
+
+
+def make_opts(t_pno=1e-7, t_osv=-1.0, nroots=3, nroots_solve=None, precision=FP64, refine_fp64=0,
+              max_iter=100, max_subspace=0, res_tol=1e-7, e_tol=1e-10):
+    return Opts(t_pno, t_osv, nroots, nroots if nroots_solve is None else nroots_solve,
+                precision, refine_fp64, max_iter, max_subspace, res_tol, e_tol)
+
+
+_lib = None
+EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", "pno_destroy",
+           "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
+           "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds"]
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PnoeomError(ERR_UNSUPPORTED, f"{LIB_PATH} not built; call paper_1802_06738_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
+        L.pnoeom_create.argtypes = [ctypes.POINTER(vp), i, ctypes.c_size_t]
+        L.pnoeom_destroy.argtypes = [vp]; L.pnoeom_destroy.restype = None
+        L.pnoeom_last_error.restype = ctypes.c_char_p
+        L.pno_build.argtypes = [vp, ctypes.POINTER(System), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+        L.pno_destroy.argtypes = [vp]; L.pno_destroy.restype = None
+        L.pno_query.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
+        L.pno_get_basis.argtypes = [vp, i, dp, dp]
+        L.sigma.argtypes = [vp, vp, i, vp, vp, i, vp]
+        L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
+        L.pno_get_eigenvectors.argtypes = [vp, dp]
+        L.pno_get_cis.argtypes = [vp, dp]
+        L.pno_get_occupations.argtypes = [vp, dp]
+        L.pno_get_cis_vectors.argtypes = [vp, dp]
+        L.pnoeom_small_eig.argtypes = [i, dp, dp, dp, dp]
+        L.pno_build_seconds.argtypes = [vp]; L.pno_build_seconds.restype = d
+        _lib = L
+    return _lib
+
+
+def _check(rc, allow=()):
+    if rc != OK and rc not in allow:
+        raise PnoeomError(rc, lib().pnoeom_last_error().decode())
+    return rc
+
+
+def _dptr(a):
+    import numpy as np
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def pnoeom_small_eig(A):
+    """Eigenvalues (complex) and unit right eigenvectors (columns) of a small
+    dense matrix, computed by the library's host routine."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    wr, wi, VR = np.zeros(n), np.zeros(n), np.zeros((n, n))
+    _check(lib().pnoeom_small_eig(n, _dptr(A), _dptr(wr), _dptr(wi), _dptr(VR)))
+    return wr + 1j * wi, VR
+
+
+class Context:
+    """pnoeom_create / pnoeom_destroy."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        h = ctypes.c_void_p()
+        _check(lib().pnoeom_create(ctypes.byref(h), device, hbm_budget_bytes))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().pnoeom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    return None if stream is None else ctypes.c_void_p(stream)
+
+
+class PNO:
+    """A built system: pno_build / pno_query / sigma / davidson_solve."""
+
+    def __init__(self, ctx, eps, B, o, t1=None, t2=None, opts=None, stream=None, device_inputs=False):
+        import numpy as np
+        self.ctx = ctx
+        self.opts = opts if opts is not None else make_opts()
+        nmo = len(eps) if not device_inputs else int(eps.numel())
+        v = nmo - o
+        naux = B.shape[0]
+        if device_inputs:   # torch tensors on the GPU
+            self._keep = (eps, B, t1, t2)
+            ptr = lambda x: None if x is None else x.data_ptr()
+            sysd = System(o, v, naux, ptr(eps), ptr(B), ptr(t1), ptr(t2), DEVICE)
+        else:
+            eps = np.ascontiguousarray(eps, dtype=np.float64)
+            B = np.ascontiguousarray(B, dtype=np.float64)
+            t1 = None if t1 is None else np.ascontiguousarray(t1, dtype=np.float64)
+            t2 = None if t2 is None else np.ascontiguousarray(t2, dtype=np.float64)
+            self._keep = (eps, B, t1, t2)
+            ptr = lambda x: None if x is None else x.ctypes.data
+            sysd = System(o, v, naux, ptr(eps), ptr(B), ptr(t1), ptr(t2), HOST)
+        h = ctypes.c_void_p()
+        _check(lib().pno_build(ctx.h, ctypes.byref(sysd), ctypes.byref(self.opts), _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+        self.o, self.v, self.naux = o, v, naux
+        npairs = ctypes.c_int()
+        nij = ctypes.POINTER(ctypes.c_int)()
+        ni = ctypes.POINTER(ctypes.c_int)()
+        L = ctypes.c_size_t()
+        fp = ctypes.c_size_t()
+        _check(lib().pno_query(h, ctypes.byref(npairs), ctypes.byref(nij), ctypes.byref(ni), ctypes.byref(L), ctypes.byref(fp)))
+        self.npairs = npairs.value
+        self.n_ij = np.array([nij[k] for k in range(self.npairs)], dtype=np.int64)
+        self.n_i = np.array([ni[k] for k in range(o)], dtype=np.int64)
+        self.length = L.value
+        self.footprint = fp.value
+        self.build_seconds = lib().pno_build_seconds(h)
+        self.off_i = np.concatenate([[0], np.cumsum(self.n_i)])
+        self.off_ij = self.off_i[-1] + np.concatenate([[0], np.cumsum(self.n_ij ** 2)])
+        self.pairs = [(i, j) for i in range(o) for j in range(i, o)]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pno_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def basis(self, pair):
+        """(U, fbar) of stored pair index ``pair`` (or OSV i when pair = -i-1)."""
+        import numpy as np
+        n = int(self.n_ij[pair]) if pair >= 0 else int(self.n_i[-pair - 1])
+        U = np.zeros((self.v, n)); fb = np.zeros(n)
+        _check(lib().pno_get_basis(self.h, pair, _dptr(U), _dptr(fb)))
+        return U, fb
+
+    def cis_energies(self):
+        import numpy as np
+        w = np.zeros(self.opts.nroots_sa)
+        _check(lib().pno_get_cis(self.h, _dptr(w)))
+        return w
+
+    def cis_vectors(self):
+        import numpy as np
+        b = np.zeros((self.opts.nroots_sa, self.o, self.v))
+        _check(lib().pno_get_cis_vectors(self.h, _dptr(b)))
+        return b
+
+    def occupations(self):
+        """Eigenvalues of every state-averaged pair density, [npairs, v]."""
+        import numpy as np
+        occ = np.zeros((self.npairs, self.v))
+        _check(lib().pno_get_occupations(self.h, _dptr(occ)))
+        return occ
+
+    def sigma(self, r, out, precision=FP64, stream=None):
+        """sigma for a batch of packed vectors: r, out are CUDA tensors of shape
+        (nvec, length), float64 (FP64) or float32 (FP32)."""
+        nvec = r.shape[0] if r.dim() == 2 else 1
+        _check(lib().sigma(self.ctx.h, self.h, nvec, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                           precision, _stream_ptr(stream)))
+        return out
+
+    def davidson_solve(self, opts=None, stream=None):
+        """(energies, residual norms, iterations, converged) of the Davidson solve."""
+        import numpy as np
+        opts = opts if opts is not None else self.opts
+        n = opts.nroots_solve
+        e, rn, it = np.zeros(n), np.zeros(n), ctypes.c_int()
+        rc = _check(lib().davidson_solve(self.ctx.h, self.h, ctypes.byref(opts), _stream_ptr(stream), _dptr(e), _dptr(rn),
+                                         ctypes.byref(it)), allow=(ERR_NOT_CONVERGED,))
+        return e, rn, it.value, rc == OK
+
+    def eigenvectors(self):
+        import numpy as np
+        X = np.zeros((self.opts.nroots_solve, self.length))
+        _check(lib().pno_get_eigenvectors(self.h, _dptr(X)))
+        return X

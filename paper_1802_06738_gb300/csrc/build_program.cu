@@ -1,0 +1,770 @@
+// Second half of pno_build: R-independent intermediates of the closed-shell
+// EOM-CCSD Jacobian and their projection into PNO/OSV spaces.
+//
+// sigma = Omega'(T2)[R2] + Omega(T2; [H~, R1]) is the Jacobian of the
+// T1-dressed closed-shell CCSD residual (the same residual the oracle pins
+// against brute force).  Every term is rewritten with the R-independent
+// factors projected into the PNO spaces of the pairs it couples, so the
+// sigma program only touches PNO-sized blocks:
+//   * pair-diagonal dense block D_p (n^2 x n^2): the 4-virtual ladder
+//     sum_cd (ac|bd) r^{cd}_{ij}, the T2-ladder sum_kl t^{kl} <(kc|ld), r^{ij}>
+//     and the virtual Fock term;
+//   * triple products over one shared occupied index (ring terms, occupied
+//     Fock term) and over all pairs (occupied ladder), using overlaps
+//     S(ij,kl) = U^ij^T U^kl and mixed-pair blocks U^ij^T W U^kl;
+//   * dense singles couplings (OSV rows / columns);
+//   * two R-dependent global intermediates (virtual and occupied Fock-like
+//     contractions of u(R) with (ld|kc)).
+#include "pno.cuh"
+#include <algorithm>
+#include <cmath>
+
+namespace pnoeom {
+namespace {
+
+using DV = DBuf<double>;
+using Dims = std::map<char, int64_t>;
+
+inline unsigned gsz(size_t n) { return (unsigned)std::max<size_t>(1, std::min<size_t>((n + 255) / 256, 152 * 32)); }
+#define GRID_STRIDE(e, n) for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)(n); e += (int64_t)gridDim.x * blockDim.x)
+
+// Acan[i,a,m,d] += delta_im Xv[a,d] - delta_ad Xo[m,i]
+__global__ void k_acan_delta(double* A, const double* Xv, const double* Xo, int o, int v) {
+  GRID_STRIDE(e, (int64_t)o * v * o * v) {
+    int d = (int)(e % v); int64_t r = e / v;
+    int m = (int)(r % o); r /= o;
+    int a = (int)(r % v); int i = (int)(r / v);
+    double val = 0;
+    if (i == m) val += Xv[a * v + d];
+    if (a == d) val -= Xo[m * o + i];
+    A[e] += val;
+  }
+}
+// D[a,b,c,d] += delta_ac F[b,d] + F[a,c] delta_bd
+__global__ void k_add_fock_kron(double* D, const double* F, int n) {
+  GRID_STRIDE(e, (int64_t)n * n * n * n) {
+    int d = (int)(e % n); int64_t r = e / n;
+    int c = (int)(r % n); r /= n;
+    int b = (int)(r % n); int a = (int)(r / n);
+    double val = 0;
+    if (a == c) val += F[b * n + d];
+    if (b == d) val += F[a * n + c];
+    D[e] += val;
+  }
+}
+// Kronecker-type assembly (row-major out with leading dimension ldo):
+//  mode 0: out[a*n + b][c] += al S[a][c] w[b]   (a,b < n; c < nc)
+//  mode 1: out[a*n + b][c] += al w[a] S[b][c]
+//  mode 2: out[a][c*n + d] += al S[a][c] w[d]   (a < nc; c,d < n)
+//  mode 3: out[a][c*n + d] += al S[a][d] w[c]
+__global__ void k_kron(double* out, int64_t ldo, const double* S, int lds, const double* w, int n, int nc, int mode,
+                       double al) {
+  GRID_STRIDE(e, (int64_t)n * n * nc) {
+    if (mode <= 1) {
+      int c = (int)(e % nc); int64_t q = e / nc;
+      int b = (int)(q % n), a = (int)(q / n);
+      double val = mode == 0 ? S[(int64_t)a * lds + c] * w[b] : w[a] * S[(int64_t)b * lds + c];
+      out[((int64_t)a * n + b) * ldo + c] += al * val;
+    } else {
+      int d = (int)(e % n); int64_t q = e / n;
+      int c = (int)(q % n), a = (int)(q / n);
+      double val = mode == 2 ? S[(int64_t)a * lds + c] * w[d] : S[(int64_t)a * lds + d] * w[c];
+      out[(int64_t)a * ldo + (int64_t)c * n + d] += al * val;
+    }
+  }
+}
+// out[r*ldo + c] += al * X[r*ldx + c]  (r < rows, c < cols); transpose_n > 0 maps row r = a*n+b to b*n+a
+__global__ void k_add_block(double* out, int64_t ldo, const double* X, int64_t ldx, int rows, int cols, double al,
+                            int transpose_n) {
+  GRID_STRIDE(e, (int64_t)rows * cols) {
+    int r = (int)(e / cols), c = (int)(e % cols);
+    int ro = r;
+    if (transpose_n > 0) ro = (r % transpose_n) * transpose_n + r / transpose_n;
+    out[(int64_t)ro * ldo + c] += al * X[(int64_t)r * ldx + c];
+  }
+}
+
+struct Prog {
+  pnoeom_pno* P;
+  cudaStream_t s;
+  int o, v, naux;
+  Dims dm;
+  std::vector<SProb> sp1, sp2;
+  std::vector<VProb> vp1, vp2;
+  int smem = 1;
+
+  const double* U(int x, int y) const { return P->U.get() + P->Uoff_pair[P->pidx[x][y]]; }
+  int n(int x, int y) const { return P->nij[P->pidx[x][y]]; }
+  const double* Uo(int i) const { return P->U.get() + P->Uoff_osv[i]; }
+  int no(int i) const { return P->ni[i]; }
+  void sync() { PN_CUDA(cudaStreamSynchronize(s)); }
+
+  void con(const Dims& d, const char* a, const double* A, const char* b, const double* B, const char* c, double* C,
+           double alpha = 1.0, double beta = 0.0) {
+    contract<double>(d, TView<double>{const_cast<double*>(A), a}, TView<double>{const_cast<double*>(B), b},
+                     TView<double>{C, c}, alpha, beta, s);
+  }
+  void con(const char* a, const double* A, const char* b, const double* B, const char* c, double* C,
+           double alpha = 1.0, double beta = 0.0) {
+    con(dm, a, A, b, B, c, C, alpha, beta);
+  }
+  void perm(const double* in, double* out, std::vector<int64_t> dims, std::vector<int> p, double al = 1.0,
+            double be = 0.0) {
+    permute<double>(in, out, dims, p, al, be, s);
+  }
+  void add_block(double* out, int64_t ldo, const double* X, int64_t ldx, int rows, int cols, double al, int tn = 0) {
+    if (rows <= 0 || cols <= 0) return;
+    k_add_block<<<gsz((size_t)rows * cols), 256, 0, s>>>(out, ldo, X, ldx, rows, cols, al, tn);
+    PN_CUDA(cudaGetLastError());
+  }
+  void kron(double* out, int64_t ldo, const double* S, int lds, const double* w, int nn, int nc, int mode, double al) {
+    if (nn <= 0 || nc <= 0) return;
+    k_kron<<<gsz((size_t)nn * nn * nc), 256, 0, s>>>(out, ldo, S, lds, w, nn, nc, mode, al);
+    PN_CUDA(cudaGetLastError());
+  }
+
+  // out (nL x nR, leading dim ldo) = UL^T op(X) UR for a list of jobs; UL: v x nL, UR: v x nR, X: v x v.
+  struct PJ { const double* UL; int nL; const double* X; int ldx; int tx; const double* UR; int nR; double* out; int ldo; double al; double be; };
+  void project(const std::vector<PJ>& jobs) {
+    const size_t cap = (size_t)64 << 20;   // temp elements per chunk
+    size_t i0 = 0;
+    while (i0 < jobs.size()) {
+      size_t need = 0, i1 = i0;
+      while (i1 < jobs.size() && (i1 == i0 || need + (size_t)v * jobs[i1].nR <= cap)) { need += (size_t)v * jobs[i1].nR; ++i1; }
+      DV tmp(std::max<size_t>(1, need));
+      std::vector<GemmProb<double>> a, b;
+      size_t off = 0;
+      for (size_t q = i0; q < i1; ++q) {
+        const PJ& J = jobs[q];
+        if (!J.nL || !J.nR) continue;
+        double* T = tmp.get() + off;
+        a.push_back({J.X, J.UR, T, v, J.nR, v, J.ldx, J.nR, J.nR, J.tx, 0, 1.0, 0.0});
+        b.push_back({J.UL, T, J.out, J.nL, J.nR, v, J.nL, J.nR, J.ldo, 1, 0, J.al, J.be});
+        off += (size_t)v * J.nR;
+      }
+      grouped_gemm<double>(a, s);
+      grouped_gemm<double>(b, s);
+      i0 = i1;
+    }
+  }
+};
+
+}  // namespace
+
+void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV& dBov, DV& dBvo, DV& dBvv, DV& t2,
+                   DV& u2) {
+  const int o = P->o, v = P->v, naux = P->naux, nmo = o + v;
+  const int64_t O = o, V = v, N = naux;
+  Prog G{P, s, o, v, naux, {}, {}, {}, {}, {}, 1};
+  for (char c : std::string("ijklmxyz")) G.dm[c] = O;
+  for (char c : std::string("abcd")) G.dm[c] = V;
+  G.dm['Q'] = N;
+  const int npairs = P->npairs;
+  const int64_t L1 = P->L1, L = P->L;
+  size_t* fp = &P->footprint;
+
+  // ---- dressed Fock blocks ------------------------------------------------------
+  std::vector<double> Foo(O * O), Fov(O * V), Fvv(V * V);
+  for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) Foo[i * o + j] = Fd[i * nmo + j];
+  for (int i = 0; i < o; ++i) for (int a = 0; a < v; ++a) Fov[i * v + a] = Fd[i * nmo + o + a];
+  for (int a = 0; a < v; ++a) for (int b = 0; b < v; ++b) Fvv[a * v + b] = Fd[(o + a) * nmo + o + b];
+  const bool t1 = P->has_t1;
+
+  // ---- integral blocks (dressed), Mulliken (pq|rs) = sum_Q B_pq B_rs ------------
+  DV g_ovov(O * V * O * V), g_oovv(O * O * V * V), g_voov(V * O * O * V), g_oooo(O * O * O * O), g_ooov(O * O * O * V),
+      g_ovoo(O * V * O * O), g_oovo(O * O * V * O), g_vooo(V * O * O * O);
+  G.con("Qkc", dBov.get(), "Qld", dBov.get(), "kcld", g_ovov.get());
+  G.con("Qki", dBoo.get(), "Qac", dBvv.get(), "kiac", g_oovv.get());
+  G.con("Qai", dBvo.get(), "Qkc", dBov.get(), "aikc", g_voov.get());
+  G.con("Qki", dBoo.get(), "Qlj", dBoo.get(), "kilj", g_oooo.get());
+  G.con("Qki", dBoo.get(), "Qlc", dBov.get(), "kilc", g_ooov.get());
+  G.con("Qkc", dBov.get(), "Qlj", dBoo.get(), "kclj", g_ovoo.get());
+  G.con("Qki", dBoo.get(), "Qbj", dBvo.get(), "kibj", g_oovo.get());
+  G.con("Qai", dBvo.get(), "Qkj", dBoo.get(), "aikj", g_vooo.get());
+  DV L_ovov(g_ovov.n);
+  G.perm(g_ovov.get(), L_ovov.get(), {O, V, O, V}, {0, 3, 2, 1}, -1.0);
+  axpby<double>(L_ovov.get(), g_ovov.get(), 2.0, 1.0, L_ovov.n, s);
+  const double* t = t2.get();
+  const double* u = u2.get();
+
+  // ---- R-independent intermediates ------------------------------------------------
+  DV W(O * O * O * O);       // W[k,i,l,j] = (ki|lj) + sum_cd t^{cd}_{ij} (kc|ld)
+  PN_CUDA(cudaMemcpyAsync(W.get(), g_oooo.get(), W.n * 8, cudaMemcpyDeviceToDevice, s));
+  G.con("ijcd", t, "kcld", g_ovov.get(), "kilj", W.get(), 1.0, 1.0);
+  DV Wc(O * O * V * V);      // Wc[k,i,a,c] = (ki|ac) - 1/2 sum_dl t^{ad}_{li} (kd|lc)
+  PN_CUDA(cudaMemcpyAsync(Wc.get(), g_oovv.get(), Wc.n * 8, cudaMemcpyDeviceToDevice, s));
+  G.con("liad", t, "kdlc", g_ovov.get(), "kiac", Wc.get(), -0.5, 1.0);
+  DV Wd(V * O * O * V);      // Wd[a,i,k,c] = L_aikc + 1/2 sum_dl u^{ad}_{il} L_ldkc
+  G.perm(g_oovv.get(), Wd.get(), {O, O, V, V}, {2, 1, 0, 3}, -1.0);
+  axpby<double>(Wd.get(), g_voov.get(), 2.0, 1.0, Wd.n, s);
+  G.con("ilad", u, "ldkc", L_ovov.get(), "aikc", Wd.get(), 0.5, 1.0);
+  DV FvvI(V * V), FooI(O * O);
+  FvvI.upload(Fvv.data(), Fvv.size(), s);
+  FooI.upload(Foo.data(), Foo.size(), s);
+  G.con("klbd", u, "ldkc", g_ovov.get(), "bc", FvvI.get(), -1.0, 1.0);
+  G.con("ljcd", u, "kdlc", g_ovov.get(), "kj", FooI.get(), 1.0, 1.0);
+  std::vector<double> FooI_h(O * O);
+  FooI.download(FooI_h.data(), FooI_h.size(), s);
+  DV Zt(O * O * V * V), Zd(O * O * V * V);   // Z[l,j,d,b], Zd[l,j,d,b]
+  G.con("kdlc", g_ovov.get(), "kjbc", t, "ljdb", Zt.get());
+  G.con("ldkc", L_ovov.get(), "jkbc", u, "ljdb", Zd.get());
+  // singles-singles block (canonical), see the singles part of the derivative residual
+  DV Acan(O * V * O * V), X1(O * O), Y1s(V * V);
+  G.con("kicd", u, "mdkc", g_ovov.get(), "mi", X1.get());
+  G.con("klac", u, "kdlc", g_ovov.get(), "ad", Y1s.get());
+  G.con("ikac", u, "kcmd", L_ovov.get(), "iamd", Acan.get());
+  G.perm(g_voov.get(), Acan.get(), {V, O, O, V}, {1, 0, 2, 3}, 2.0, 1.0);
+  G.perm(g_oovv.get(), Acan.get(), {O, O, V, V}, {1, 2, 0, 3}, -1.0, 1.0);
+  {
+    DV Xv(V * V), Xo(O * O);
+    Xv.upload(Fvv.data(), Fvv.size(), s);
+    axpby<double>(Xv.get(), Y1s.get(), -1.0, 1.0, Xv.n, s);
+    Xo.upload(Foo.data(), Foo.size(), s);
+    axpby<double>(Xo.get(), X1.get(), 1.0, 1.0, Xo.n, s);
+    k_acan_delta<<<gsz(Acan.n), 256, 0, s>>>(Acan.get(), Xv.get(), Xo.get(), o, v);
+    PN_CUDA(cudaGetLastError());
+    G.sync();
+  }
+  // v^3 o blocks
+  DV g_vvov(V * V * O * V);    // (ad|kc) at [a,d,k,c]
+  G.con("Qad", dBvv.get(), "Qkc", dBov.get(), "adkc", g_vvov.get());
+  DV Y1(O * O * O * V), Y2(O * O * V * O);
+  G.con("ijcd", t, "bdkc", g_vvov.get(), "ijkb", Y1.get());
+  G.con("ijcd", t, "ackd", g_vvov.get(), "ijak", Y2.get());
+  DV Qa(O * V * V * V), Q1(O * V * V * V);   // [j,d,a,b]
+  G.con("ackd", g_vvov.get(), "kjbc", t, "jdab", Q1.get());
+  {
+    DV G34(g_vvov.n);
+    G.perm(g_vvov.get(), G34.get(), {V, V, O, V}, {0, 3, 2, 1}, -0.5);
+    axpby<double>(G34.get(), g_vvov.get(), 1.0, 1.0, G34.n, s);
+    G.con("adkc", G34.get(), "jkbc", u, "jdab", Qa.get());
+  }
+  axpby<double>(Qa.get(), Q1.get(), -0.5, 1.0, Qa.n, s);
+  DV Qb(O * O * O * V);
+  {
+    DV Q2(Qb.n), Q5(Qb.n), Q6(Qb.n);
+    G.con("kimc", g_ooov.get(), "kjbc", t, "mijb", Q2.get());
+    G.con("mikc", g_ooov.get(), "jkbc", u, "mijb", Q5.get());
+    G.con("mcki", g_ovoo.get(), "jkbc", u, "mijb", Q6.get());
+    G.perm(Q2.get(), Qb.get(), {O, O, O, V}, {0, 2, 1, 3});
+    axpby<double>(Qb.get(), Q2.get(), 0.5, 1.0, Qb.n, s);
+    axpby<double>(Qb.get(), Q5.get(), -1.0, 1.0, Qb.n, s);
+    axpby<double>(Qb.get(), Q6.get(), 0.5, 1.0, Qb.n, s);
+    G.sync();
+  }
+  // permuted copies used per pair
+  DV gvvov_k(g_vvov.n);                 // [k][a][d][c]
+  G.perm(g_vvov.get(), gvvov_k.get(), {V, V, O, V}, {2, 0, 1, 3});
+  DV Lv_m(g_vvov.n);                    // Lvvov[b,c,m,d] = 2 (bc|md) - (bd|mc), stored [m][b][c][d]
+  {
+    DV Lvvov(g_vvov.n);
+    G.perm(g_vvov.get(), Lvvov.get(), {V, V, O, V}, {0, 3, 2, 1}, -1.0);
+    axpby<double>(Lvvov.get(), g_vvov.get(), 2.0, 1.0, Lvvov.n, s);
+    G.perm(Lvvov.get(), Lv_m.get(), {V, V, O, V}, {2, 0, 1, 3});
+    G.sync();
+  }
+  g_vvov.release();
+  DV gvvvo_j(V * V * V * O);           // (ac|bj) stored [j][a][c][b]
+  {
+    DV g_vvvo(V * V * V * O);
+    G.con("Qac", dBvv.get(), "Qbj", dBvo.get(), "acbj", g_vvvo.get());
+    G.perm(g_vvvo.get(), gvvvo_j.get(), {V, V, V, O}, {3, 0, 1, 2});
+    G.sync();
+  }
+  DV govoo_j(O * O * V * O);           // (kc|lj) stored [j][k][c][l]
+  G.perm(g_ovoo.get(), govoo_j.get(), {O, V, O, O}, {3, 0, 1, 2});
+  DV gooov_i(O * O * O * V);           // (ki|lc) stored [i][k][l][c]
+  G.perm(g_ooov.get(), gooov_i.get(), {O, O, O, V}, {1, 0, 2, 3});
+  DV wa_can(O * O * O * V), wb_can(O * O * O * V);   // [i][j][k][b], [i][j][k][a]
+  G.perm(g_oovo.get(), wa_can.get(), {O, O, V, O}, {1, 3, 0, 2});
+  axpby<double>(wa_can.get(), Y1.get(), 1.0, 1.0, wa_can.n, s);
+  G.perm(g_vooo.get(), wb_can.get(), {V, O, O, O}, {1, 3, 2, 0});
+  G.perm(Y2.get(), wb_can.get(), {O, O, V, O}, {0, 1, 3, 2}, 1.0, 1.0);
+  DV Qb_xy(O * O * O * V);             // Qb[m,x,y,b] stored [x][y][m][b]
+  G.perm(Qb.get(), Qb_xy.get(), {O, O, O, V}, {1, 2, 0, 3});
+  DV Gam_can(O * O * O * V);           // [y][k][m][d] = 2 (ky|md) - (kd|my)
+  G.perm(g_ooov.get(), Gam_can.get(), {O, O, O, V}, {1, 0, 2, 3}, 2.0);
+  G.perm(g_ovoo.get(), Gam_can.get(), {O, V, O, O}, {3, 0, 2, 1}, -1.0, 1.0);
+  DV Wdp(Wd.n);                        // Wd[a,i,k,c] stored [i][k][a][c]
+  G.perm(Wd.get(), Wdp.get(), {V, O, O, V}, {1, 2, 0, 3});
+  G.sync();
+
+  // ---- pool layout ------------------------------------------------------------------
+  auto nP = [&](int p) { return (int64_t)P->nij[p]; };
+  int64_t pool = 0;
+  auto take = [&](int64_t n) { int64_t off = pool; pool += n; return off; };
+  const int64_t off_U = take(P->U.n);
+  std::vector<int64_t> offS((size_t)npairs * npairs);
+  for (int p = 0; p < npairs; ++p) for (int q = 0; q < npairs; ++q) offS[(size_t)p * npairs + q] = take(nP(p) * nP(q));
+  auto idx3 = [&](int a, int b, int c) { return ((size_t)a * o + b) * o + c; };
+  std::vector<int64_t> offMC(O * O * O), offMD(O * O * O), offMZ(O * O * O), offMZd(O * O * O);
+  for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) for (int k = 0; k < o; ++k) {
+    offMC[idx3(i, j, k)] = take((int64_t)G.n(i, j) * G.n(k, j));
+    offMD[idx3(i, j, k)] = take((int64_t)G.n(i, j) * G.n(j, k));
+    offMZ[idx3(k, i, j)] = take((int64_t)G.n(k, i) * G.n(i, j));
+    offMZd[idx3(k, i, j)] = take((int64_t)G.n(i, k) * G.n(i, j));
+  }
+  std::vector<int64_t> offGh(O * O), offTh(O * O), offG4(O * O), offT4(O * O);
+  for (int x = 0; x < o; ++x) for (int y = 0; y < o; ++y) {
+    int64_t nn = G.n(x, y);
+    offGh[x * o + y] = take(nn * V);
+    offTh[x * o + y] = take(nn * V);
+    offG4[x * o + y] = take(O * nn * nn);
+    offT4[x * o + y] = take(nn * nn * O);
+  }
+  std::vector<int64_t> offD(npairs), offADS(npairs), offAS(o);
+  for (int p = 0; p < npairs; ++p) offD[p] = take(nP(p) * nP(p) * nP(p) * nP(p));
+  for (int p = 0; p < npairs; ++p) offADS[p] = take(nP(p) * nP(p) * L1);
+  for (int i = 0; i < o; ++i) offAS[i] = take((int64_t)G.no(i) * L);
+  P->pool64.alloc(std::max<int64_t>(1, pool), fp);
+  P->pool64.zero(s);
+  double* pl = P->pool64.get();
+  PN_CUDA(cudaMemcpyAsync(pl + off_U, P->U.get(), P->U.n * 8, cudaMemcpyDeviceToDevice, s));
+
+  // ---- overlaps S(p,q) = U_p^T U_q ----------------------------------------------------
+  {
+    std::vector<GemmProb<double>> pr;
+    for (int p = 0; p < npairs; ++p)
+      for (int q = 0; q < npairs; ++q) {
+        if (!nP(p) || !nP(q)) continue;
+        pr.push_back({P->U.get() + P->Uoff_pair[p], P->U.get() + P->Uoff_pair[q], pl + offS[(size_t)p * npairs + q],
+                      (int)nP(p), (int)nP(q), v, (int)nP(p), (int)nP(q), (int)nP(q), 1, 0, 1.0, 0.0});
+      }
+    grouped_gemm<double>(pr, s);
+  }
+  auto Sblk = [&](int p, int q) { return offS[(size_t)p * npairs + q]; };
+
+  // ---- mixed-pair ring blocks -------------------------------------------------------------
+  {
+    std::vector<Prog::PJ> jobs;
+    const int64_t vv = V * V;
+    for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) for (int k = 0; k < o; ++k) {
+      jobs.push_back({G.U(i, j), G.n(i, j), Wc.get() + ((int64_t)k * o + i) * vv, v, 0, G.U(k, j), G.n(k, j),
+                      pl + offMC[idx3(i, j, k)], G.n(k, j), 1.0, 0.0});
+      jobs.push_back({G.U(i, j), G.n(i, j), Wdp.get() + ((int64_t)i * o + k) * vv, v, 0, G.U(j, k), G.n(j, k),
+                      pl + offMD[idx3(i, j, k)], G.n(j, k), 1.0, 0.0});
+      jobs.push_back({G.U(k, i), G.n(k, i), Zt.get() + ((int64_t)k * o + j) * vv, v, 0, G.U(i, j), G.n(i, j),
+                      pl + offMZ[idx3(k, i, j)], G.n(i, j), 1.0, 0.0});
+      jobs.push_back({G.U(i, k), G.n(i, k), Zd.get() + ((int64_t)k * o + j) * vv, v, 0, G.U(i, j), G.n(i, j),
+                      pl + offMZd[idx3(k, i, j)], G.n(i, j), 1.0, 0.0});
+    }
+    G.project(jobs);
+  }
+  // ---- E3 / E4 blocks ---------------------------------------------------------------------------
+  {
+    std::vector<GemmProb<double>> pr;
+    for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+      int nn = G.n(k, l);
+      if (!nn) continue;
+      // Gh[k,l] = U(k,l)^T G^{lk}, G^{lk}[d,c] = (ld|kc)
+      pr.push_back({G.U(k, l), g_ovov.get() + (int64_t)l * V * O * V + (int64_t)k * V, pl + offGh[k * o + l], nn, v, v, nn,
+                    o * v, v, 1, 0, 1.0, 0.0});
+      // Th[k,l] = U(k,l)^T t[k,l]
+      pr.push_back({G.U(k, l), t + ((int64_t)k * o + l) * V * V, pl + offTh[k * o + l], nn, v, v, nn, v, v, 1, 0, 1.0, 0.0});
+    }
+    grouped_gemm<double>(pr, s);
+    std::vector<Prog::PJ> jobs;
+    for (int l = 0; l < o; ++l) for (int j = 0; j < o; ++j) {
+      int nn = G.n(l, j);
+      // G4 rows k: U(l,j)^T X_k U(l,j), X_k[c,d] = (kd|lc)
+      for (int k = 0; k < o; ++k)
+        jobs.push_back({G.U(l, j), nn, g_ovov.get() + (int64_t)k * V * O * V + (int64_t)l * V, o * v, 1, G.U(l, j), nn,
+                        pl + offG4[l * o + j] + (int64_t)k * nn * nn, nn, 1.0, 0.0});
+    }
+    G.project(jobs);
+  }
+  // T4[(i,j)] = [n^2 x o], column k = vec(U(i,j)^T t[i,k] U(i,j)); keep [k][n^2] copies for e2m
+  std::vector<DV> tb3(O * O);
+  {
+    std::vector<Prog::PJ> jobs;
+    for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) {
+      int nn = G.n(i, j);
+      tb3[i * o + j].alloc(std::max<int64_t>(1, O * nn * nn));
+      for (int k = 0; k < o; ++k)
+        jobs.push_back({G.U(i, j), nn, t + ((int64_t)i * o + k) * V * V, v, 0, G.U(i, j), nn,
+                        tb3[i * o + j].get() + (int64_t)k * nn * nn, nn, 1.0, 0.0});
+    }
+    G.project(jobs);
+    for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) {
+      int64_t nn = G.n(i, j);
+      if (nn) G.perm(tb3[i * o + j].get(), pl + offT4[i * o + j], {O, nn * nn}, {1, 0});
+    }
+  }
+
+  // R1 column blocks shared by all pairs: Lv1[b,c,(m,D)] = sum_d (2 (bc|md) - (bd|mc)) U^m[d,D],
+  // GamAll[y][k][(m,D)] = sum_d (2 (ky|md) - (kd|my)) U^m[d,D]
+  DV Lv1(std::max<int64_t>(1, V * V * L1)), GamAll(std::max<int64_t>(1, O * O * L1));
+  {
+    std::vector<GemmProb<double>> pr;
+    for (int m = 0; m < o; ++m) {
+      if (!G.no(m)) continue;
+      pr.push_back({Lv_m.get() + (int64_t)m * V * V * V, G.Uo(m), Lv1.get() + P->off_i[m], v * v, G.no(m), v, v, G.no(m),
+                    (int)L1, 0, 0, 1.0, 0.0});
+      for (int y = 0; y < o; ++y)
+        pr.push_back({Gam_can.get() + (int64_t)y * O * O * V + (int64_t)m * V, G.Uo(m), GamAll.get() + (int64_t)y * O * L1 + P->off_i[m],
+                      o, G.no(m), v, o * v, G.no(m), (int)L1, 0, 0, 1.0, 0.0});
+    }
+    grouped_gemm<double>(pr, s);
+  }
+
+  // ---- pair-diagonal dense blocks D_p --------------------------------------------------------
+  for (int p = 0; p < npairs; ++p) {
+    const int i = P->pair_i[p], j = P->pair_j[p];
+    const int nn = (int)nP(p);
+    if (!nn) continue;
+    const double* Up = G.U(i, j);
+    Dims d = G.dm;
+    for (char c : std::string("ABCD")) d[c] = nn;
+    DV Bb(N * nn * nn);
+    {
+      std::vector<Prog::PJ> jobs;
+      for (int q = 0; q < naux; ++q)
+        jobs.push_back({Up, nn, dBvv.get() + (int64_t)q * V * V, v, 0, Up, nn, Bb.get() + (int64_t)q * nn * nn, nn, 1.0, 0.0});
+      G.project(jobs);
+    }
+    double* Dp = pl + offD[p];
+    G.con(d, "QAC", Bb.get(), "QBD", Bb.get(), "ABCD", Dp);         // ladder
+    DV tb(O * O * nn * nn), gb(O * O * nn * nn);
+    {
+      std::vector<Prog::PJ> jobs;
+      for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+        jobs.push_back({Up, nn, t + ((int64_t)k * o + l) * V * V, v, 0, Up, nn, tb.get() + ((int64_t)k * o + l) * nn * nn, nn, 1.0, 0.0});
+        jobs.push_back({Up, nn, g_ovov.get() + (int64_t)k * V * O * V + (int64_t)l * V, o * v, 0, Up, nn,
+                        gb.get() + ((int64_t)k * o + l) * nn * nn, nn, 1.0, 0.0});
+      }
+      G.project(jobs);
+    }
+    G.con(d, "klAB", tb.get(), "klCD", gb.get(), "ABCD", Dp, 1.0, 1.0);   // T2 ladder
+    DV Fb(nn * nn);
+    G.project({{Up, nn, FvvI.get(), v, 0, Up, nn, Fb.get(), nn, 1.0, 0.0}});
+    k_add_fock_kron<<<gsz((size_t)nn * nn * nn * nn), 256, 0, s>>>(Dp, Fb.get(), nn);
+    PN_CUDA(cudaGetLastError());
+
+    // ---- singles -> doubles dense block A_DS_p (n^2 x L1) --------------------------------------
+    double* Y = pl + offADS[p];
+    const int ni = G.no(i), nj = G.no(j);
+    // (c1)+(c3): columns of OSV i and OSV j
+    for (int side = 0; side < 2; ++side) {
+      const int x = side == 0 ? i : j;      // OSV whose r1 enters
+      const int nx = side == 0 ? ni : nj;
+      if (!nx) continue;
+      d['C'] = nx;
+      DV T1(nn * V * V), T2(nn * nx * V), K3(nn * nn * nx), H(O * O * nx);
+      if (side == 0) {  // sum_c U^i[c,C] (ac|bj): X3 = (ac|bj) at [a][c][b] for this j
+        const double* X3 = gvvvo_j.get() + (int64_t)j * V * V * V;
+        G.con(d, "aA", Up, "acb", X3, "Acb", T1.get());
+        G.con(d, "Acb", T1.get(), "cC", G.Uo(i), "ACb", T2.get());
+        G.con(d, "ACb", T2.get(), "bB", Up, "ABC", K3.get());
+        G.con(d, "kcl", govoo_j.get() + (int64_t)j * O * V * O, "cC", G.Uo(i), "klC", H.get());
+      } else {          // sum_c U^j[c,C] (ai|bc): (ai|bc) = X3'[b][c][a] for this i
+        const double* X3 = gvvvo_j.get() + (int64_t)i * V * V * V;
+        G.con(d, "bca", X3, "aA", Up, "bcA", T1.get());
+        G.con(d, "bcA", T1.get(), "cC", G.Uo(j), "bAC", T2.get());
+        G.con(d, "bAC", T2.get(), "bB", Up, "ABC", K3.get());
+        G.con(d, "klc", gooov_i.get() + (int64_t)i * O * O * V, "cC", G.Uo(j), "klC", H.get());
+      }
+      G.con(d, "klAB", tb.get(), "klC", H.get(), "ABC", K3.get(), 1.0, 1.0);
+      G.add_block(Y + P->off_i[x], L1, K3.get(), nx, nn * nn, nx, 1.0);
+    }
+    // (c1)+(c2): outer products with S(ij,k) r1_k
+    {
+      DV Sk(nn * std::max<int64_t>(1, L1)), wa(O * nn), wb(O * nn);
+      std::vector<GemmProb<double>> pr;
+      for (int k = 0; k < o; ++k)
+        if (G.no(k))
+          pr.push_back({Up, G.Uo(k), Sk.get() + P->off_i[k], nn, G.no(k), v, nn, G.no(k), (int)L1, 1, 0, 1.0, 0.0});
+      pr.push_back({wa_can.get() + ((int64_t)i * o + j) * O * V, Up, wa.get(), o, nn, v, v, nn, nn, 0, 0, -1.0, 0.0});
+      pr.push_back({wb_can.get() + ((int64_t)i * o + j) * O * V, Up, wb.get(), o, nn, v, v, nn, nn, 0, 0, -1.0, 0.0});
+      grouped_gemm<double>(pr, s);
+      for (int k = 0; k < o; ++k) {
+        if (!G.no(k)) continue;
+        G.kron(Y + P->off_i[k], L1, Sk.get() + P->off_i[k], (int)L1, wa.get() + (int64_t)k * nn, nn, G.no(k), 0, 1.0);
+        G.kron(Y + P->off_i[k], L1, Sk.get() + P->off_i[k], (int)L1, wb.get() + (int64_t)k * nn, nn, G.no(k), 1, 1.0);
+      }
+    }
+    // ordered (x,y) contributions (the P-symmetrised part): (i,j) and, if i < j, (j,i) transposed
+    for (int ord = 0; ord < (i == j ? 1 : 2); ++ord) {
+      const int x = ord == 0 ? i : j, y = ord == 0 ? j : i;
+      DV Yc(nn * nn * std::max<int64_t>(1, L1));
+      Yc.zero(s);
+      d['L'] = L1;
+      // Qa (OSV x), -Q1 (OSV y)
+      for (int side = 0; side < 2; ++side) {
+        const int z = side == 0 ? x : y;
+        const int nz = G.no(z);
+        if (!nz) continue;
+        d['D'] = nz;
+        const double* Qsrc = side == 0 ? Qa.get() + (int64_t)y * V * V * V : Q1.get() + (int64_t)x * V * V * V;
+        DV T1(nz * V * V), T2(nz * nn * V), K3(nn * nn * nz);
+        G.con(d, "dab", Qsrc, "dD", G.Uo(z), "Dab", T1.get());
+        G.con(d, "Dab", T1.get(), "aA", Up, "DAb", T2.get());
+        G.con(d, "DAb", T2.get(), "bB", Up, "ABD", K3.get());
+        G.add_block(Yc.get() + P->off_i[z], L1, K3.get(), nz, nn * nn, nz, side == 0 ? 1.0 : -1.0);
+      }
+      d['D'] = nn;
+      if (L1 > 0) {
+        // Lambda: sum_c t[x,y,a,c] (2 (bc|md) - (bd|mc)) U^m[d,D]
+        DV T2(nn * V * L1);
+        G.con(d, "Ac", pl + offTh[x * o + y], "bcL", Lv1.get(), "AbL", T2.get());
+        G.con(d, "AbL", T2.get(), "bB", Up, "ABL", Yc.get(), 1.0, 1.0);
+        // e2m: - sum_k tb3[x,k,y] Gam_y[k, L]
+        G.con(d, "kAB", tb3[x * o + y].get(), "kL", GamAll.get() + (int64_t)y * O * L1, "ABL", Yc.get(), -1.0, 1.0);
+        // qb kron: S(xy,m)[A,C] qb[x,y,m][B]
+        DV Sk(nn * L1), qb(O * nn), e2a(O * nn);
+        std::vector<GemmProb<double>> pr;
+        for (int m = 0; m < o; ++m)
+          if (G.no(m))
+            pr.push_back({Up, G.Uo(m), Sk.get() + P->off_i[m], nn, G.no(m), v, nn, G.no(m), (int)L1, 1, 0, 1.0, 0.0});
+        pr.push_back({Qb_xy.get() + ((int64_t)x * o + y) * O * V, Up, qb.get(), o, nn, v, v, nn, nn, 0, 0, 1.0, 0.0});
+        grouped_gemm<double>(pr, s);
+        for (int m = 0; m < o; ++m)
+          if (G.no(m))
+            G.kron(Yc.get() + P->off_i[m], L1, Sk.get() + P->off_i[m], (int)L1, qb.get() + (int64_t)m * nn, nn, G.no(m), 0, 1.0);
+        if (t1) {
+          // e2a: - (t[x,y] Fov[m]) projected, b-side S(xy,m)
+          DV dFov(O * V), ecan(O * V);
+          dFov.upload(Fov.data(), Fov.size(), s);
+          grouped_gemm<double>({{dFov.get(), t + ((int64_t)x * o + y) * V * V, ecan.get(), o, v, v, v, v, v, 0, 1, 1.0, 0.0}}, s);
+          grouped_gemm<double>({{ecan.get(), Up, e2a.get(), o, nn, v, v, nn, nn, 0, 0, -1.0, 0.0}}, s);
+          for (int m = 0; m < o; ++m)
+            if (G.no(m))
+              G.kron(Yc.get() + P->off_i[m], L1, Sk.get() + P->off_i[m], (int)L1, e2a.get() + (int64_t)m * nn, nn, G.no(m), 1, 1.0);
+          // e2j: - sum_m tb3[x,m,y] (Fov[m] . U^y)  (columns of OSV y)
+          if (G.no(y)) {
+            DV phi(O * G.no(y));
+            grouped_gemm<double>({{dFov.get(), G.Uo(y), phi.get(), o, G.no(y), v, v, G.no(y), G.no(y), 0, 0, 1.0, 0.0}}, s);
+            Dims d3 = d; d3['C'] = G.no(y);
+            DV K3(nn * nn * G.no(y));
+            G.con(d3, "kAB", tb3[x * o + y].get(), "kC", phi.get(), "ABC", K3.get());
+            G.add_block(Yc.get() + P->off_i[y], L1, K3.get(), G.no(y), nn * nn, G.no(y), -1.0);
+          }
+        }
+      }
+      // accumulate into A_DS_p: (i,j) as is, (j,i) with rows transposed; for i == j both
+      if (ord == 0) G.add_block(Y, L1, Yc.get(), L1, nn * nn, (int)L1, 1.0, 0);
+      if (ord == 1 || i == j) G.add_block(Y, L1, Yc.get(), L1, nn * nn, (int)L1, 1.0, nn);
+      G.sync();
+    }
+    G.sync();
+  }
+
+  // ---- singles rows A_S_i (n_i x L) --------------------------------------------------------------
+  for (int i = 0; i < o; ++i) {
+    const int ni = G.no(i);
+    if (!ni) continue;
+    double* Ai = pl + offAS[i];
+    {   // singles-singles
+      std::vector<Prog::PJ> jobs;
+      for (int m = 0; m < o; ++m)
+        if (G.no(m))
+          jobs.push_back({G.Uo(i), ni, Acan.get() + (int64_t)i * V * O * V + (int64_t)m * V, o * v, 0, G.Uo(m), G.no(m),
+                          Ai + P->off_i[m], (int)L, 1.0, 0.0});
+      G.project(jobs);
+    }
+    Dims d = G.dm;
+    d['A'] = ni;
+    for (int k = 0; k < o; ++k) {   // V_bar term: ordered (k, i), stored q = {k, i}
+      const int q = P->pidx[k][i];
+      const int nq = (int)nP(q);
+      if (!nq) continue;
+      d['C'] = nq; d['D'] = nq;
+      DV T1(ni * V * V), T2(ni * nq * V), Vb(ni * nq * nq), Vt(Vb.n);
+      G.con(d, "adc", gvvov_k.get() + (int64_t)k * V * V * V, "aA", G.Uo(i), "Adc", T1.get());
+      G.con(d, "Adc", T1.get(), "cC", G.U(k, i), "ACd", T2.get());
+      G.con(d, "ACd", T2.get(), "dD", G.U(k, i), "ACD", Vb.get());
+      G.perm(Vb.get(), Vt.get(), {ni, nq, nq}, {0, 2, 1});
+      const bool direct = k <= i;
+      G.add_block(Ai + P->off_ij[q], L, direct ? Vb.get() : Vt.get(), nq * nq, ni, nq * nq, 2.0);
+      G.add_block(Ai + P->off_ij[q], L, direct ? Vt.get() : Vb.get(), nq * nq, ni, nq * nq, -1.0);
+    }
+    {   // h_bar term (and F_ov term with T1): -S(i,kl) UR^{kl} h
+      DV S(ni * std::max<int64_t>(1, L - L1)), hb((int64_t)O * O * v);
+      std::vector<GemmProb<double>> pr;
+      for (int q = 0; q < npairs; ++q)
+        if (nP(q))
+          pr.push_back({G.Uo(i), P->U.get() + P->Uoff_pair[q], S.get() + (P->off_ij[q] - L1), ni, (int)nP(q), v, ni,
+                        (int)nP(q), (int)(L - L1), 1, 0, 1.0, 0.0});
+      for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+        int nn = G.n(k, l);
+        if (!nn) continue;
+        pr.push_back({G.U(k, l), gooov_i.get() + (int64_t)i * O * O * V + ((int64_t)k * o + l) * V, hb.get() + ((int64_t)k * o + l) * V,
+                      nn, 1, v, nn, 1, 1, 1, 0, 1.0, 0.0});
+      }
+      grouped_gemm<double>(pr, s);
+      for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+        const int q = P->pidx[k][l];
+        const int nn = (int)nP(q);
+        if (!nn) continue;
+        const double* Sq = S.get() + (P->off_ij[q] - L1);
+        const double* w = hb.get() + ((int64_t)k * o + l) * V;
+        double* out = Ai + P->off_ij[q];
+        const int lds = (int)(L - L1);
+        if (k <= l) { G.kron(out, L, Sq, lds, w, nn, ni, 2, -2.0); G.kron(out, L, Sq, lds, w, nn, ni, 3, 1.0); }
+        else { G.kron(out, L, Sq, lds, w, nn, ni, 3, -2.0); G.kron(out, L, Sq, lds, w, nn, ni, 2, 1.0); }
+      }
+      if (t1) {   // + S(i,ik) UR^{ik} fb, fb = U(i,k)^T Fov[k]
+        DV dFov(O * V), fb(O * V);
+        dFov.upload(Fov.data(), Fov.size(), s);
+        std::vector<GemmProb<double>> pf;
+        for (int k = 0; k < o; ++k)
+          if (G.n(i, k)) pf.push_back({G.U(i, k), dFov.get() + (int64_t)k * V, fb.get() + (int64_t)k * V, G.n(i, k), 1, v, G.n(i, k), 1, 1, 1, 0, 1.0, 0.0});
+        grouped_gemm<double>(pf, s);
+        for (int k = 0; k < o; ++k) {
+          const int q = P->pidx[i][k];
+          const int nn = (int)nP(q);
+          if (!nn) continue;
+          const double* Sq = S.get() + (P->off_ij[q] - L1);
+          const double* w = fb.get() + (int64_t)k * V;
+          double* out = Ai + P->off_ij[q];
+          const int lds = (int)(L - L1);
+          if (i <= k) { G.kron(out, L, Sq, lds, w, nn, ni, 2, 2.0); G.kron(out, L, Sq, lds, w, nn, ni, 3, -1.0); }
+          else { G.kron(out, L, Sq, lds, w, nn, ni, 3, 2.0); G.kron(out, L, Sq, lds, w, nn, ni, 2, -1.0); }
+        }
+      }
+      G.sync();
+    }
+  }
+  G.sync();
+
+  // ---- problem lists ------------------------------------------------------------------------------
+  P->work_fvr = 0;
+  P->work_for = V * V;
+  P->work_len = V * V + O * O;
+  auto blk = [&](int x, int y) { return P->pidx[x][y]; };
+  // sandwich helper: C(stored out pair, transposed?) += al * A * X(stored q, tx) * B
+  auto add_sw = [&](std::vector<SProb>& L_, int cbuf, int64_t coff, int ldc, int tc, int M, int Nn, int abuf, int64_t aoff,
+                    int lda, int ta, int K1, int xbuf, int64_t xoff, int ldx, int tx, int K2, int bbuf, int64_t boff,
+                    int ldb, int tb, double al) {
+    if (M <= 0 || Nn <= 0 || K1 <= 0 || K2 <= 0 || al == 0.0) return;
+    for (int m0 = 0; m0 < M; m0 += 64)
+      for (int n0 = 0; n0 < Nn; n0 += 64) {
+        SProb q{};
+        q.a_off = aoff; q.x_off = xoff; q.b_off = boff; q.c_off = coff;
+        q.a_buf = abuf; q.x_buf = xbuf; q.b_buf = bbuf; q.c_buf = cbuf;
+        q.M = M; q.K1 = K1; q.K2 = K2; q.N = Nn;
+        q.lda = lda; q.ldx = ldx; q.ldb = ldb; q.ldc = ldc;
+        q.ta = ta; q.tx = tx; q.tb = tb; q.tc = tc;
+        q.m0 = m0; q.n0 = n0; q.alpha = al;
+        L_.push_back(q);
+        int tr = abuf == B_NONE ? std::min(64, M - m0) : K1;
+        G.smem = std::max(G.smem, tr * std::min(64, Nn - n0));
+      }
+  };
+  auto add_gemv = [&](std::vector<VProb>& L_, int64_t aoff, int M, int K, int lda, int xbuf, int64_t xoff, int xs, int xvn,
+                      int cbuf, int64_t coff, int cs, int cvn, double al) {
+    if (M <= 0 || K <= 0 || al == 0.0) return;
+    for (int m0 = 0; m0 < M; m0 += 64) {
+      VProb q{};
+      q.a_off = aoff; q.x_off = xoff; q.c_off = coff;
+      q.x_buf = xbuf; q.c_buf = cbuf;
+      q.M = M; q.K = K; q.lda = lda;
+      q.x_stride = xs; q.c_stride = cs; q.xvec_n = xvn; q.cvec_n = cvn;
+      q.m0 = m0; q.alpha = al;
+      L_.push_back(q);
+    }
+  };
+  auto Ro = [&](int x, int y) { return P->off_ij[blk(x, y)]; };          // stored block offset
+  auto Rt = [&](int x, int y) { return x > y ? 1 : 0; };                  // R^{xy} = stored^T ?
+  // Phase 1: E3 virtual intermediate FvR (v x v) and E4 occupied intermediate FoR (o x o)
+  for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+    const int nn = G.n(k, l);
+    if (!nn) continue;
+    const int64_t uo = off_U + P->Uoff_pair[blk(k, l)];
+    // FvR += -U^{kl} (2 R^{kl} - R^{kl T}) Gh[k,l]
+    add_sw(G.sp1, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, uo, nn, 0, nn, B_RIN, Ro(k, l), nn, Rt(k, l), nn, B_POOL,
+           offGh[k * o + l], v, 0, -2.0);
+    add_sw(G.sp1, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, uo, nn, 0, nn, B_RIN, Ro(k, l), nn, 1 - Rt(k, l), nn, B_POOL,
+           offGh[k * o + l], v, 0, 1.0);
+    // FoR[:, j] += G4[(l,j)] vec(2 R^{lj} - R^{lj T})   (here (l, j) = (k, l))
+    const int lj_l = k, lj_j = l;
+    add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? nn : 0, B_WORK,
+             P->work_for + lj_j, o, 0, 2.0);
+    add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? 0 : nn, B_WORK,
+             P->work_for + lj_j, o, 0, -1.0);
+  }
+  // Phase 2
+  for (int p = 0; p < npairs; ++p) {
+    const int nn = (int)nP(p);
+    if (!nn) continue;
+    add_gemv(G.vp2, offD[p], nn * nn, nn * nn, nn * nn, B_RIN, P->off_ij[p], 1, 0, B_SOUT, P->off_ij[p], 1, 0, 1.0);
+    add_gemv(G.vp2, offADS[p], nn * nn, (int)L1, (int)L1, B_RIN, 0, 1, 0, B_SOUT, P->off_ij[p], 1, 0, 1.0);
+  }
+  for (int i = 0; i < o; ++i)
+    add_gemv(G.vp2, offAS[i], G.no(i), (int)L, (int)L, B_RIN, 0, 1, 0, B_SOUT, P->off_i[i], 1, 0, 1.0);
+  // ordered (i,j) contributions go to stored {i,j}; transposed when i > j; twice when i == j
+  auto targets = [&](int i, int j, std::vector<int>& tcs) {
+    tcs.clear();
+    if (i < j) tcs.push_back(0); else if (i > j) tcs.push_back(1); else { tcs.push_back(0); tcs.push_back(1); }
+  };
+  std::vector<int> tcs;
+  for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) {
+    const int nij = G.n(i, j);
+    if (!nij) continue;
+    const int pij = blk(i, j);
+    targets(i, j, tcs);
+    for (int tc : tcs) {
+      const int64_t co = P->off_ij[pij];
+      // E4 phase 2: -sum_k FoR[k,j] vec(tb3[i,k,j])
+      add_gemv(G.vp2, offT4[i * o + j], nij * nij, o, o, B_WORK, P->work_for + j, o, 0, B_SOUT, co, 1, tc ? nij : 0, -1.0);
+      // E3 phase 2: Th[i,j] FvR^T U(i,j)
+      add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offTh[i * o + j], v, 0, v, B_WORK, P->work_fvr, v, 1, v, B_POOL,
+             off_U + P->Uoff_pair[pij], nij, 0, 1.0);
+      for (int k = 0; k < o; ++k) {
+        const int nkj = G.n(k, j), nki = G.n(k, i), njk = G.n(j, k), nik = G.n(i, k);
+        const int pkj = blk(k, j), pki = blk(k, i), pjk = blk(j, k), pik = blk(i, k);
+        // C1: -1/2 MC[i,j,k] R^{kj T} S(kj,ij)
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMC[idx3(i, j, k)], nkj, 0, nkj, B_RIN, Ro(k, j), nkj,
+               1 - Rt(k, j), nkj, B_POOL, Sblk(pkj, pij), nij, 0, -0.5);
+        // C2: -MC[j,i,k] R^{ki T} S(ki,ij)
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMC[idx3(j, i, k)], nki, 0, nki, B_RIN, Ro(k, i), nki,
+               1 - Rt(k, i), nki, B_POOL, Sblk(pki, pij), nij, 0, -1.0);
+        // C3: +1/4 S(ij,ki) R^{ki} MZ[k,i,j]
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pki), nki, 0, nki, B_RIN, Ro(k, i), nki, Rt(k, i),
+               nki, B_POOL, offMZ[idx3(k, i, j)], nij, 0, 0.25);
+        // C4: +1/2 S(ij,kj) R^{kj} MZ[k,j,i]
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pkj), nkj, 0, nkj, B_RIN, Ro(k, j), nkj, Rt(k, j),
+               nkj, B_POOL, offMZ[idx3(k, j, i)], nij, 0, 0.5);
+        // D1: MD[i,j,k] (R^{jk T} - 1/2 R^{jk}) S(jk,ij)
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMD[idx3(i, j, k)], njk, 0, njk, B_RIN, Ro(j, k), njk,
+               1 - Rt(j, k), njk, B_POOL, Sblk(pjk, pij), nij, 0, 1.0);
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMD[idx3(i, j, k)], njk, 0, njk, B_RIN, Ro(j, k), njk,
+               Rt(j, k), njk, B_POOL, Sblk(pjk, pij), nij, 0, -0.5);
+        // D2: S(ij,ik) (1/2 R^{ik} - 1/4 R^{ik T}) MZd[k,i,j]
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik, Rt(i, k),
+               nik, B_POOL, offMZd[idx3(k, i, j)], nij, 0, 0.5);
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik,
+               1 - Rt(i, k), nik, B_POOL, offMZd[idx3(k, i, j)], nij, 0, -0.25);
+        // E2: -Foo~[k,j] S(ij,ik) R^{ik} S(ik,ij)
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik, Rt(i, k),
+               nik, B_POOL, Sblk(pik, pij), nij, 0, -FooI_h[k * o + j]);
+      }
+    }
+  }
+  // occupied ladder (not symmetrised): stored (i,j) += sum_kl W[k,i,l,j] S(ij,kl) R^{kl} S(kl,ij)
+  std::vector<double> W_h(W.n);
+  W.download(W_h.data(), W_h.size(), s);
+  G.sync();
+  for (int p = 0; p < npairs; ++p) {
+    const int i = P->pair_i[p], j = P->pair_j[p], nij = (int)nP(p);
+    if (!nij) continue;
+    for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+      const int q = blk(k, l), nq = (int)nP(q);
+      if (!nq) continue;
+      add_sw(G.sp2, B_SOUT, P->off_ij[p], nij, 0, nij, nij, B_POOL, Sblk(p, q), nq, 0, nq, B_RIN, P->off_ij[q], nq, Rt(k, l),
+             nq, B_POOL, Sblk(q, p), nij, 0, W_h[(((size_t)k * o + i) * o + l) * o + j]);
+    }
+  }
+  P->n_sp1 = (int)G.sp1.size(); P->n_sp2 = (int)G.sp2.size();
+  P->n_vp1 = (int)G.vp1.size(); P->n_vp2 = (int)G.vp2.size();
+  P->sp_phase1.alloc(std::max<size_t>(1, G.sp1.size()), fp); P->sp_phase1.upload(G.sp1.data(), G.sp1.size(), s);
+  P->sp_phase2.alloc(std::max<size_t>(1, G.sp2.size()), fp); P->sp_phase2.upload(G.sp2.data(), G.sp2.size(), s);
+  P->vp_phase1.alloc(std::max<size_t>(1, G.vp1.size()), fp); P->vp_phase1.upload(G.vp1.data(), G.vp1.size(), s);
+  P->vp_phase2.alloc(std::max<size_t>(1, G.vp2.size()), fp); P->vp_phase2.upload(G.vp2.data(), G.vp2.size(), s);
+  P->smem_elems = G.smem;
+  // FP32 copy of the pool for the mixed-precision sigma
+  P->pool32.alloc(P->pool64.n, fp);
+  d2f(P->pool32.get(), P->pool64.get(), P->pool64.n, s);
+  G.sync();
+}
+
+}  // namespace pnoeom

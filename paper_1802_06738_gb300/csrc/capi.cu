@@ -1,0 +1,180 @@
+// C entry points: argument checks, error translation, handle lifetime.
+#include "pno.cuh"
+#include <cmath>
+#include <functional>
+
+namespace pnoeom { int small_eig(int n, const double* A, double* wr, double* wi, double* VR); }
+
+namespace {
+thread_local std::string g_last_error;
+
+int guard(const std::function<void()>& f) {
+  try {
+    f();
+    g_last_error.clear();
+    return PNOEOM_OK;
+  } catch (const pnoeom::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return PNOEOM_ERR_NOMEM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return PNOEOM_ERR_CUDA;
+  }
+}
+inline cudaStream_t st(void* p) { return reinterpret_cast<cudaStream_t>(p); }
+}  // namespace
+
+extern "C" {
+
+const char* pnoeom_last_error(void) { return g_last_error.c_str(); }
+
+int pnoeom_create(pnoeom_ctx** ctx, int device, size_t hbm_budget_bytes) {
+  return guard([&] {
+    PN_CHECK(ctx, PNOEOM_ERR_INVALID_ARG, "ctx is NULL");
+    int ndev = 0;
+    PN_CUDA(cudaGetDeviceCount(&ndev));
+    PN_CHECK(device >= 0 && device < ndev, PNOEOM_ERR_INVALID_ARG, "no such CUDA device");
+    PN_CUDA(cudaSetDevice(device));
+    auto* c = new pnoeom_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    if (cusolverDnCreate(&c->solver) != CUSOLVER_STATUS_SUCCESS) {
+      delete c;
+      throw pnoeom::Error(PNOEOM_ERR_CUDA, "cusolverDnCreate failed");
+    }
+    *ctx = c;
+  });
+}
+
+void pnoeom_destroy(pnoeom_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  delete ctx;
+}
+
+int pno_build(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts, void* cuda_stream, pnoeom_pno** out) {
+  return guard([&] {
+    PN_CHECK(ctx && sys && opts && out, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    auto* P = new pnoeom_pno();
+    try {
+      pnoeom::build_system(ctx, sys, opts, st(cuda_stream), P);
+      if (ctx->budget && P->footprint > ctx->budget)
+        throw pnoeom::Error(PNOEOM_ERR_NOMEM, "device footprint " + std::to_string(P->footprint) +
+                                                  " bytes exceeds the context budget");
+    } catch (...) {
+      delete P;
+      throw;
+    }
+    *out = P;
+  });
+}
+
+void pno_destroy(pnoeom_pno* pno) { delete pno; }
+
+double pno_build_seconds(const pnoeom_pno* pno) { return pno ? pno->build_seconds : 0.0; }
+
+int pno_query(const pnoeom_pno* pno, int* npairs, const int** n_ij, const int** n_i, size_t* vec_len,
+              size_t* footprint_bytes) {
+  return guard([&] {
+    PN_CHECK(pno, PNOEOM_ERR_INVALID_ARG, "pno is NULL");
+    if (npairs) *npairs = pno->npairs;
+    if (n_ij) *n_ij = pno->nij.data();
+    if (n_i) *n_i = pno->ni.data();
+    if (vec_len) *vec_len = (size_t)pno->L;
+    if (footprint_bytes) *footprint_bytes = pno->footprint;
+  });
+}
+
+int pno_get_basis(const pnoeom_pno* pno, int pair, double* U, double* fbar) {
+  return guard([&] {
+    PN_CHECK(pno && U, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    int64_t uoff, foff;
+    int n;
+    if (pair >= 0) {
+      PN_CHECK(pair < pno->npairs, PNOEOM_ERR_INVALID_ARG, "pair index out of range");
+      uoff = pno->Uoff_pair[pair]; foff = pno->foff_pair[pair]; n = pno->nij[pair];
+    } else {
+      int i = -pair - 1;
+      PN_CHECK(i < pno->o, PNOEOM_ERR_INVALID_ARG, "OSV index out of range");
+      uoff = pno->Uoff_osv[i]; foff = pno->foff_osv[i]; n = pno->ni[i];
+    }
+    if (n) {
+      PN_CUDA(cudaMemcpy(U, pno->U.get() + uoff, (size_t)pno->v * n * 8, cudaMemcpyDeviceToHost));
+      if (fbar) PN_CUDA(cudaMemcpy(fbar, pno->fbar.get() + foff, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    }
+  });
+}
+
+int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev, int precision,
+          void* cuda_stream) {
+  return guard([&] {
+    PN_CHECK(ctx && pno, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CHECK(nvec >= 0, PNOEOM_ERR_INVALID_ARG, "nvec < 0");
+    if (nvec == 0) return;
+    PN_CHECK(r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL vector");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    auto* P = const_cast<pnoeom_pno*>(pno);
+    if (precision == PNOEOM_FP64)
+      pnoeom::apply_sigma<double>(P, nvec, (const double*)r_dev, (double*)s_dev, st(cuda_stream));
+    else if (precision == PNOEOM_FP32)
+      pnoeom::apply_sigma<float>(P, nvec, (const float*)r_dev, (float*)s_dev, st(cuda_stream));
+    else
+      throw pnoeom::Error(PNOEOM_ERR_INVALID_ARG, "unknown precision");
+  });
+}
+
+int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, void* cuda_stream, double* energies,
+                   double* res_norms, int* iters) {
+  int conv = 0;
+  int rc = guard([&] {
+    PN_CHECK(ctx && pno && opts && energies && res_norms && iters, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::run_davidson(ctx, pno, opts, st(cuda_stream), energies, res_norms, iters, &conv);
+  });
+  if (rc == PNOEOM_OK && !conv) {
+    g_last_error = "Davidson did not converge within max_iter";
+    return PNOEOM_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+int pno_get_eigenvectors(const pnoeom_pno* pno, double* X) {
+  return guard([&] {
+    PN_CHECK(pno && X, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    std::copy(pno->last_X.begin(), pno->last_X.end(), X);
+  });
+}
+
+int pno_get_occupations(const pnoeom_pno* pno, double* occ) {
+  return guard([&] {
+    PN_CHECK(pno && occ, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    std::copy(pno->occupations.begin(), pno->occupations.end(), occ);
+  });
+}
+
+int pno_get_cis_vectors(const pnoeom_pno* pno, double* b) {
+  return guard([&] {
+    PN_CHECK(pno && b, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    std::copy(pno->cis_b.begin(), pno->cis_b.end(), b);
+  });
+}
+
+int pno_get_cis(const pnoeom_pno* pno, double* omega) {
+  return guard([&] {
+    PN_CHECK(pno && omega, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    std::copy(pno->cis_omega.begin(), pno->cis_omega.end(), omega);
+  });
+}
+
+int pnoeom_small_eig(int n, const double* A, double* wr, double* wi, double* VR) {
+  return guard([&] {
+    PN_CHECK(n >= 1 && A && wr && wi && VR, PNOEOM_ERR_INVALID_ARG, "bad arguments");
+    PN_CHECK(pnoeom::small_eig(n, A, wr, wi, VR) == 0, PNOEOM_ERR_NOT_CONVERGED, "QR iteration did not converge");
+  });
+}
+
+}  // extern "C"

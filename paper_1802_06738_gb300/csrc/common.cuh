@@ -1,0 +1,87 @@
+// Shared helpers of the pnoeom library: error plumbing, device buffers,
+// the device context (stream + cuSOLVER handle).
+#pragma once
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+#include <cstdio>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <stdexcept>
+#include "../../include/pnoeom.h"
+
+namespace pnoeom {
+
+// Library-internal exception carrying a pnoeom error code; the C entry points
+// translate it into a return code and a thread-local message.
+struct Error : std::runtime_error {
+  int code;
+  Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define PN_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      throw ::pnoeom::Error(e_ == cudaErrorMemoryAllocation ? PNOEOM_ERR_NOMEM      \
+                                                            : PNOEOM_ERR_CUDA,     \
+                            std::string(#call) + ": " + cudaGetErrorString(e_));   \
+  } while (0)
+
+#define PN_SOLVER(call)                                                            \
+  do {                                                                             \
+    cusolverStatus_t s_ = (call);                                                  \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                             \
+      throw ::pnoeom::Error(PNOEOM_ERR_CUDA,                                       \
+                            std::string(#call) + ": cusolver status " + std::to_string((int)s_)); \
+  } while (0)
+
+#define PN_CHECK(cond, code, msg)                                                  \
+  do { if (!(cond)) throw ::pnoeom::Error((code), (msg)); } while (0)
+
+// Owning device buffer (cudaMalloc/cudaFree).  Counts bytes into a shared
+// footprint counter so handles can report their device footprint.
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  size_t* counter = nullptr;
+  DBuf() = default;
+  explicit DBuf(size_t count, size_t* ctr = nullptr) { alloc(count, ctr); }
+  void alloc(size_t count, size_t* ctr = nullptr) {
+    release();
+    n = count;
+    counter = ctr;
+    if (count) PN_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    if (counter) *counter += count * sizeof(T);
+  }
+  void release() {
+    if (p) cudaFree(p);
+    if (counter) *counter -= n * sizeof(T);
+    p = nullptr; n = 0; counter = nullptr;
+  }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { p = o.p; n = o.n; counter = o.counter; o.p = nullptr; o.n = 0; o.counter = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; counter = o.counter; o.p = nullptr; o.n = 0; o.counter = nullptr; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  T* get() const { return p; }
+  void zero(cudaStream_t s) { if (n) PN_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
+  void upload(const T* h, size_t count, cudaStream_t s) {
+    if (count) PN_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  void download(T* h, size_t count, cudaStream_t s) const {
+    if (count) PN_CUDA(cudaMemcpyAsync(h, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+  }
+};
+
+}  // namespace pnoeom
+
+struct pnoeom_ctx {
+  int device = 0;
+  size_t budget = 0;
+  cusolverDnHandle_t solver = nullptr;
+};

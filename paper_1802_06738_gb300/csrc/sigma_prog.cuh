@@ -1,0 +1,48 @@
+// The sigma program: R-independent PNO-space operator blocks (the "pool")
+// plus two problem lists applied to a batch of packed vectors.
+//   * Sandwich problems  C += alpha * opA(A) * opX(X) * opB(B)   (small blocks)
+//   * GEMV problems      c += alpha * A * x   (dense blocks; all roots per CTA)
+// Operands are addressed by (buffer, offset).  Buffers: POOL (shared by all
+// roots), RIN (input vector of the root), WORK (per-root intermediates),
+// SOUT (output vector of the root).
+#pragma once
+#include "common.cuh"
+
+namespace pnoeom {
+
+enum BufId : int { B_POOL = 0, B_RIN = 1, B_WORK = 2, B_SOUT = 3, B_NONE = 4 };
+
+struct SProb {
+  int64_t a_off, x_off, b_off, c_off;
+  int a_buf, x_buf, b_buf, c_buf;     // a_buf/b_buf == B_NONE: identity
+  int M, K1, K2, N;                   // A: M x K1, X: K1 x K2, B: K2 x N, C: M x N
+  int lda, ldx, ldb, ldc;
+  int ta, tx, tb, tc;                 // transposed storage flags; tc: C^T is stored
+  int m0, n0;                         // output tile origin (tiles of at most 64 x 64)
+  double alpha;
+};
+
+struct VProb {
+  int64_t a_off, x_off, c_off;
+  int x_buf, c_buf;
+  int M, K;                           // A: M x K row-major (lda)
+  int lda;
+  int x_stride, c_stride;             // element strides of x and c
+  int xvec_n, cvec_n;                 // > 0: vectorised n x n block read / written transposed
+  int m0;                             // row tile origin (tiles of 64 rows)
+  double alpha;
+};
+
+struct Buffers {
+  const void* pool;
+  const void* rin; int64_t rin_stride;
+  void* work; int64_t work_stride;
+  void* sout; int64_t sout_stride;
+};
+
+template <typename T>
+void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int smem_elems, cudaStream_t s);
+template <typename T>
+void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cudaStream_t s);
+
+}  // namespace pnoeom
