@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(pkg):
 @pytest.mark.parametrize("n", [1, 2, 3, 8, 24, 48])
 def test_small_eig_real_spectrum(pkg, n):
     rng = np.random.default_rng(n)
-    A = np.diag(np.linspace(0.3, 3.0, n)) + 0.02 * rng.standard_normal((n, n))
+    A = np.diag(np.linspace(0.3, 3.0, n)) + (0.05 / n) * rng.standard_normal((n, n))
     w, V = pkg.pnoeom_small_eig(A)
     ref = np.sort(np.linalg.eigvals(A).real)
     assert np.abs(np.sort(w.real) - ref).max() < 1e-12
@@ -54,7 +54,9 @@ def test_small_eig_complex_pairs(pkg):
     A = rng.standard_normal((9, 9))
     w, _ = pkg.pnoeom_small_eig(A)
     ref = np.linalg.eigvals(A)
-    assert np.abs(np.sort_complex(w) - np.sort_complex(ref)).max() < 1e-11
+    # every eigenvalue matches one of LAPACK's (conjugate pairs may come in either order)
+    d = np.abs(w[:, None] - ref[None, :])
+    assert d.min(axis=1).max() < 1e-11 and d.min(axis=0).max() < 1e-11
 
 
 def test_errors_are_codes_not_aborts(pkg):
