@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 state-averaged PNO-EOM-CCSD engine.
+
+Workload (one GPU): the medium synthetic system, o = 20 occupied, v = 200
+virtual, naux = 600 density-fitting functions, 6 roots, T_CutPNO = 1e-7, T2
+from Eq. T1 (seed 2 of the generator in synthetic.py).  A step is one
+sigma evaluation of all 6 roots with the PNO-space operators resident in
+HBM; the metric is sigma-evaluations per second (one sigma-eval = Hbar applied
+to one root vector).  The headline runs the mixed path (FP32 sigma); the FP64
+path, full Davidson solve latencies (mixed + FP64 refinement, and plain FP64)
+and the setup time are reported beside it.
+
+Multi-GPU: every rank solves its own replica of the workload (independent
+systems, no collective on the data path); value = all ranks' sigma-evals /
+max-over-ranks time ("scaling": "weak").
+
+--impl reference times the FP64 CPU oracle (oracle/) on the host cores on
+the same workload and metric; each step is one oracle sigma-eval of one
+root vector, after an untimed oracle setup.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "medium": dict(o=20, v=200, naux=600, nroots=6, t_pno=1e-7, seed=2),
+    "small": dict(o=5, v=20, naux=60, nroots=3, t_pno=1e-7, seed=1),
+}
+METRIC = "PNO-EOM-CCSD sigma-evals/s (mixed FP32 sigma, FP64 setup/orthogonalisation)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium", choices=list(WORKLOADS))
+    ap.add_argument("--solves", type=int, default=3, help="repeated Davidson solves for latency percentiles")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); smax = float(r[2])
+                for nm, val in zip(names, r[5:9]):
+                    if "Active" in val and "Not" not in val:
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_setup(w):
+    """The oracle's PNO-space sigma for the workload (host, FP64)."""
+    import numpy as np
+    from synthetic import make_system
+    from oracle import ccsd, eom, hamiltonian as hm, pno
+    s = make_system(w["o"], w["v"], w["naux"], w["seed"])
+    eps, B, o, v = s["eps"], s["B"], w["o"], w["v"]
+    t2 = ccsd.mp1_t2(eps, B, o)
+    sig = eom.Sigma(np.zeros((o, v)), t2, hm.hcore_from_fock(eps, B, o), B, o)
+    sp = pno.PNOSpace(eps, B, o, w["nroots"], w["t_pno"])
+    return sp, pno.PNOSigma(sig, sp)
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, ws, rank):
+    """Oracle arm: FP64 CPU sigma-evals/s on the host cores."""
+    if rank != 0:
+        return
+    import numpy as np
+    w = WORKLOADS[args.workload]
+    t0 = time.time()
+    sp, ps = oracle_setup(w)
+    setup_s = time.time() - t0
+    rng = np.random.default_rng(0)
+    x = sp.symmetrize(rng.standard_normal(sp.length))
+    for _ in range(min(args.warmup, 1)):
+        ps(x)
+    # one oracle sigma-eval takes tens of seconds: time at most 3 of them so the
+    # arm ends within a few minutes ("steps" reports the number timed)
+    nsteps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        ps(x)
+    dt = time.perf_counter() - t0
+    args.steps = nsteps
+    val = args.steps / dt
+    cores = cpu_threads()
+    line = {"impl": "reference", "metric": METRIC.replace("mixed FP32 sigma, FP64 setup/orthogonalisation", "FP64 CPU oracle"),
+            "value": val, "unit": "sigma-evals/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: o={w['o']} v={w['v']} naux={w['naux']} roots={w['nroots']} "
+                                   f"T_PNO={w['t_pno']} MP1 T2 (seed {w['seed']})", "vec_len": int(sp.length)},
+            "cpu_baseline": {"value": val, "unit": "sigma-evals/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle sigma-evals of one root vector after a {setup_s:.0f} s untimed setup"},
+            "e2e": {"value": val, "unit": "sigma-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import numpy as np
+    import torch
+    import paper_1802_06738_gb300 as pkg
+    from synthetic import make_system
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        pkg.build()
+    barrier(ws)
+    w = WORKLOADS[args.workload]
+    o, nr = w["o"], w["nroots"]
+    s = make_system(w["o"], w["v"], w["naux"], w["seed"])
+    ctx = pkg.Context(local)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    opts_mixed = pkg.make_opts(t_pno=w["t_pno"], nroots=nr, precision=pkg.FP32, refine_fp64=1)
+    gp = pkg.PNO(ctx, s["eps"], s["B"], o, opts=opts_mixed, stream=stream)
+    build_s = gp.build_seconds
+    L = gp.length
+
+    # --- full Davidson solves: latency (mixed + FP64 refinement, and plain FP64)
+    lat_mixed, lat_fp64 = [], []
+    e_mixed = e_fp64 = None
+    it_mixed = it_fp64 = None
+    opts_fp64 = pkg.make_opts(t_pno=w["t_pno"], nroots=nr, precision=pkg.FP64)
+    for k in range(args.solves):
+        torch.cuda.synchronize(); t0 = time.perf_counter()
+        e_mixed, rn, it_mixed, conv_m = gp.davidson_solve(opts_mixed, stream=stream)
+        torch.cuda.synchronize(); lat_mixed.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        e_fp64, rn64, it_fp64, conv_64 = gp.davidson_solve(opts_fp64, stream=stream)
+        torch.cuda.synchronize(); lat_fp64.append(time.perf_counter() - t0)
+
+    # --- timed sigma steps, operators resident in HBM
+    rng = np.random.default_rng(1 + rank)
+    R64 = torch.tensor(rng.standard_normal((nr, L)), device=dev)
+    R32 = R64.float()
+    S32 = torch.empty_like(R32)
+    S64 = torch.empty_like(R64)
+    for _ in range(args.warmup):
+        gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
+    gp.set_timing(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
+        ev1.record()
+        torch.cuda.synchronize()
+    barrier(ws)
+    t_mixed = ev0.elapsed_time(ev1) / 1e3
+    prof = gp.sigma_timing(nr, pkg.FP32)
+    gp.set_timing(False)
+    t_mixed = max_over_ranks(t_mixed, ws, dev)
+
+    # FP64 sigma steps
+    k64 = max(3, args.steps // 2)
+    for _ in range(max(1, args.warmup // 2)):
+        gp.sigma(R64, S64, precision=pkg.FP64, stream=stream)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(k64):
+        gp.sigma(R64, S64, precision=pkg.FP64, stream=stream)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_fp64 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+
+    # end to end through the C ABI: host vectors in pinned memory, copies inside the timed region
+    Rh = R32.cpu().pin_memory()
+    Sh = torch.empty_like(Rh).pin_memory()
+    Rd = torch.empty_like(R32)
+    Sd = torch.empty_like(R32)
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Rd.copy_(Rh, non_blocking=True)
+        gp.sigma(Rd, Sd, precision=pkg.FP32, stream=stream)
+        Sh.copy_(Sd, non_blocking=True)
+        torch.cuda.synchronize()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws, dev)
+
+    # mixed vs FP64 sigma on the same vectors
+    gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
+    gp.sigma(R64, S64, precision=pkg.FP64, stream=stream)
+    torch.cuda.synchronize()
+    sig_rel_err = float((S32.double() - S64).abs().max() / S64.abs().max())
+
+    if rank != 0:
+        return
+    value = ws * nr * args.steps / t_mixed
+    # roofline of the dominant kernel class
+    peaks = {}
+    pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pf):
+        peaks = json.load(open(pf))
+    hbm_peak, peak_src = (peaks.get("hbm_gbs"), "of measured") if peaks.get("hbm_gbs") else (6800.0, "of fallback")
+    dom = max(prof, key=lambda d: d["ms"])
+    avg_ms = dom["ms"] / args.steps          # per sigma call (the class's launches of one call)
+    achieved_gbs = dom["bytes"] / (avg_ms * 1e-3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        traffic = json.load(open(tf)).get(dom["name"])
+    cpu = None
+    if not args.no_cpu_baseline and args.gpus == 1:
+        t0 = time.time()
+        sp, ps = oracle_setup(w)
+        setup_s = time.time() - t0
+        x = sp.symmetrize(np.random.default_rng(0).standard_normal(sp.length))
+        t0 = time.perf_counter()
+        ps(x)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "sigma-evals/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"1 oracle sigma-eval of one root vector of the same workload ({dt:.1f} s) after a "
+                         f"{setup_s:.0f} s untimed oracle setup"}
+    golden = None
+    gfile = os.path.join(ROOT, "tests", "golden", f"oracle_{args.workload}.json")
+    if os.path.exists(gfile):
+        gold = json.load(open(gfile))
+        golden = {"oracle_energies": gold["energies"],
+                  "abs_err_mixed_refined": [abs(a - b) for a, b in zip(e_mixed, gold["energies"])],
+                  "abs_err_fp64": [abs(a - b) for a, b in zip(e_fp64, gold["energies"])]}
+    lat = lambda xs: {"p50_s": float(np.percentile(xs, 50)), "p99_s": float(np.percentile(xs, 99)), "n": len(xs)}
+    line = {
+        "metric": METRIC, "value": value, "unit": "sigma-evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: o={w['o']} v={w['v']} naux={w['naux']} roots={nr} "
+                               f"T_PNO={w['t_pno']} MP1 T2 (seed {w['seed']})",
+                   "vec_len": int(L), "n_ij_mean": float(np.mean(gp.n_ij)), "n_ij_max": int(np.max(gp.n_ij)),
+                   "n_osv_total": int(np.sum(gp.n_i)), "parallelism": f"replicas x{ws}",
+                   "l2": "operator pool larger than L2 (no flush)", "device_footprint_bytes": int(gp.footprint)},
+        "fp64_path": {"value": ws * nr * k64 / t_fp64, "unit": "sigma-evals/s", "steps": k64,
+                      "ms_per_step": 1e3 * t_fp64 / k64},
+        "mixed_vs_fp64_sigma_max_rel_err": sig_rel_err,
+        "solve": {"mixed_refined": {**lat(lat_mixed), "iterations": it_mixed, "energies": list(map(float, e_mixed))},
+                  "fp64": {**lat(lat_fp64), "iterations": it_fp64, "energies": list(map(float, e_fp64))},
+                  "pno_build_s": build_s},
+        "energy_check": golden,
+        "e2e": {"value": ws * nr * args.steps / t_e2e, "unit": "sigma-evals/s",
+                "h2d_bytes_per_step": int(Rh.numel() * 4), "d2h_bytes_per_step": int(Sh.numel() * 4)},
+        "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved_gbs / hbm_peak, "peak_source": peak_src,
+                     "traffic": traffic, "algorithmic_bytes_per_call": dom["bytes"], "avg_ms_per_call": avg_ms,
+                     "launches_per_call": dom["launches"] / args.steps},
+        "kernels": prof,
+        "gpu_launches": int(sum(d["launches"] for d in prof)),
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -159,6 +159,22 @@ int pno_get_cis(const pnoeom_pno* pno, double* omega);
  * PNOEOM_ERR_INVALID_ARG, or PNOEOM_ERR_NOT_CONVERGED. */
 int pnoeom_small_eig(int n, const double* A, double* wr, double* wi, double* VR);
 
+/* Tracing of sigma.  pno_set_timing(pno, 1) clears the counters and makes
+ * every later sigma call on this handle record CUDA events, on the stream it
+ * launches on, around each of its kernels; 0 stops recording.
+ * pno_sigma_timing reports, for kernel class `k` (0: ring/ladder sandwich
+ * products into the R-dependent intermediates, 1: dense blocks into those
+ * intermediates, 2: sandwich products into sigma, 3: dense blocks into
+ * sigma), the number of kernel launches recorded, their summed device time
+ * in ms, the algorithmic bytes one sigma call's launches of that class move
+ * for nvec vectors (operator blocks
+ * read once, vector blocks read and written once per vector, at the element
+ * size of `precision`) and their flops.  Any pointer may be NULL.  Blocks
+ * until the recorded events complete. */
+int pno_set_timing(pnoeom_pno* pno, int enable);
+int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, const char** name, int* launches,
+                     double* ms, double* bytes, double* flops);
+
 /* Seconds spent in the last pno_build of this handle (setup time). */
 double pno_build_seconds(const pnoeom_pno* pno);
 

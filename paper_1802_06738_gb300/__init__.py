@@ -48,7 +48,8 @@ def make_opts(t_pno=1e-7, t_osv=-1.0, nroots=3, nroots_solve=None, precision=FP6
 _lib = None
 EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", "pno_destroy",
            "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
-           "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds"]
+           "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds",
+           "pno_set_timing", "pno_sigma_timing"]
 
 
 def lib():
@@ -74,6 +75,8 @@ def lib():
         L.pno_get_cis_vectors.argtypes = [vp, dp]
         L.pnoeom_small_eig.argtypes = [i, dp, dp, dp, dp]
         L.pno_build_seconds.argtypes = [vp]; L.pno_build_seconds.restype = d
+        L.pno_set_timing.argtypes = [vp, i]
+        L.pno_sigma_timing.argtypes = [vp, i, i, i, ctypes.POINTER(ctypes.c_char_p), ip, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -221,6 +224,20 @@ class PNO:
         rc = _check(lib().davidson_solve(self.ctx.h, self.h, ctypes.byref(opts), _stream_ptr(stream), _dptr(e), _dptr(rn),
                                          ctypes.byref(it)), allow=(ERR_NOT_CONVERGED,))
         return e, rn, it.value, rc == OK
+
+    def set_timing(self, enable=True):
+        _check(lib().pno_set_timing(self.h, 1 if enable else 0))
+
+    def sigma_timing(self, nvec, precision=FP64):
+        """Per kernel class: dict(name, launches, ms, bytes, flops) of the recorded sigma calls."""
+        out = []
+        for k in range(4):
+            nm, n = ctypes.c_char_p(), ctypes.c_int()
+            ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _check(lib().pno_sigma_timing(self.h, k, nvec, precision, ctypes.byref(nm), ctypes.byref(n), ctypes.byref(ms),
+                                          ctypes.byref(by), ctypes.byref(fl)))
+            out.append(dict(name=nm.value.decode(), launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value))
+        return out
 
     def eigenvectors(self):
         import numpy as np

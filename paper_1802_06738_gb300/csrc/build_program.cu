@@ -18,6 +18,7 @@
 #include "pno.cuh"
 #include <algorithm>
 #include <cmath>
+#include <set>
 
 namespace pnoeom {
 namespace {
@@ -653,15 +654,16 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   auto add_gemv = [&](std::vector<VProb>& L_, int64_t aoff, int M, int K, int lda, int xbuf, int64_t xoff, int xs, int xvn,
                       int cbuf, int64_t coff, int cs, int cvn, double al) {
     if (M <= 0 || K <= 0 || al == 0.0) return;
-    for (int m0 = 0; m0 < M; m0 += 64) {
-      VProb q{};
-      q.a_off = aoff; q.x_off = xoff; q.c_off = coff;
-      q.x_buf = xbuf; q.c_buf = cbuf;
-      q.M = M; q.K = K; q.lda = lda;
-      q.x_stride = xs; q.c_stride = cs; q.xvec_n = xvn; q.cvec_n = cvn;
-      q.m0 = m0; q.alpha = al;
-      L_.push_back(q);
-    }
+    for (int m0 = 0; m0 < M; m0 += 64)
+      for (int k0 = 0; k0 < K; k0 += GEMV_KC) {
+        VProb q{};
+        q.a_off = aoff; q.x_off = xoff; q.c_off = coff;
+        q.x_buf = xbuf; q.c_buf = cbuf;
+        q.M = M; q.K = K; q.lda = lda;
+        q.x_stride = xs; q.c_stride = cs; q.xvec_n = xvn; q.cvec_n = cvn;
+        q.m0 = m0; q.k0 = k0; q.klen = std::min(GEMV_KC, K - k0); q.alpha = al;
+        L_.push_back(q);
+      }
   };
   auto Ro = [&](int x, int y) { return P->off_ij[blk(x, y)]; };          // stored block offset
   auto Rt = [&](int x, int y) { return x > y ? 1 : 0; };                  // R^{xy} = stored^T ?
@@ -754,6 +756,61 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
              nq, B_POOL, Sblk(q, p), nij, 0, W_h[(((size_t)k * o + i) * o + l) * o + j]);
     }
   }
+  // algorithmic traffic and flops of each kernel class (tracing / roofline):
+  // operator blocks counted once per launch (distinct blocks), vector blocks
+  // once per vector (distinct ranges), flops as issued
+  {
+    auto acc_sw = [&](const std::vector<SProb>& Lst, int cls) {
+      std::set<std::pair<int64_t, int64_t>> pool_blocks, vec_blocks;
+      double fl = 0;
+      for (const SProb& q : Lst) {
+        if (q.a_buf == B_POOL) pool_blocks.insert({q.a_off, (int64_t)q.M * q.K1});
+        if (q.b_buf == B_POOL) pool_blocks.insert({q.b_off, (int64_t)q.K2 * q.N});
+        if (q.x_buf != B_POOL) vec_blocks.insert({q.x_off + ((int64_t)q.x_buf << 40), (int64_t)q.K1 * q.K2});
+        vec_blocks.insert({q.c_off + ((int64_t)q.c_buf << 40), (int64_t)q.M * q.N});
+        const int Mt = std::min(64, q.M - q.m0), Nt = std::min(64, q.N - q.n0);
+        fl += 2.0 * q.K1 * Nt * q.K2 + 2.0 * Mt * Nt * q.K1;
+      }
+      double pe = 0, ve = 0;
+      for (auto& b : pool_blocks) pe += b.second;
+      for (auto& b : vec_blocks) ve += b.second;
+      P->prof_pool_elems[cls] = pe; P->prof_vec_elems[cls] = ve; P->prof_flops[cls] = fl;
+    };
+    auto acc_v = [&](const std::vector<VProb>& Lst, int cls) {
+      std::set<std::pair<int64_t, int64_t>> vec_blocks;
+      double pe = 0, fl = 0;
+      for (const VProb& q : Lst) {
+        const int rows = std::min(64, q.M - q.m0);
+        pe += (double)rows * q.klen;
+        fl += 2.0 * rows * q.klen;
+        vec_blocks.insert({q.x_off + ((int64_t)q.x_buf << 40), (int64_t)q.K * q.x_stride});
+        vec_blocks.insert({q.c_off + ((int64_t)q.c_buf << 40), (int64_t)q.M * q.c_stride});
+      }
+      double ve = 0;
+      for (auto& b : vec_blocks) ve += b.second;
+      P->prof_pool_elems[cls] = pe; P->prof_vec_elems[cls] = ve; P->prof_flops[cls] = fl;
+    };
+    acc_sw(G.sp1, 0); acc_v(G.vp1, 1); acc_sw(G.sp2, 2); acc_v(G.vp2, 3);
+  }
+  // split each sandwich list: all dims <= SMALL_DIM (single tile) go to the shared-memory kernel
+  auto split = [&](const std::vector<SProb>& Lst, std::vector<SProb>& small, std::vector<SProb>& gen, int* dims) {
+    for (const SProb& q : Lst) {
+      if (q.M <= SMALL_DIM && q.N <= SMALL_DIM && q.K1 <= SMALL_DIM && q.K2 <= SMALL_DIM) {
+        small.push_back(q);
+        dims[0] = std::max(dims[0], q.M); dims[1] = std::max(dims[1], q.K1);
+        dims[2] = std::max(dims[2], q.K2); dims[3] = std::max(dims[3], q.N);
+      } else {
+        gen.push_back(q);
+      }
+    }
+  };
+  std::vector<SProb> s1s, s1g, s2s, s2g;
+  split(G.sp1, s1s, s1g, P->small_dims1);
+  split(G.sp2, s2s, s2g, P->small_dims2);
+  P->n_sp1s = (int)s1s.size(); P->n_sp2s = (int)s2s.size();
+  P->sp_small1.alloc(std::max<size_t>(1, s1s.size()), fp); P->sp_small1.upload(s1s.data(), s1s.size(), s);
+  P->sp_small2.alloc(std::max<size_t>(1, s2s.size()), fp); P->sp_small2.upload(s2s.data(), s2s.size(), s);
+  G.sp1 = s1g; G.sp2 = s2g;
   P->n_sp1 = (int)G.sp1.size(); P->n_sp2 = (int)G.sp2.size();
   P->n_vp1 = (int)G.vp1.size(); P->n_vp2 = (int)G.vp2.size();
   P->sp_phase1.alloc(std::max<size_t>(1, G.sp1.size()), fp); P->sp_phase1.upload(G.sp1.data(), G.sp1.size(), s);

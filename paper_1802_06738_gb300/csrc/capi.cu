@@ -77,6 +77,39 @@ void pno_destroy(pnoeom_pno* pno) { delete pno; }
 
 double pno_build_seconds(const pnoeom_pno* pno) { return pno ? pno->build_seconds : 0.0; }
 
+int pno_set_timing(pnoeom_pno* pno, int enable) {
+  return guard([&] {
+    PN_CHECK(pno, PNOEOM_ERR_INVALID_ARG, "pno is NULL");
+    for (auto& e : pno->events) { cudaEventSynchronize(e.second.second); cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
+    pno->events.clear();
+    for (int& x : pno->prof_launches) x = 0;
+    pno->timing = enable != 0;
+  });
+}
+
+int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, const char** name, int* launches,
+                     double* ms, double* bytes, double* flops) {
+  static const char* names[4] = {"sandwich->intermediates", "dense->intermediates", "sandwich->sigma", "dense->sigma"};
+  return guard([&] {
+    PN_CHECK(pno && k >= 0 && k < 4, PNOEOM_ERR_INVALID_ARG, "bad arguments");
+    int n = 0;
+    double t = 0;
+    for (const auto& e : pno->events) {
+      if (e.first != k) continue;
+      PN_CUDA(cudaEventSynchronize(e.second.second));
+      float x = 0;
+      PN_CUDA(cudaEventElapsedTime(&x, e.second.first, e.second.second));
+      t += x; ++n;   // n: sigma calls recorded
+    }
+    const double es = precision == PNOEOM_FP32 ? 4.0 : 8.0;
+    if (name) *name = names[k];
+    if (launches) *launches = pno->prof_launches[k];
+    if (ms) *ms = t;
+    if (bytes) *bytes = es * (pno->prof_pool_elems[k] + (double)nvec * pno->prof_vec_elems[k]);
+    if (flops) *flops = (double)nvec * pno->prof_flops[k];
+  });
+}
+
 int pno_query(const pnoeom_pno* pno, int* npairs, const int** n_ij, const int** n_i, size_t* vec_len,
               size_t* footprint_bytes) {
   return guard([&] {

@@ -5,6 +5,9 @@
 #include "sigma_prog.cuh"
 
 struct pnoeom_pno {
+  ~pnoeom_pno() {
+    for (auto& e : events) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
+  }
   int o = 0, v = 0, naux = 0, nroots_sa = 0;
   double t_pno = 0, t_osv = 0;
   bool has_t1 = false;
@@ -24,6 +27,10 @@ struct pnoeom_pno {
   pnoeom::DBuf<pnoeom::SProb> sp_phase1, sp_phase2;
   pnoeom::DBuf<pnoeom::VProb> vp_phase1, vp_phase2;
   int n_sp1 = 0, n_sp2 = 0, n_vp1 = 0, n_vp2 = 0;
+  pnoeom::DBuf<pnoeom::SProb> sp_small1, sp_small2;   // sandwich problems with all dims <= SMALL_DIM
+  int n_sp1s = 0, n_sp2s = 0;
+  int small_dims1[4] = {1, 1, 1, 1}, small_dims2[4] = {1, 1, 1, 1};   // max M, K1, K2, N
+  int prof_launches[4] = {0, 0, 0, 0};
   int smem_elems = 0;
   int64_t work_len = 0;                      // FvR (v*v) + FoR (o*o)
   int64_t work_fvr = 0, work_for = 0;
@@ -36,6 +43,11 @@ struct pnoeom_pno {
   int last_nroots = 0;
   // per-call scratch kept across calls
   pnoeom::DBuf<double> work64; pnoeom::DBuf<float> work32;
+  // tracing: per kernel class, operator elements read once per launch,
+  // vector elements read+written per vector, flops per vector
+  double prof_pool_elems[4] = {0, 0, 0, 0}, prof_vec_elems[4] = {0, 0, 0, 0}, prof_flops[4] = {0, 0, 0, 0};
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
   size_t footprint = 0;
   double build_seconds = 0;
 };

@@ -69,33 +69,104 @@ __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ prob
   }
 }
 
+// Small sandwich: one problem per CTA, all roots in the CTA.  A (M x K1) and
+// B (K2 x N) are staged once in shared memory; per root X is staged, T = X B
+// formed in shared memory, then C += alpha A T (atomic).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict__ probs, Buffers bufs, int nroots,
+                                                        int dm, int dk1, int dk2, int dn) {
+  extern __shared__ unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);     // dm x dk1
+  T* Bs = As + dm * dk1;                      // dk2 x dn
+  T* Xs = Bs + dk2 * dn;                      // dk1 x dk2
+  T* Ts = Xs + dk1 * dk2;                     // dk1 x dn
+  const SProb P = probs[blockIdx.x];
+  const int M = P.M, N = P.N, K1 = P.K1, K2 = P.K2;
+  const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
+  if (hasA) {
+    const T* A = cbuf<T>(bufs, P.a_buf, 0) + P.a_off;
+    for (int e = threadIdx.x; e < M * K1; e += blockDim.x) {
+      const int m = e / K1, k = e % K1;
+      As[m * dk1 + k] = P.ta ? A[(int64_t)k * P.lda + m] : A[(int64_t)m * P.lda + k];
+    }
+  }
+  if (hasB) {
+    const T* Bm = cbuf<T>(bufs, P.b_buf, 0) + P.b_off;
+    for (int e = threadIdx.x; e < K2 * N; e += blockDim.x) {
+      const int k = e / N, n = e % N;
+      Bs[k * dn + n] = P.tb ? Bm[(int64_t)n * P.ldb + k] : Bm[(int64_t)k * P.ldb + n];
+    }
+  }
+  const T alpha = (T)P.alpha;
+  for (int r = 0; r < nroots; ++r) {
+    const T* X = cbuf<T>(bufs, P.x_buf, r) + P.x_off;
+    __syncthreads();
+    for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
+      const int a = e / K2, b = e % K2;
+      Xs[a * dk2 + b] = P.tx ? X[(int64_t)b * P.ldx + a] : X[(int64_t)a * P.ldx + b];
+    }
+    __syncthreads();
+    if (hasB) {
+      for (int e = threadIdx.x; e < K1 * N; e += blockDim.x) {
+        const int a = e / N, n = e % N;
+        T acc = T(0);
+        for (int k = 0; k < K2; ++k) acc += Xs[a * dk2 + k] * Bs[k * dn + n];
+        Ts[a * dn + n] = acc;
+      }
+      __syncthreads();
+    }
+    T* C = mbuf<T>(bufs, P.c_buf, r) + P.c_off;
+    for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
+      const int m = e / N, n = e % N;
+      T acc = T(0);
+      if (hasA) {
+        if (hasB) for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Ts[k * dn + n];
+        else for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Xs[k * dk2 + n];
+      } else {
+        acc = hasB ? Ts[m * dn + n] : Xs[m * dk2 + n];
+      }
+      T* c = P.tc ? C + (int64_t)n * P.ldc + m : C + (int64_t)m * P.ldc + n;
+      atomicAdd(c, alpha * acc);
+    }
+  }
+}
+
 constexpr int VR = 8;   // roots per pass inside a GEMV CTA
 
-// One 64-row tile of one dense block per CTA; each warp owns 8 rows, lanes
-// stride the K dimension (coalesced reads of the row-major block), and all
-// roots are handled in the same pass so the block is read from HBM once.
+// One (64-row, K-chunk) tile of one dense block per CTA (split-K, atomic
+// accumulation).  The K-chunk of every root's input vector is staged in shared
+// memory; each warp owns 8 rows and its lanes stride K, so the block rows are
+// read from HBM once, coalesced, for all roots.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, Buffers bufs, int nroots) {
+  extern __shared__ unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);   // VR x GEMV_KC
   const VProb P = probs[blockIdx.x];
   const T* A = (const T*)bufs.pool + P.a_off;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const T alpha = (T)P.alpha;
+  const int kl = P.klen;
   for (int r0 = 0; r0 < nroots; r0 += VR) {
     const int nr = min(VR, nroots - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * kl; e += blockDim.x) {
+      const int q = e / kl, kk = e % kl;
+      int xk = P.k0 + kk;
+      if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
+      xs[q * GEMV_KC + kk] = cbuf<T>(bufs, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
+    }
+    __syncthreads();
     for (int ml = warp; ml < 64; ml += 8) {
       const int m = P.m0 + ml;
       if (m >= P.M) break;
-      const T* a = A + (int64_t)m * P.lda;
+      const T* a = A + (int64_t)m * P.lda + P.k0;
       T acc[VR];
 #pragma unroll
       for (int q = 0; q < VR; ++q) acc[q] = T(0);
-      for (int k = lane; k < P.K; k += 32) {
-        const T av = a[k];
-        int xk = k;
-        if (P.xvec_n > 0) xk = (k % P.xvec_n) * P.xvec_n + k / P.xvec_n;
+      for (int kk = lane; kk < kl; kk += 32) {
+        const T av = a[kk];
 #pragma unroll
-        for (int q = 0; q < VR; ++q)
-          if (q < nr) acc[q] += av * cbuf<T>(bufs, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
+        for (int q = 0; q < VR; ++q) acc[q] += av * xs[q * GEMV_KC + kk];
       }
 #pragma unroll
       for (int q = 0; q < VR; ++q) {
@@ -136,13 +207,36 @@ void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b,
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cudaStream_t s) {
   if (nprob <= 0 || nroots <= 0) return;
-  k_gemv<T><<<nprob, 256, 0, s>>>(d_probs, b, nroots);
+  const size_t smem = (size_t)VR * GEMV_KC * sizeof(T);
+  static thread_local bool configured[2] = {false, false};
+  if (!configured[sizeof(T) == 8]) {
+    PN_CUDA(cudaFuncSetAttribute(k_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured[sizeof(T) == 8] = true;
+  }
+  k_gemv<T><<<nprob, 256, smem, s>>>(d_probs, b, nroots);
+  PN_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void run_sandwich_small(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int dm, int dk1, int dk2, int dn,
+                        cudaStream_t s) {
+  if (nprob <= 0 || nroots <= 0) return;
+  const size_t smem = (size_t)(dm * dk1 + dk2 * dn + dk1 * dk2 + dk1 * dn) * sizeof(T);
+  static thread_local size_t configured[2] = {0, 0};
+  size_t& conf = configured[sizeof(T) == 8];
+  if (smem > 48 * 1024 && smem > conf) {
+    PN_CUDA(cudaFuncSetAttribute(k_sandwich_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conf = smem;
+  }
+  k_sandwich_small<T><<<nprob, 256, smem, s>>>(d_probs, b, nroots, dm, dk1, dk2, dn);
   PN_CUDA(cudaGetLastError());
 }
 
 template void run_sandwich<double>(const SProb*, int, int, const Buffers&, int, cudaStream_t);
 template void run_sandwich<float>(const SProb*, int, int, const Buffers&, int, cudaStream_t);
 template void run_gemv<double>(const VProb*, int, int, const Buffers&, cudaStream_t);
+template void run_sandwich_small<double>(const SProb*, int, int, const Buffers&, int, int, int, int, cudaStream_t);
+template void run_sandwich_small<float>(const SProb*, int, int, const Buffers&, int, int, int, int, cudaStream_t);
 template void run_gemv<float>(const VProb*, int, int, const Buffers&, cudaStream_t);
 
 }  // namespace pnoeom

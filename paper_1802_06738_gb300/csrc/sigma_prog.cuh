@@ -30,8 +30,12 @@ struct VProb {
   int x_stride, c_stride;             // element strides of x and c
   int xvec_n, cvec_n;                 // > 0: vectorised n x n block read / written transposed
   int m0;                             // row tile origin (tiles of 64 rows)
+  int k0, klen;                       // K chunk of this tile (split-K; klen <= GEMV_KC)
   double alpha;
 };
+
+constexpr int GEMV_KC = 1024;         // K chunk staged in shared memory per GEMV tile
+constexpr int SMALL_DIM = 64;         // sandwich problems with all dims <= this use the shared-memory kernel
 
 struct Buffers {
   const void* pool;
@@ -42,6 +46,10 @@ struct Buffers {
 
 template <typename T>
 void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int smem_elems, cudaStream_t s);
+// all dims <= SMALL_DIM, single tile: A and B staged once, every root in the same CTA
+template <typename T>
+void run_sandwich_small(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int dm, int dk1, int dk2,
+                        int dn, cudaStream_t s);
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cudaStream_t s);
 

@@ -26,10 +26,34 @@ void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s) {
   b.rin = r; b.rin_stride = P->L;
   b.work = work.get(); b.work_stride = P->work_len;
   b.sout = out; b.sout_stride = P->L;
-  run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
-  run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s);
-  run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
-  run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s);
+  auto timed = [&](int cls, auto&& launch) {
+    if (!P->timing) { launch(); return; }
+    cudaEvent_t e0, e1;
+    PN_CUDA(cudaEventCreate(&e0));
+    PN_CUDA(cudaEventCreate(&e1));
+    PN_CUDA(cudaEventRecord(e0, s));
+    launch();
+    PN_CUDA(cudaEventRecord(e1, s));
+    P->events.push_back({cls, {e0, e1}});
+  };
+  const int* d1 = P->small_dims1;
+  const int* d2 = P->small_dims2;
+  timed(0, [&] {
+    run_sandwich_small<T>(P->sp_small1.get(), P->n_sp1s, nvec, b, d1[0], d1[1], d1[2], d1[3], s);
+    run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
+  });
+  timed(1, [&] { run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s); });
+  timed(2, [&] {
+    run_sandwich_small<T>(P->sp_small2.get(), P->n_sp2s, nvec, b, d2[0], d2[1], d2[2], d2[3], s);
+    run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
+  });
+  timed(3, [&] { run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s); });
+  if (P->timing) {   // kernel launches per class in this call
+    P->prof_launches[0] += (P->n_sp1s > 0) + (P->n_sp1 > 0);
+    P->prof_launches[1] += P->n_vp1 > 0;
+    P->prof_launches[2] += (P->n_sp2s > 0) + (P->n_sp2 > 0);
+    P->prof_launches[3] += P->n_vp2 > 0;
+  }
 }
 template void apply_sigma<double>(pnoeom_pno*, int, const double*, double*, cudaStream_t);
 template void apply_sigma<float>(pnoeom_pno*, int, const float*, float*, cudaStream_t);

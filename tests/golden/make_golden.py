@@ -1,0 +1,73 @@
+"""Write oracle fixtures for the GPU tests and the benchmark.
+
+Calls only oracle/ and the seeded generator.  For a workload it stores:
+  * the PNO counts n_ij and n_i;
+  * the Davidson excitation energies (the oracle's FP64 solve, Sec. 2);
+  * sigma of one seeded canonical trial vector, projected (Sec. 2), for the
+    singles and a sample of pair blocks, in the canonical basis (so the
+    comparison does not depend on PNO phases).
+
+Usage: python tests/golden/make_golden.py medium   (about an hour on 8 cores)
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import numpy as np  # noqa: E402
+
+from synthetic import make_system  # noqa: E402
+from oracle import ccsd, davidson, eom, hamiltonian as hm, pno  # noqa: E402
+
+WORKLOADS = {
+    "small": dict(o=5, v=20, naux=60, nroots=3, t_pno=1e-7, seed=1, gs="ccsd"),
+    "medium": dict(o=20, v=200, naux=600, nroots=6, t_pno=1e-7, seed=2, gs="mp1"),
+}
+SAMPLE_PAIRS = {"small": [(0, 0), (0, 4), (2, 3), (4, 4)], "medium": [(0, 19), (5, 5), (7, 12), (18, 19), (19, 19)]}
+
+
+def trial_vector(o, v, seed=123):
+    """Seeded canonical trial vector (r1, symmetric r2)."""
+    rng = np.random.default_rng(seed)
+    r1 = rng.standard_normal((o, v))
+    r2 = rng.standard_normal((o, o, v, v))
+    return r1, 0.5 * (r2 + r2.transpose(1, 0, 3, 2))
+
+
+def main(name):
+    w = WORKLOADS[name]
+    o, v = w["o"], w["v"]
+    t0 = time.time()
+    s = make_system(o, v, w["naux"], w["seed"])
+    eps, B = s["eps"], s["B"]
+    h = hm.hcore_from_fock(eps, B, o)
+    if w["gs"] == "ccsd":
+        t1, t2, _, _ = ccsd.solve_ccsd(eps, B, o)
+    else:
+        t1, t2 = np.zeros((o, v)), ccsd.mp1_t2(eps, B, o)
+    sig = eom.Sigma(t1, t2, h, B, o)
+    sp = pno.PNOSpace(eps, B, o, w["nroots"], w["t_pno"])
+    ps = pno.PNOSigma(sig, sp)
+    print(f"setup {time.time() - t0:.0f} s, L = {sp.length}", flush=True)
+    r1, r2 = trial_vector(o, v)
+    s1, s2 = sp.unpack(ps(sp.pack(r1, r2)))
+    out = {"workload": name, **{k: w[k] for k in ("o", "v", "naux", "nroots", "t_pno", "seed", "gs")},
+           "n_ij": sp.n_ij.tolist(), "n_i": sp.n_i.tolist(), "vec_len": int(sp.length),
+           "sigma_trial_seed": 123, "sigma_s1": s1.tolist(),
+           "sigma_pairs": {f"{i},{j}": s2[i, j].tolist() for (i, j) in SAMPLE_PAIRS[name]}}
+    print(f"sigma done {time.time() - t0:.0f} s", flush=True)
+    e, X, rn, it, conv = davidson.solve(ps, sp, w["nroots"])
+    out.update({"energies": e.tolist(), "residual_norms": rn.tolist(), "iterations": int(it), "converged": bool(conv),
+                "cis_energies": sp.cis_omega.tolist(), "seconds": time.time() - t0})
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    json.dump(out, open(path, "w"))
+    print(f"wrote {path}: energies {e}, converged {conv}, {time.time() - t0:.0f} s", flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "small")
