@@ -127,6 +127,27 @@ int pno_get_basis(const pnoeom_pno* pno, int pair, double* U, double* fbar);
 int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
           int precision, void* cuda_stream);
 
+/* sigma without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory
+ * while they run, such as a serving loop whose latency budget cannot absorb
+ * the device-wide synchronisation cudaMalloc/cudaFree imply, or an
+ * application that has handed all device memory to its own pool allocator.
+ * It computes exactly what sigma() computes, but its scratch memory (the
+ * R-dependent intermediates, nvec * (v*v + o*o) elements) lives in a
+ * file-scope device array of PNOEOM_NOALLOC_SCRATCH_BYTES bytes that every
+ * GPU which loads the library keeps until the process exits.  Calls needing
+ * more scratch than that return PNOEOM_ERR_UNSUPPORTED without launching
+ * anything.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  The array is shared by all calls and keeps the last
+ * call's contents (each call clears what it needs): calls whose executions
+ * overlap on the GPU race on it, so issue them on one stream or otherwise
+ * serialise them.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Arguments, layouts and errors are those of sigma(). */
+#define PNOEOM_NOALLOC_SCRATCH_BYTES (8u << 20)
+int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
+                  int precision, void* cuda_stream);
+
 /* Davidson solve (Sec. 2, PNO-EOM-CCSD Davidson): projected CIS guesses,
  * semicanonical preconditioner omega + f_ii (+ f_jj) - fbar_a (- fbar_b),
  * FP64 orthogonalisation and subspace diagonalisation.  energies and

@@ -49,7 +49,7 @@ _lib = None
 EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", "pno_destroy",
            "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
            "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds",
-           "pno_set_timing", "pno_sigma_timing"]
+           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc"]
 
 
 def lib():
@@ -68,6 +68,7 @@ def lib():
         L.pno_query.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]
         L.pno_get_basis.argtypes = [vp, i, dp, dp]
         L.sigma.argtypes = [vp, vp, i, vp, vp, i, vp]
+        L.sigma_noalloc.argtypes = [vp, vp, i, vp, vp, i, vp]
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
         L.pno_get_cis.argtypes = [vp, dp]

@@ -7,8 +7,18 @@ namespace pnoeom { int small_eig(int n, const double* A, double* wr, double* wi,
 
 namespace {
 thread_local std::string g_last_error;
+}  // namespace
 
-int guard(const std::function<void()>& f) {
+namespace pnoeom {
+// Runs f, translating exceptions into a return code and the thread-local message.
+int guard_call(const std::function<void()>& f);
+}
+
+namespace {
+int guard(const std::function<void()>& f) { return pnoeom::guard_call(f); }
+}  // namespace
+
+int pnoeom::guard_call(const std::function<void()>& f) {
   try {
     f();
     g_last_error.clear();
@@ -24,6 +34,8 @@ int guard(const std::function<void()>& f) {
     return PNOEOM_ERR_CUDA;
   }
 }
+
+namespace {
 inline cudaStream_t st(void* p) { return reinterpret_cast<cudaStream_t>(p); }
 }  // namespace
 

@@ -1,0 +1,79 @@
+// sigma_noalloc: sigma whose scratch lives in a file-scope device array, for
+// callers that must not allocate device memory while they run.
+#include "pno.cuh"
+#include <functional>
+#include <mutex>
+
+namespace pnoeom {
+int guard_call(const std::function<void()>& f);
+}
+
+namespace {
+
+// Scratch of every sigma_noalloc call (all calls share it; see the header).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PNOEOM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 128;
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of the scratch array on `device` (which must be current).
+// In host code the array's name is only a host-side stand-in, so the address
+// is looked up once per device with cudaGetSymbolAddress.
+void* scratch_address(int device) {
+  PN_CHECK(device >= 0 && device < kMaxDevices, PNOEOM_ERR_UNSUPPORTED, "device index too large for sigma_noalloc");
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    void* p = nullptr;
+    PN_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    PN_CHECK(p != nullptr, PNOEOM_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    g_scratch_addr[device] = p;
+  }
+  return g_scratch_addr[device];
+}
+
+template <typename T>
+void sigma_into_scratch(const pnoeom_pno* P, int nvec, const T* r, T* out, T* work, cudaStream_t s) {
+  using namespace pnoeom;
+  PN_CUDA(cudaMemsetAsync(out, 0, (size_t)nvec * P->L * sizeof(T), s));
+  PN_CUDA(cudaMemsetAsync(work, 0, (size_t)nvec * P->work_len * sizeof(T), s));
+  Buffers b;
+  b.pool = sizeof(T) == 8 ? (const void*)P->pool64.get() : (const void*)P->pool32.get();
+  b.rin = r; b.rin_stride = P->L;
+  b.work = work; b.work_stride = P->work_len;
+  b.sout = out; b.sout_stride = P->L;
+  const int* d1 = P->small_dims1;
+  const int* d2 = P->small_dims2;
+  run_sandwich_small<T>(P->sp_small1.get(), P->n_sp1s, nvec, b, d1[0], d1[1], d1[2], d1[3], s);
+  run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
+  run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s);
+  run_sandwich_small<T>(P->sp_small2.get(), P->n_sp2s, nvec, b, d2[0], d2[1], d2[2], d2[3], s);
+  run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
+  run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s);
+}
+
+}  // namespace
+
+extern "C" int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
+                             int precision, void* cuda_stream) {
+  return pnoeom::guard_call([&] {
+    PN_CHECK(ctx && pno, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CHECK(nvec >= 0, PNOEOM_ERR_INVALID_ARG, "nvec < 0");
+    if (nvec == 0) return;
+    PN_CHECK(r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL vector");
+    PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32, PNOEOM_ERR_INVALID_ARG, "unknown precision");
+    const size_t elem = precision == PNOEOM_FP64 ? 8 : 4;
+    const size_t need = (size_t)nvec * (size_t)pno->work_len * elem;
+    PN_CHECK(need <= PNOEOM_NOALLOC_SCRATCH_BYTES, PNOEOM_ERR_UNSUPPORTED,
+             "sigma_noalloc needs " + std::to_string(need) + " bytes of scratch for " + std::to_string(nvec) +
+                 " vectors, more than its fixed " + std::to_string((size_t)PNOEOM_NOALLOC_SCRATCH_BYTES) +
+                 "-byte array; pass fewer vectors per call or use sigma()");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    void* work = scratch_address(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (precision == PNOEOM_FP64)
+      sigma_into_scratch<double>(pno, nvec, (const double*)r_dev, (double*)s_dev, (double*)work, s);
+    else
+      sigma_into_scratch<float>(pno, nvec, (const float*)r_dev, (float*)s_dev, (float*)work, s);
+  });
+}
