@@ -337,6 +337,7 @@ def main():
                      "traffic": traffic, "algorithmic_bytes_per_call": dom["bytes"], "avg_ms_per_call": avg_ms,
                      "launches_per_call": dom["launches"] / args.steps},
         "kernels": prof,
+        "autotune": dict(zip(["candidates_group_rpc_ms", "choice"], gp.autotune_info())),
         "gpu_launches": int(sum(d["launches"] for d in prof)),
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

@@ -49,7 +49,7 @@ _lib = None
 EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", "pno_destroy",
            "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
            "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds",
-           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc"]
+           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info"]
 
 
 def lib():
@@ -69,6 +69,7 @@ def lib():
         L.pno_get_basis.argtypes = [vp, i, dp, dp]
         L.sigma.argtypes = [vp, vp, i, vp, vp, i, vp]
         L.sigma_noalloc.argtypes = [vp, vp, i, vp, vp, i, vp]
+        L.pno_autotune_info.argtypes = [vp, i, ip, ip, dp, ip]
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
         L.pno_get_cis.argtypes = [vp, dp]
@@ -225,6 +226,17 @@ class PNO:
         rc = _check(lib().davidson_solve(self.ctx.h, self.h, ctypes.byref(opts), _stream_ptr(stream), _dptr(e), _dptr(rn),
                                          ctypes.byref(it)), allow=(ERR_NOT_CONVERGED,))
         return e, rn, it.value, rc == OK
+
+    def autotune_info(self):
+        """Candidates [(group size, vectors per CTA, ms per sigma)] and the chosen index."""
+        import numpy as np
+        gs = (ctypes.c_int * 32)()
+        rp = (ctypes.c_int * 32)()
+        ms = np.zeros(32)
+        ch = ctypes.c_int()
+        _check(lib().pno_autotune_info(self.h, 32, gs, rp, _dptr(ms), ctypes.byref(ch)))
+        n = sum(1 for k in range(32) if gs[k] > 0)
+        return [(gs[k], rp[k], float(ms[k])) for k in range(n)], ch.value
 
     def set_timing(self, enable=True):
         _check(lib().pno_set_timing(self.h, 1 if enable else 0))

@@ -464,6 +464,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
                             DV& t2, DV& u2);
   build_program(P, s, Fd.data(), dBoo, dBov, dBvo, dBvv, t2, u2);
   bd.sync();
+  autotune(P, s);
   P->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
 }
 

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 #include <set>
+#include <utility>
 
 namespace pnoeom {
 namespace {
@@ -792,24 +793,77 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     };
     acc_sw(G.sp1, 0); acc_v(G.vp1, 1); acc_sw(G.sp2, 2); acc_v(G.vp2, 3);
   }
-  // split each sandwich list: all dims <= SMALL_DIM (single tile) go to the shared-memory kernel
-  auto split = [&](const std::vector<SProb>& Lst, std::vector<SProb>& small, std::vector<SProb>& gen, int* dims) {
+  // split each sandwich list: problems with every dim <= SMALL_DIM (single tile) go to the
+  // shared-memory kernel, bucketed by their largest dim
+  auto bucket_of = [](const SProb& q) {
+    int d = std::max(std::max(q.M, q.N), std::max(q.K1, q.K2));
+    return d <= 16 ? 0 : d <= 32 ? 1 : d <= SMALL_DIM ? 2 : -1;
+  };
+  // order by output block (heaviest blocks first); group boundaries for every candidate size
+  auto order_by_output = [&](std::vector<SProb>& Lst) {
+    auto key_less = [](const SProb& a, const SProb& b) {
+      if (a.c_buf != b.c_buf) return a.c_buf < b.c_buf;
+      if (a.c_off != b.c_off) return a.c_off < b.c_off;
+      if (a.tc != b.tc) return a.tc < b.tc;
+      if (a.M != b.M) return a.M < b.M;
+      return a.N < b.N;
+    };
+    auto same = [](const SProb& a, const SProb& b) {
+      return a.c_buf == b.c_buf && a.c_off == b.c_off && a.tc == b.tc && a.M == b.M && a.N == b.N;
+    };
+    std::stable_sort(Lst.begin(), Lst.end(), key_less);
+    std::vector<std::pair<double, std::pair<size_t, size_t>>> blocks;
+    for (size_t i = 0; i < Lst.size();) {
+      size_t j = i;
+      double work = 0;
+      while (j < Lst.size() && same(Lst[j], Lst[i])) {
+        work += (double)Lst[j].K1 * Lst[j].N * Lst[j].K2 + (double)Lst[j].M * Lst[j].N * Lst[j].K1;
+        ++j;
+      }
+      blocks.push_back({work, {i, j}});
+      i = j;
+    }
+    std::stable_sort(blocks.begin(), blocks.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::vector<SProb> out;
+    std::vector<std::pair<int, int>> ranges;
+    for (auto& b : blocks) {
+      ranges.push_back({(int)out.size(), (int)(out.size() + b.second.second - b.second.first)});
+      for (size_t k = b.second.first; k < b.second.second; ++k) out.push_back(Lst[k]);
+    }
+    Lst.swap(out);
+    return ranges;
+  };
+  auto make_sets = [&](const std::vector<SProb>& Lst, pnoeom_pno::SmallSet* sets, std::vector<SProb>& gen) {
+    std::vector<SProb> b[3];
     for (const SProb& q : Lst) {
-      if (q.M <= SMALL_DIM && q.N <= SMALL_DIM && q.K1 <= SMALL_DIM && q.K2 <= SMALL_DIM) {
-        small.push_back(q);
-        dims[0] = std::max(dims[0], q.M); dims[1] = std::max(dims[1], q.K1);
-        dims[2] = std::max(dims[2], q.K2); dims[3] = std::max(dims[3], q.N);
-      } else {
-        gen.push_back(q);
+      int k = bucket_of(q);
+      if (k < 0) gen.push_back(q); else b[k].push_back(q);
+    }
+    for (int k = 0; k < 3; ++k) {
+      auto& S = sets[k];
+      for (const SProb& q : b[k]) {
+        S.dims[0] = std::max(S.dims[0], q.M); S.dims[1] = std::max(S.dims[1], q.K1);
+        S.dims[2] = std::max(S.dims[2], q.K2); S.dims[3] = std::max(S.dims[3], q.N);
+      }
+      auto ranges = order_by_output(b[k]);
+      S.nprob = (int)b[k].size();
+      S.probs.alloc(std::max<size_t>(1, b[k].size()), fp);
+      S.probs.upload(b[k].data(), b[k].size(), s);
+      for (int c = 0; c < NGROUP_CAND; ++c) {
+        std::vector<int> st;
+        for (auto& r : ranges)
+          for (int x = r.first; x < r.second; x += GROUP_CAND[c]) st.push_back(x);
+        st.push_back(S.nprob);
+        S.ngroups[c] = (int)st.size() - 1;
+        S.starts[c].alloc(st.size(), fp);
+        S.starts[c].upload(st.data(), st.size(), s);
       }
     }
   };
-  std::vector<SProb> s1s, s1g, s2s, s2g;
-  split(G.sp1, s1s, s1g, P->small_dims1);
-  split(G.sp2, s2s, s2g, P->small_dims2);
-  P->n_sp1s = (int)s1s.size(); P->n_sp2s = (int)s2s.size();
-  P->sp_small1.alloc(std::max<size_t>(1, s1s.size()), fp); P->sp_small1.upload(s1s.data(), s1s.size(), s);
-  P->sp_small2.alloc(std::max<size_t>(1, s2s.size()), fp); P->sp_small2.upload(s2s.data(), s2s.size(), s);
+  std::vector<SProb> s1g, s2g;
+  make_sets(G.sp1, P->small1, s1g);
+  make_sets(G.sp2, P->small2, s2g);
+  P->group_choice = 0;
   G.sp1 = s1g; G.sp2 = s2g;
   P->n_sp1 = (int)G.sp1.size(); P->n_sp2 = (int)G.sp2.size();
   P->n_vp1 = (int)G.vp1.size(); P->n_vp2 = (int)G.vp2.size();

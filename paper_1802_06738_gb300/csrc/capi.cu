@@ -89,6 +89,19 @@ void pno_destroy(pnoeom_pno* pno) { delete pno; }
 
 double pno_build_seconds(const pnoeom_pno* pno) { return pno ? pno->build_seconds : 0.0; }
 
+int pno_autotune_info(const pnoeom_pno* pno, int ncand, int* group_sizes, int* roots_per_cta, double* ms, int* choice) {
+  return guard([&] {
+    PN_CHECK(pno, PNOEOM_ERR_INVALID_ARG, "pno is NULL");
+    const int total = pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND;
+    for (int c = 0; c < std::min(ncand, total); ++c) {
+      if (group_sizes) group_sizes[c] = pnoeom::GROUP_CAND[c / pnoeom::NRPC_CAND];
+      if (roots_per_cta) roots_per_cta[c] = pnoeom::RPC_CAND[c % pnoeom::NRPC_CAND];
+      if (ms) ms[c] = pno->tune_ms[c];
+    }
+    if (choice) *choice = pno->group_choice * pnoeom::NRPC_CAND + pno->rpc_choice;
+  });
+}
+
 int pno_set_timing(pnoeom_pno* pno, int enable) {
   return guard([&] {
     PN_CHECK(pno, PNOEOM_ERR_INVALID_ARG, "pno is NULL");

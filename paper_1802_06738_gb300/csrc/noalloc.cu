@@ -32,6 +32,8 @@ void* scratch_address(int device) {
   return g_scratch_addr[device];
 }
 
+using pnoeom::RPC_CAND;
+
 template <typename T>
 void sigma_into_scratch(const pnoeom_pno* P, int nvec, const T* r, T* out, T* work, cudaStream_t s) {
   using namespace pnoeom;
@@ -42,12 +44,10 @@ void sigma_into_scratch(const pnoeom_pno* P, int nvec, const T* r, T* out, T* wo
   b.rin = r; b.rin_stride = P->L;
   b.work = work; b.work_stride = P->work_len;
   b.sout = out; b.sout_stride = P->L;
-  const int* d1 = P->small_dims1;
-  const int* d2 = P->small_dims2;
-  run_sandwich_small<T>(P->sp_small1.get(), P->n_sp1s, nvec, b, d1[0], d1[1], d1[2], d1[3], s);
+  run_small_sets<T>(P, P->small1, nvec, b, s);
   run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
   run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s);
-  run_sandwich_small<T>(P->sp_small2.get(), P->n_sp2s, nvec, b, d2[0], d2[1], d2[2], d2[3], s);
+  run_small_sets<T>(P, P->small2, nvec, b, s);
   run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
   run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s);
 }

@@ -27,9 +27,21 @@ struct pnoeom_pno {
   pnoeom::DBuf<pnoeom::SProb> sp_phase1, sp_phase2;
   pnoeom::DBuf<pnoeom::VProb> vp_phase1, vp_phase2;
   int n_sp1 = 0, n_sp2 = 0, n_vp1 = 0, n_vp2 = 0;
-  pnoeom::DBuf<pnoeom::SProb> sp_small1, sp_small2;   // sandwich problems with all dims <= SMALL_DIM
-  int n_sp1s = 0, n_sp2s = 0;
-  int small_dims1[4] = {1, 1, 1, 1}, small_dims2[4] = {1, 1, 1, 1};   // max M, K1, K2, N
+  // small sandwich problems, bucketed by their largest dimension (<= 16, 32, 64) so that each
+  // bucket's launch sizes shared memory for its own blocks; within a bucket the problems are
+  // ordered by output block, with one group-boundary list per candidate group size
+  static constexpr int NGROUP_CAND = 4;
+  struct SmallSet {
+    pnoeom::DBuf<pnoeom::SProb> probs;
+    pnoeom::DBuf<int> starts[NGROUP_CAND];
+    int ngroups[NGROUP_CAND] = {0};
+    int dims[4] = {1, 1, 1, 1};   // max M, K1, K2, N
+    int nprob = 0;
+  };
+  SmallSet small1[3], small2[3];
+  int group_choice = 0;                              // index into GROUP_CAND, set by the autotuner
+  int rpc_choice = 0;                                // index into RPC_CAND
+  double tune_ms[NGROUP_CAND * 3] = {0};
   int prof_launches[4] = {0, 0, 0, 0};
   int smem_elems = 0;
   int64_t work_len = 0;                      // FvR (v*v) + FoR (o*o)
@@ -53,6 +65,22 @@ struct pnoeom_pno {
 };
 
 namespace pnoeom {
+constexpr int NGROUP_CAND = pnoeom_pno::NGROUP_CAND;
+constexpr int GROUP_CAND[NGROUP_CAND] = {1, 2, 4, 8};
+constexpr int NRPC_CAND = 3;
+constexpr int RPC_CAND[NRPC_CAND] = {1, 2, 8};
+void autotune(pnoeom_pno* P, cudaStream_t s);
+// launch the bucketed small-sandwich problems of one phase with the tuned choices
+template <typename T>
+inline void run_small_sets(const pnoeom_pno* P, const pnoeom_pno::SmallSet* sets, int nvec, const Buffers& b,
+                           cudaStream_t s) {
+  for (int k = 0; k < 3; ++k) {
+    const auto& S = sets[k];
+    if (!S.nprob) continue;
+    run_sandwich_small<T>(S.probs.get(), S.starts[P->group_choice].get(), S.ngroups[P->group_choice], nvec, b, S.dims[0],
+                          S.dims[1], S.dims[2], S.dims[3], RPC_CAND[P->rpc_choice], s);
+  }
+}
 void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts, cudaStream_t s,
                   pnoeom_pno* P);
 template <typename T>

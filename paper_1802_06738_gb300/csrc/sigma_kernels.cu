@@ -69,64 +69,89 @@ __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ prob
   }
 }
 
-// Small sandwich: one problem per CTA, all roots in the CTA.  A (M x K1) and
-// B (K2 x N) are staged once in shared memory; per root X is staged, T = X B
-// formed in shared memory, then C += alpha A T (atomic).
+// Small sandwich, grouped by output block: one group of problems sharing the
+// same C block per CTA, all roots in the CTA.  Per problem, A (M x K1) and B
+// (K2 x N) are staged once in shared memory; per root X is staged, T = X B is
+// formed, and alpha A T is accumulated into a shared-memory copy of the C
+// block of that root.  After the group, the accumulators are added to C
+// (atomic: several groups may share a C block).
 template <typename T>
-__global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict__ probs, Buffers bufs, int nroots,
-                                                        int dm, int dk1, int dk2, int dn) {
+__global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
+                                                        Buffers bufs, int nroots, int total_roots, int dm, int dk1,
+                                                        int dk2, int dn) {
   extern __shared__ unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);     // dm x dk1
   T* Bs = As + dm * dk1;                      // dk2 x dn
   T* Xs = Bs + dk2 * dn;                      // dk1 x dk2
   T* Ts = Xs + dk1 * dk2;                     // dk1 x dn
-  const SProb P = probs[blockIdx.x];
-  const int M = P.M, N = P.N, K1 = P.K1, K2 = P.K2;
-  const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
-  if (hasA) {
-    const T* A = cbuf<T>(bufs, P.a_buf, 0) + P.a_off;
-    for (int e = threadIdx.x; e < M * K1; e += blockDim.x) {
-      const int m = e / K1, k = e % K1;
-      As[m * dk1 + k] = P.ta ? A[(int64_t)k * P.lda + m] : A[(int64_t)m * P.lda + k];
-    }
-  }
-  if (hasB) {
-    const T* Bm = cbuf<T>(bufs, P.b_buf, 0) + P.b_off;
-    for (int e = threadIdx.x; e < K2 * N; e += blockDim.x) {
-      const int k = e / N, n = e % N;
-      Bs[k * dn + n] = P.tb ? Bm[(int64_t)n * P.ldb + k] : Bm[(int64_t)k * P.ldb + n];
-    }
-  }
-  const T alpha = (T)P.alpha;
-  for (int r = 0; r < nroots; ++r) {
-    const T* X = cbuf<T>(bufs, P.x_buf, r) + P.x_off;
+  T* Cs = Ts + dk1 * dn;                      // nroots x dm x dn accumulators
+  const int g0 = gstart[blockIdx.x], g1 = gstart[blockIdx.x + 1];
+  // this CTA's roots: [blockIdx.y * nroots, ...) of the launch (nroots = roots per CTA)
+  const int rbase = blockIdx.y * nroots;
+  nroots = min(nroots, total_roots - rbase);
+  if (nroots <= 0) return;
+  const SProb P0 = probs[g0];
+  const int M = P0.M, N = P0.N;
+  for (int e = threadIdx.x; e < nroots * M * N; e += blockDim.x) Cs[e] = T(0);
+  for (int g = g0; g < g1; ++g) {
+    const SProb P = probs[g];
+    const int K1 = P.K1, K2 = P.K2;
+    const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
     __syncthreads();
-    for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
-      const int a = e / K2, b = e % K2;
-      Xs[a * dk2 + b] = P.tx ? X[(int64_t)b * P.ldx + a] : X[(int64_t)a * P.ldx + b];
+    if (hasA) {
+      const T* A = cbuf<T>(bufs, P.a_buf, 0) + P.a_off;
+      for (int e = threadIdx.x; e < M * K1; e += blockDim.x) {
+        const int m = e / K1, k = e % K1;
+        As[m * dk1 + k] = P.ta ? A[(int64_t)k * P.lda + m] : A[(int64_t)m * P.lda + k];
+      }
     }
-    __syncthreads();
     if (hasB) {
-      for (int e = threadIdx.x; e < K1 * N; e += blockDim.x) {
-        const int a = e / N, n = e % N;
-        T acc = T(0);
-        for (int k = 0; k < K2; ++k) acc += Xs[a * dk2 + k] * Bs[k * dn + n];
-        Ts[a * dn + n] = acc;
+      const T* Bm = cbuf<T>(bufs, P.b_buf, 0) + P.b_off;
+      for (int e = threadIdx.x; e < K2 * N; e += blockDim.x) {
+        const int k = e / N, n = e % N;
+        Bs[k * dn + n] = P.tb ? Bm[(int64_t)n * P.ldb + k] : Bm[(int64_t)k * P.ldb + n];
+      }
+    }
+    const T alpha = (T)P.alpha;
+    for (int r = 0; r < nroots; ++r) {
+      const T* X = cbuf<T>(bufs, P.x_buf, rbase + r) + P.x_off;
+      __syncthreads();
+      for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
+        const int a = e / K2, b = e % K2;
+        Xs[a * dk2 + b] = P.tx ? X[(int64_t)b * P.ldx + a] : X[(int64_t)a * P.ldx + b];
       }
       __syncthreads();
+      if (hasB) {
+        for (int e = threadIdx.x; e < K1 * N; e += blockDim.x) {
+          const int a = e / N, n = e % N;
+          T acc = T(0);
+          for (int k = 0; k < K2; ++k) acc += Xs[a * dk2 + k] * Bs[k * dn + n];
+          Ts[a * dn + n] = acc;
+        }
+        __syncthreads();
+      }
+      T* Cr = Cs + (size_t)r * M * N;
+      for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
+        const int m = e / N, n = e % N;
+        T acc = T(0);
+        if (hasA) {
+          if (hasB) for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Ts[k * dn + n];
+          else for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Xs[k * dk2 + n];
+        } else {
+          acc = hasB ? Ts[m * dn + n] : Xs[m * dk2 + n];
+        }
+        Cr[e] += alpha * acc;
+      }
     }
-    T* C = mbuf<T>(bufs, P.c_buf, r) + P.c_off;
+  }
+  __syncthreads();
+  for (int r = 0; r < nroots; ++r) {
+    T* C = mbuf<T>(bufs, P0.c_buf, rbase + r) + P0.c_off;
+    const T* Cr = Cs + (size_t)r * M * N;
     for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
       const int m = e / N, n = e % N;
-      T acc = T(0);
-      if (hasA) {
-        if (hasB) for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Ts[k * dn + n];
-        else for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Xs[k * dk2 + n];
-      } else {
-        acc = hasB ? Ts[m * dn + n] : Xs[m * dk2 + n];
-      }
-      T* c = P.tc ? C + (int64_t)n * P.ldc + m : C + (int64_t)m * P.ldc + n;
-      atomicAdd(c, alpha * acc);
+      T* c = P0.tc ? C + (int64_t)n * P0.ldc + m : C + (int64_t)m * P0.ldc + n;
+      atomicAdd(c, Cr[e]);
     }
   }
 }
@@ -218,25 +243,41 @@ void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cud
 }
 
 template <typename T>
-void run_sandwich_small(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int dm, int dk1, int dk2, int dn,
-                        cudaStream_t s) {
-  if (nprob <= 0 || nroots <= 0) return;
-  const size_t smem = (size_t)(dm * dk1 + dk2 * dn + dk1 * dk2 + dk1 * dn) * sizeof(T);
+void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, int nroots, const Buffers& b,
+                        int dm, int dk1, int dk2, int dn, int roots_per_cta, cudaStream_t s) {
+  if (ngroups <= 0 || nroots <= 0) return;
+  const size_t base = (size_t)(dm * dk1 + dk2 * dn + dk1 * dk2 + dk1 * dn) * sizeof(T);
+  const size_t per_root = (size_t)dm * dn * sizeof(T);
+  const size_t limit = 200 * 1024;
+  PN_CHECK(base + per_root <= limit, PNOEOM_ERR_UNSUPPORTED, "PNO blocks too large for the grouped sandwich kernel");
+  int rpc = std::max(1, std::min(roots_per_cta, nroots));
+  rpc = (int)std::min<size_t>(rpc, (limit - base) / per_root);
+  const size_t smem = base + (size_t)rpc * per_root;
   static thread_local size_t configured[2] = {0, 0};
   size_t& conf = configured[sizeof(T) == 8];
   if (smem > 48 * 1024 && smem > conf) {
     PN_CUDA(cudaFuncSetAttribute(k_sandwich_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conf = smem;
   }
-  k_sandwich_small<T><<<nprob, 256, smem, s>>>(d_probs, b, nroots, dm, dk1, dk2, dn);
+  const int ychunks = (nroots + rpc - 1) / rpc;
+  for (int y0 = 0; y0 < ychunks; y0 += 65535) {
+    const int ny = std::min(65535, ychunks - y0);
+    Buffers br = b;   // shift the per-root buffers to this launch's first root
+    const int64_t r0 = (int64_t)y0 * rpc;
+    br.rin = (const T*)b.rin + r0 * b.rin_stride;
+    br.work = (T*)b.work + r0 * b.work_stride;
+    br.sout = (T*)b.sout + r0 * b.sout_stride;
+    k_sandwich_small<T><<<dim3(ngroups, ny), 256, smem, s>>>(d_probs, d_group_start, br, rpc, (int)(nroots - r0), dm, dk1,
+                                                             dk2, dn);
+  }
   PN_CUDA(cudaGetLastError());
 }
 
 template void run_sandwich<double>(const SProb*, int, int, const Buffers&, int, cudaStream_t);
 template void run_sandwich<float>(const SProb*, int, int, const Buffers&, int, cudaStream_t);
 template void run_gemv<double>(const VProb*, int, int, const Buffers&, cudaStream_t);
-template void run_sandwich_small<double>(const SProb*, int, int, const Buffers&, int, int, int, int, cudaStream_t);
-template void run_sandwich_small<float>(const SProb*, int, int, const Buffers&, int, int, int, int, cudaStream_t);
+template void run_sandwich_small<double>(const SProb*, const int*, int, int, const Buffers&, int, int, int, int, int, cudaStream_t);
+template void run_sandwich_small<float>(const SProb*, const int*, int, int, const Buffers&, int, int, int, int, int, cudaStream_t);
 template void run_gemv<float>(const VProb*, int, int, const Buffers&, cudaStream_t);
 
 }  // namespace pnoeom

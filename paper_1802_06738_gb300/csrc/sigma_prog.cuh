@@ -46,10 +46,13 @@ struct Buffers {
 
 template <typename T>
 void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int smem_elems, cudaStream_t s);
-// all dims <= SMALL_DIM, single tile: A and B staged once, every root in the same CTA
+// all dims <= SMALL_DIM, single tile: A and B staged once, every root in the same CTA.
+// Problems are grouped by output block: group g is probs[group_start[g] .. group_start[g+1]),
+// all with the same C block; the CTA accumulates the group for every root in shared
+// memory and adds it to C once.
 template <typename T>
-void run_sandwich_small(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int dm, int dk1, int dk2,
-                        int dn, cudaStream_t s);
+void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, int nroots, const Buffers& b,
+                        int dm, int dk1, int dk2, int dn, int roots_per_cta, cudaStream_t s);
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cudaStream_t s);
 

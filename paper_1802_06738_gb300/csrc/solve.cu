@@ -36,27 +36,58 @@ void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s) {
     PN_CUDA(cudaEventRecord(e1, s));
     P->events.push_back({cls, {e0, e1}});
   };
-  const int* d1 = P->small_dims1;
-  const int* d2 = P->small_dims2;
   timed(0, [&] {
-    run_sandwich_small<T>(P->sp_small1.get(), P->n_sp1s, nvec, b, d1[0], d1[1], d1[2], d1[3], s);
+    run_small_sets<T>(P, P->small1, nvec, b, s);
     run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
   });
   timed(1, [&] { run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s); });
   timed(2, [&] {
-    run_sandwich_small<T>(P->sp_small2.get(), P->n_sp2s, nvec, b, d2[0], d2[1], d2[2], d2[3], s);
+    run_small_sets<T>(P, P->small2, nvec, b, s);
     run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
   });
   timed(3, [&] { run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s); });
   if (P->timing) {   // kernel launches per class in this call
-    P->prof_launches[0] += (P->n_sp1s > 0) + (P->n_sp1 > 0);
+    auto nsets = [](const pnoeom_pno::SmallSet* S) { int n = 0; for (int k = 0; k < 3; ++k) n += S[k].nprob > 0; return n; };
+    P->prof_launches[0] += nsets(P->small1) + (P->n_sp1 > 0);
     P->prof_launches[1] += P->n_vp1 > 0;
-    P->prof_launches[2] += (P->n_sp2s > 0) + (P->n_sp2 > 0);
+    P->prof_launches[2] += nsets(P->small2) + (P->n_sp2 > 0);
     P->prof_launches[3] += P->n_vp2 > 0;
   }
 }
 template void apply_sigma<double>(pnoeom_pno*, int, const double*, double*, cudaStream_t);
 template void apply_sigma<float>(pnoeom_pno*, int, const float*, float*, cudaStream_t);
+
+// Autotuner: time the FP32 sigma of nroots_sa vectors for every candidate group size of the
+// grouped small-sandwich kernel and every roots-per-CTA choice (CUDA events on the build
+// stream) and keep the fastest pair.
+void autotune(pnoeom_pno* P, cudaStream_t s) {
+  const int nv = std::max(1, P->nroots_sa);
+  DBuf<float> r((size_t)nv * P->L), o((size_t)nv * P->L);
+  r.zero(s);
+  cudaEvent_t e0, e1;
+  PN_CUDA(cudaEventCreate(&e0));
+  PN_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  int pick = 0, pick_r = 0;
+  for (int c = 0; c < NGROUP_CAND; ++c)
+    for (int rr = 0; rr < NRPC_CAND; ++rr) {
+      P->group_choice = c;
+      P->rpc_choice = rr;
+      apply_sigma<float>(P, nv, r.get(), o.get(), s);   // warm-up
+      PN_CUDA(cudaEventRecord(e0, s));
+      for (int k = 0; k < 3; ++k) apply_sigma<float>(P, nv, r.get(), o.get(), s);
+      PN_CUDA(cudaEventRecord(e1, s));
+      PN_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      P->tune_ms[c * NRPC_CAND + rr] = ms / 3;
+      if (ms < best) { best = ms; pick = c; pick_r = rr; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->group_choice = pick;
+  P->rpc_choice = pick_r;
+}
 
 // ---------------------------------------------------------------------------
 // Small dense non-symmetric eigenproblem on the host: Householder reduction
