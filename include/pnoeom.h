@@ -156,6 +156,30 @@ int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* 
 int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, void* cuda_stream,
                    double* energies, double* res_norms, int* iters);
 
+/* Batches (many systems in one launch sequence).  A batch references n built
+ * systems (1 <= n <= 128, still owned by the caller, who must keep them alive
+ * and destroy the batch first).  pnoeom_batch_create merges their sigma
+ * programs: every pair block of every system is one problem of the same
+ * kernels, so each sigma of the batch is one launch sequence, replayed as a
+ * CUDA graph on non-default streams.  The merged program's tile choices are
+ * autotuned at creation. */
+typedef struct pnoeom_batch pnoeom_batch;
+int pnoeom_batch_create(pnoeom_ctx* ctx, pnoeom_pno* const* members, int n, void* cuda_stream, pnoeom_batch** out);
+void pnoeom_batch_destroy(pnoeom_batch* batch);
+
+/* sigma for every member at once: nvec[k] packed vectors of member k at
+ * r_dev[k] (member k's vec_len each) into s_dev[k]; nvec[k] = 0 skips member k.
+ * Precision and layouts as in sigma().  Asynchronous on cuda_stream. */
+int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, const void* const* r_dev,
+                       void* const* s_dev, int precision, void* cuda_stream);
+
+/* Davidson solves of all members in lockstep (each member its own subspace;
+ * every round evaluates all members' pending vectors in one sigma launch).
+ * Host outputs: energies and res_norms n x nroots_solve, iters and converged n.
+ * Returns PNOEOM_ERR_NOT_CONVERGED if any member did not converge. */
+int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* opts, void* cuda_stream,
+                       double* energies, double* res_norms, int* iters, int* converged);
+
 /* Eigenvectors of the last davidson_solve on this handle, as packed FP64
  * vectors on the host (nroots_solve * vec_len doubles). */
 int pno_get_eigenvectors(const pnoeom_pno* pno, double* X);

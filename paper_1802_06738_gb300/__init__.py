@@ -49,7 +49,8 @@ _lib = None
 EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", "pno_destroy",
            "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
            "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds",
-           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info"]
+           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info",
+           "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve"]
 
 
 def lib():
@@ -70,6 +71,10 @@ def lib():
         L.sigma.argtypes = [vp, vp, i, vp, vp, i, vp]
         L.sigma_noalloc.argtypes = [vp, vp, i, vp, vp, i, vp]
         L.pno_autotune_info.argtypes = [vp, i, ip, ip, dp, ip]
+        L.pnoeom_batch_create.argtypes = [vp, ctypes.POINTER(vp), i, vp, ctypes.POINTER(vp)]
+        L.pnoeom_batch_destroy.argtypes = [vp]; L.pnoeom_batch_destroy.restype = None
+        L.pnoeom_batch_sigma.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
+        L.pnoeom_batch_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip, ip]
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
         L.pno_get_cis.argtypes = [vp, dp]
@@ -257,3 +262,43 @@ class PNO:
         X = np.zeros((self.opts.nroots_solve, self.length))
         _check(lib().pno_get_eigenvectors(self.h, _dptr(X)))
         return X
+
+
+class Batch:
+    """pnoeom_batch_*: several built systems evaluated in one launch sequence."""
+
+    def __init__(self, ctx, pnos, stream=None):
+        self.ctx, self.pnos = ctx, list(pnos)
+        arr = (ctypes.c_void_p * len(self.pnos))(*[p.h.value for p in self.pnos])
+        h = ctypes.c_void_p()
+        _check(lib().pnoeom_batch_create(ctx.h, arr, len(self.pnos), _stream_ptr(stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pnoeom_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sigma(self, rs, outs, precision=FP64, stream=None):
+        """rs, outs: per member a CUDA tensor (nvec_k, length_k) or None."""
+        n = len(self.pnos)
+        nv = (ctypes.c_int * n)(*[0 if r is None else (r.shape[0] if r.dim() == 2 else 1) for r in rs])
+        rp = (ctypes.c_void_p * n)(*[0 if r is None else r.data_ptr() for r in rs])
+        op = (ctypes.c_void_p * n)(*[0 if o is None else o.data_ptr() for o in outs])
+        _check(lib().pnoeom_batch_sigma(self.ctx.h, self.h, nv, rp, op, precision, _stream_ptr(stream)))
+
+    def solve(self, opts, stream=None):
+        """(energies [n, nroots], residual norms, iterations [n], converged [n])."""
+        import numpy as np
+        n, nr = len(self.pnos), opts.nroots_solve
+        e, rn = np.zeros((n, nr)), np.zeros((n, nr))
+        it, cv = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        _check(lib().pnoeom_batch_solve(self.ctx.h, self.h, ctypes.byref(opts), _stream_ptr(stream), _dptr(e), _dptr(rn),
+                                        it, cv), allow=(ERR_NOT_CONVERGED,))
+        return e, rn, list(it), [bool(x) for x in cv]

@@ -833,49 +833,64 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     Lst.swap(out);
     return ranges;
   };
-  auto make_sets = [&](const std::vector<SProb>& Lst, pnoeom_pno::SmallSet* sets, std::vector<SProb>& gen) {
+  auto make_sets = [&](const std::vector<SProb>& Lst, SmallSet* sets, std::vector<SProb>& gen) {
     std::vector<SProb> b[3];
     for (const SProb& q : Lst) {
       int k = bucket_of(q);
       if (k < 0) gen.push_back(q); else b[k].push_back(q);
     }
     for (int k = 0; k < 3; ++k) {
-      auto& S = sets[k];
+      SmallSet& S = sets[k];
       for (const SProb& q : b[k]) {
         S.dims[0] = std::max(S.dims[0], q.M); S.dims[1] = std::max(S.dims[1], q.K1);
         S.dims[2] = std::max(S.dims[2], q.K2); S.dims[3] = std::max(S.dims[3], q.N);
       }
       auto ranges = order_by_output(b[k]);
       S.nprob = (int)b[k].size();
-      S.probs.alloc(std::max<size_t>(1, b[k].size()), fp);
-      S.probs.upload(b[k].data(), b[k].size(), s);
+      S.h_probs = b[k];
       for (int c = 0; c < NGROUP_CAND; ++c) {
-        std::vector<int> st;
+        std::vector<int>& st = S.h_starts[c];
+        st.clear();
         for (auto& r : ranges)
           for (int x = r.first; x < r.second; x += GROUP_CAND[c]) st.push_back(x);
         st.push_back(S.nprob);
         S.ngroups[c] = (int)st.size() - 1;
-        S.starts[c].alloc(st.size(), fp);
-        S.starts[c].upload(st.data(), st.size(), s);
       }
     }
   };
-  std::vector<SProb> s1g, s2g;
-  make_sets(G.sp1, P->small1, s1g);
-  make_sets(G.sp2, P->small2, s2g);
-  P->group_choice = 0;
-  G.sp1 = s1g; G.sp2 = s2g;
-  P->n_sp1 = (int)G.sp1.size(); P->n_sp2 = (int)G.sp2.size();
-  P->n_vp1 = (int)G.vp1.size(); P->n_vp2 = (int)G.vp2.size();
-  P->sp_phase1.alloc(std::max<size_t>(1, G.sp1.size()), fp); P->sp_phase1.upload(G.sp1.data(), G.sp1.size(), s);
-  P->sp_phase2.alloc(std::max<size_t>(1, G.sp2.size()), fp); P->sp_phase2.upload(G.sp2.data(), G.sp2.size(), s);
-  P->vp_phase1.alloc(std::max<size_t>(1, G.vp1.size()), fp); P->vp_phase1.upload(G.vp1.data(), G.vp1.size(), s);
-  P->vp_phase2.alloc(std::max<size_t>(1, G.vp2.size()), fp); P->vp_phase2.upload(G.vp2.data(), G.vp2.size(), s);
-  P->smem_elems = G.smem;
+  Program& PR = P->prog;
+  make_sets(G.sp1, PR.small1, PR.h_gen1);
+  make_sets(G.sp2, PR.small2, PR.h_gen2);
+  PR.h_v1 = G.vp1;
+  PR.h_v2 = G.vp2;
+  PR.smem_elems = G.smem;
+  PR.upload(s, fp);
   // FP32 copy of the pool for the mixed-precision sigma
   P->pool32.alloc(P->pool64.n, fp);
   d2f(P->pool32.get(), P->pool64.get(), P->pool64.n, s);
   G.sync();
+}
+
+void Program::upload(cudaStream_t s, size_t* fp) {
+  n_gen1 = (int)h_gen1.size(); n_gen2 = (int)h_gen2.size();
+  n_v1 = (int)h_v1.size(); n_v2 = (int)h_v2.size();
+  gen1.alloc(std::max<size_t>(1, h_gen1.size()), fp); gen1.upload(h_gen1.data(), h_gen1.size(), s);
+  gen2.alloc(std::max<size_t>(1, h_gen2.size()), fp); gen2.upload(h_gen2.data(), h_gen2.size(), s);
+  v1.alloc(std::max<size_t>(1, h_v1.size()), fp); v1.upload(h_v1.data(), h_v1.size(), s);
+  v2.alloc(std::max<size_t>(1, h_v2.size()), fp); v2.upload(h_v2.data(), h_v2.size(), s);
+  for (SmallSet* sets : {small1, small2})
+    for (int k = 0; k < 3; ++k) {
+      SmallSet& S = sets[k];
+      S.nprob = (int)S.h_probs.size();
+      S.probs.alloc(std::max<size_t>(1, S.h_probs.size()), fp);
+      S.probs.upload(S.h_probs.data(), S.h_probs.size(), s);
+      for (int c = 0; c < NGROUP_CAND; ++c) {
+        S.ngroups[c] = std::max(0, (int)S.h_starts[c].size() - 1);
+        S.starts[c].alloc(std::max<size_t>(1, S.h_starts[c].size()), fp);
+        S.starts[c].upload(S.h_starts[c].data(), S.h_starts[c].size(), s);
+      }
+    }
+  PN_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace pnoeom

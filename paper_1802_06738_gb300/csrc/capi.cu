@@ -98,7 +98,7 @@ int pno_autotune_info(const pnoeom_pno* pno, int ncand, int* group_sizes, int* r
       if (roots_per_cta) roots_per_cta[c] = pnoeom::RPC_CAND[c % pnoeom::NRPC_CAND];
       if (ms) ms[c] = pno->tune_ms[c];
     }
-    if (choice) *choice = pno->group_choice * pnoeom::NRPC_CAND + pno->rpc_choice;
+    if (choice) *choice = pno->prog.group_choice * pnoeom::NRPC_CAND + pno->prog.rpc_choice;
   });
 }
 
@@ -195,6 +195,52 @@ int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, vo
   });
   if (rc == PNOEOM_OK && !conv) {
     g_last_error = "Davidson did not converge within max_iter";
+    return PNOEOM_ERR_NOT_CONVERGED;
+  }
+  return rc;
+}
+
+int pnoeom_batch_create(pnoeom_ctx* ctx, pnoeom_pno* const* members, int n, void* cuda_stream, pnoeom_batch** out) {
+  return guard([&] {
+    PN_CHECK(ctx && members && out && n >= 1, PNOEOM_ERR_INVALID_ARG, "bad arguments");
+    for (int k = 0; k < n; ++k) PN_CHECK(members[k], PNOEOM_ERR_INVALID_ARG, "NULL member");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    auto* B = new pnoeom_batch();
+    B->device = ctx->device;
+    B->members.assign(members, members + n);
+    try {
+      pnoeom::batch_build(B, st(cuda_stream));
+    } catch (...) {
+      delete B;
+      throw;
+    }
+    *out = B;
+  });
+}
+
+void pnoeom_batch_destroy(pnoeom_batch* batch) { delete batch; }
+
+int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, const void* const* r_dev,
+                       void* const* s_dev, int precision, void* cuda_stream) {
+  return guard([&] {
+    PN_CHECK(ctx && batch && nvec && r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32, PNOEOM_ERR_INVALID_ARG, "unknown precision");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::batch_sigma(batch, nvec, r_dev, s_dev, precision, st(cuda_stream));
+  });
+}
+
+int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* opts, void* cuda_stream,
+                       double* energies, double* res_norms, int* iters, int* converged) {
+  int all = 1;
+  int rc = guard([&] {
+    PN_CHECK(ctx && batch && opts && energies && res_norms && iters && converged, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::batch_solve(batch, opts, st(cuda_stream), energies, res_norms, iters, converged);
+    for (size_t k = 0; k < batch->members.size(); ++k) all = all && converged[k];
+  });
+  if (rc == PNOEOM_OK && !all) {
+    g_last_error = "some batch members did not converge within max_iter";
     return PNOEOM_ERR_NOT_CONVERGED;
   }
   return rc;

@@ -32,24 +32,15 @@ void* scratch_address(int device) {
   return g_scratch_addr[device];
 }
 
-using pnoeom::RPC_CAND;
-
 template <typename T>
 void sigma_into_scratch(const pnoeom_pno* P, int nvec, const T* r, T* out, T* work, cudaStream_t s) {
   using namespace pnoeom;
-  PN_CUDA(cudaMemsetAsync(out, 0, (size_t)nvec * P->L * sizeof(T), s));
-  PN_CUDA(cudaMemsetAsync(work, 0, (size_t)nvec * P->work_len * sizeof(T), s));
-  Buffers b;
-  b.pool = sizeof(T) == 8 ? (const void*)P->pool64.get() : (const void*)P->pool32.get();
-  b.rin = r; b.rin_stride = P->L;
-  b.work = work; b.work_stride = P->work_len;
-  b.sout = out; b.sout_stride = P->L;
-  run_small_sets<T>(P, P->small1, nvec, b, s);
-  run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
-  run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s);
-  run_small_sets<T>(P, P->small2, nvec, b, s);
-  run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
-  run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s);
+  SysTable t;
+  t.nsys = 1;
+  t.max_nvec = nvec;
+  t.s[0] = sysbuf(P, nvec, r, out, work, sizeof(T) == 4);
+  const int64_t ol = P->L, wl = P->work_len;
+  run_program<T>(P->prog, t, &ol, &wl, s, nullptr);
 }
 
 }  // namespace

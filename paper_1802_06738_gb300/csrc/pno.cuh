@@ -4,6 +4,39 @@
 #include "engine.cuh"
 #include "sigma_prog.cuh"
 
+namespace pnoeom {
+constexpr int NGROUP_CAND = 4;
+constexpr int GROUP_CAND[NGROUP_CAND] = {1, 2, 4, 8};
+constexpr int NRPC_CAND = 3;
+constexpr int RPC_CAND[NRPC_CAND] = {1, 2, 8};
+
+// Small sandwich problems of one size bucket: ordered by output block, with one
+// group-boundary list per candidate group size.
+struct SmallSet {
+  DBuf<SProb> probs;
+  DBuf<int> starts[NGROUP_CAND];
+  int ngroups[NGROUP_CAND] = {0};
+  int dims[4] = {1, 1, 1, 1};   // max M, K1, K2, N
+  int nprob = 0;
+  std::vector<SProb> h_probs;                      // host copies (batch merging)
+  std::vector<int> h_starts[NGROUP_CAND];
+};
+
+// A launchable sigma program: the problem lists of one system, or of a batch
+// of systems (problems carry their system index).
+struct Program {
+  DBuf<SProb> gen1, gen2;          // generic sandwich problems (phase 1: intermediates, phase 2: sigma)
+  DBuf<VProb> v1, v2;              // dense GEMV tiles
+  int n_gen1 = 0, n_gen2 = 0, n_v1 = 0, n_v2 = 0;
+  SmallSet small1[3], small2[3];   // small sandwich problems per size bucket
+  int smem_elems = 1;
+  int group_choice = 0, rpc_choice = 0;
+  std::vector<SProb> h_gen1, h_gen2;
+  std::vector<VProb> h_v1, h_v2;
+  void upload(cudaStream_t s, size_t* fp);
+};
+}  // namespace pnoeom
+
 struct pnoeom_pno {
   ~pnoeom_pno() {
     for (auto& e : events) { cudaEventDestroy(e.second.first); cudaEventDestroy(e.second.second); }
@@ -24,24 +57,8 @@ struct pnoeom_pno {
   // sigma program
   pnoeom::DBuf<double> pool64;
   pnoeom::DBuf<float> pool32;
-  pnoeom::DBuf<pnoeom::SProb> sp_phase1, sp_phase2;
-  pnoeom::DBuf<pnoeom::VProb> vp_phase1, vp_phase2;
-  int n_sp1 = 0, n_sp2 = 0, n_vp1 = 0, n_vp2 = 0;
-  // small sandwich problems, bucketed by their largest dimension (<= 16, 32, 64) so that each
-  // bucket's launch sizes shared memory for its own blocks; within a bucket the problems are
-  // ordered by output block, with one group-boundary list per candidate group size
-  static constexpr int NGROUP_CAND = 4;
-  struct SmallSet {
-    pnoeom::DBuf<pnoeom::SProb> probs;
-    pnoeom::DBuf<int> starts[NGROUP_CAND];
-    int ngroups[NGROUP_CAND] = {0};
-    int dims[4] = {1, 1, 1, 1};   // max M, K1, K2, N
-    int nprob = 0;
-  };
-  SmallSet small1[3], small2[3];
-  int group_choice = 0;                              // index into GROUP_CAND, set by the autotuner
-  int rpc_choice = 0;                                // index into RPC_CAND
-  double tune_ms[NGROUP_CAND * 3] = {0};
+  pnoeom::Program prog;
+  double tune_ms[pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND] = {0};
   int prof_launches[4] = {0, 0, 0, 0};
   int smem_elems = 0;
   int64_t work_len = 0;                      // FvR (v*v) + FoR (o*o)
@@ -64,23 +81,36 @@ struct pnoeom_pno {
   double build_seconds = 0;
 };
 
+// A batch of built systems evaluated together: one merged sigma program whose
+// problems carry their member index (a11 of the hot path: all pairs of all
+// systems in one launch sequence, replayed as a CUDA graph).
+struct pnoeom_batch {
+  int device = 0;
+  std::vector<pnoeom_pno*> members;
+  pnoeom::Program prog;
+  std::vector<pnoeom::DBuf<double>> w64;
+  std::vector<pnoeom::DBuf<float>> w32;
+  cudaGraphExec_t exec = nullptr;
+  bool use_graph = true;
+  int graph_launches = 0, graph_updates = 0, graph_instantiations = 0;
+  double tune_ms[pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND] = {0};
+  size_t footprint = 0;
+  ~pnoeom_batch() { if (exec) cudaGraphExecDestroy(exec); }
+};
+
 namespace pnoeom {
-constexpr int NGROUP_CAND = pnoeom_pno::NGROUP_CAND;
-constexpr int GROUP_CAND[NGROUP_CAND] = {1, 2, 4, 8};
-constexpr int NRPC_CAND = 3;
-constexpr int RPC_CAND[NRPC_CAND] = {1, 2, 8};
 void autotune(pnoeom_pno* P, cudaStream_t s);
-// launch the bucketed small-sandwich problems of one phase with the tuned choices
+void batch_build(pnoeom_batch* B, cudaStream_t s);
+void batch_sigma(pnoeom_batch* B, const int* nvec, const void* const* r, void* const* out, int prec, cudaStream_t s);
+void batch_solve(pnoeom_batch* B, const pnoeom_opts* opts, cudaStream_t s, double* energies, double* res_norms,
+                 int* iters, int* converged);
+// per-system launch entry of a sigma call
+SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32);
+// zero the outputs and work of every system in the table, then launch the program
+// (timing hook: if rec != nullptr, rec(cls, launch) wraps each kernel class)
 template <typename T>
-inline void run_small_sets(const pnoeom_pno* P, const pnoeom_pno::SmallSet* sets, int nvec, const Buffers& b,
-                           cudaStream_t s) {
-  for (int k = 0; k < 3; ++k) {
-    const auto& S = sets[k];
-    if (!S.nprob) continue;
-    run_sandwich_small<T>(S.probs.get(), S.starts[P->group_choice].get(), S.ngroups[P->group_choice], nvec, b, S.dims[0],
-                          S.dims[1], S.dims[2], S.dims[3], RPC_CAND[P->rpc_choice], s);
-  }
-}
+void run_program(const Program& prog, const SysTable& t, const int64_t* out_len, const int64_t* work_len,
+                 cudaStream_t s, pnoeom_pno* timing_owner = nullptr);
 void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts, cudaStream_t s,
                   pnoeom_pno* P);
 template <typename T>

@@ -5,7 +5,8 @@ namespace pnoeom {
 namespace {
 
 template <typename T>
-__device__ __forceinline__ const T* cbuf(const Buffers& b, int id, int r) {
+__device__ __forceinline__ const T* cbuf(const SysTable& t, int sys, int id, int r) {
+  const SysBuf& b = t.s[sys];
   switch (id) {
     case B_POOL: return (const T*)b.pool;
     case B_RIN: return (const T*)b.rin + (int64_t)r * b.rin_stride;
@@ -14,7 +15,8 @@ __device__ __forceinline__ const T* cbuf(const Buffers& b, int id, int r) {
   }
 }
 template <typename T>
-__device__ __forceinline__ T* mbuf(const Buffers& b, int id, int r) {
+__device__ __forceinline__ T* mbuf(const SysTable& t, int sys, int id, int r) {
+  const SysBuf& b = t.s[sys];
   return id == B_WORK ? (T*)b.work + (int64_t)r * b.work_stride : (T*)b.sout + (int64_t)r * b.sout_stride;
 }
 
@@ -23,15 +25,16 @@ __device__ __forceinline__ T* mbuf(const Buffers& b, int id, int r) {
 // opA(A)[tile rows] * T_s.  Accumulation into C is atomic because many
 // problems share an output block.
 template <typename T>
-__global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ probs, Buffers bufs) {
+__global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
   extern __shared__ unsigned char smem_raw[];
   T* Ts = reinterpret_cast<T*>(smem_raw);
   const SProb P = probs[blockIdx.x];
   const int r = blockIdx.y;
-  const T* X = cbuf<T>(bufs, P.x_buf, r) + P.x_off;
-  const T* A = P.a_buf == B_NONE ? nullptr : cbuf<T>(bufs, P.a_buf, r) + P.a_off;
-  const T* Bm = P.b_buf == B_NONE ? nullptr : cbuf<T>(bufs, P.b_buf, r) + P.b_off;
-  T* C = mbuf<T>(bufs, P.c_buf, r) + P.c_off;
+  if (r >= tab.s[P.sys].nvec) return;
+  const T* X = cbuf<T>(tab, P.sys, P.x_buf, r) + P.x_off;
+  const T* A = P.a_buf == B_NONE ? nullptr : cbuf<T>(tab, P.sys, P.a_buf, r) + P.a_off;
+  const T* Bm = P.b_buf == B_NONE ? nullptr : cbuf<T>(tab, P.sys, P.b_buf, r) + P.b_off;
+  T* C = mbuf<T>(tab, P.sys, P.c_buf, r) + P.c_off;
   const int Mt = min(64, P.M - P.m0), Nt = min(64, P.N - P.n0);
   // rows of T_s: K1 if A is present, else the tile's rows of X (K1 == M)
   const int trow0 = A ? 0 : P.m0;
@@ -77,8 +80,8 @@ __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ prob
 // (atomic: several groups may share a C block).
 template <typename T>
 __global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
-                                                        Buffers bufs, int nroots, int total_roots, int dm, int dk1,
-                                                        int dk2, int dn) {
+                                                        const __grid_constant__ SysTable tab, int nroots, int dm,
+                                                        int dk1, int dk2, int dn) {
   extern __shared__ unsigned char smem_raw[];
   T* As = reinterpret_cast<T*>(smem_raw);     // dm x dk1
   T* Bs = As + dm * dk1;                      // dk2 x dn
@@ -86,11 +89,11 @@ __global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict_
   T* Ts = Xs + dk1 * dk2;                     // dk1 x dn
   T* Cs = Ts + dk1 * dn;                      // nroots x dm x dn accumulators
   const int g0 = gstart[blockIdx.x], g1 = gstart[blockIdx.x + 1];
-  // this CTA's roots: [blockIdx.y * nroots, ...) of the launch (nroots = roots per CTA)
-  const int rbase = blockIdx.y * nroots;
-  nroots = min(nroots, total_roots - rbase);
-  if (nroots <= 0) return;
   const SProb P0 = probs[g0];
+  // this CTA's roots: [blockIdx.y * nroots, ...) (nroots = roots per CTA), within the system's vectors
+  const int rbase = blockIdx.y * nroots;
+  nroots = min(nroots, tab.s[P0.sys].nvec - rbase);
+  if (nroots <= 0) return;
   const int M = P0.M, N = P0.N;
   for (int e = threadIdx.x; e < nroots * M * N; e += blockDim.x) Cs[e] = T(0);
   for (int g = g0; g < g1; ++g) {
@@ -99,14 +102,14 @@ __global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict_
     const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
     __syncthreads();
     if (hasA) {
-      const T* A = cbuf<T>(bufs, P.a_buf, 0) + P.a_off;
+      const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
       for (int e = threadIdx.x; e < M * K1; e += blockDim.x) {
         const int m = e / K1, k = e % K1;
         As[m * dk1 + k] = P.ta ? A[(int64_t)k * P.lda + m] : A[(int64_t)m * P.lda + k];
       }
     }
     if (hasB) {
-      const T* Bm = cbuf<T>(bufs, P.b_buf, 0) + P.b_off;
+      const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, 0) + P.b_off;
       for (int e = threadIdx.x; e < K2 * N; e += blockDim.x) {
         const int k = e / N, n = e % N;
         Bs[k * dn + n] = P.tb ? Bm[(int64_t)n * P.ldb + k] : Bm[(int64_t)k * P.ldb + n];
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict_
     }
     const T alpha = (T)P.alpha;
     for (int r = 0; r < nroots; ++r) {
-      const T* X = cbuf<T>(bufs, P.x_buf, rbase + r) + P.x_off;
+      const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
       __syncthreads();
       for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
         const int a = e / K2, b = e % K2;
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict_
   }
   __syncthreads();
   for (int r = 0; r < nroots; ++r) {
-    T* C = mbuf<T>(bufs, P0.c_buf, rbase + r) + P0.c_off;
+    T* C = mbuf<T>(tab, P0.sys, P0.c_buf, rbase + r) + P0.c_off;
     const T* Cr = Cs + (size_t)r * M * N;
     for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
       const int m = e / N, n = e % N;
@@ -163,11 +166,12 @@ constexpr int VR = 8;   // roots per pass inside a GEMV CTA
 // memory; each warp owns 8 rows and its lanes stride K, so the block rows are
 // read from HBM once, coalesced, for all roots.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, Buffers bufs, int nroots) {
+__global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
   extern __shared__ unsigned char smem_raw[];
   T* xs = reinterpret_cast<T*>(smem_raw);   // VR x GEMV_KC
   const VProb P = probs[blockIdx.x];
-  const T* A = (const T*)bufs.pool + P.a_off;
+  const int nroots = tab.s[P.sys].nvec;
+  const T* A = (const T*)tab.s[P.sys].pool + P.a_off;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const T alpha = (T)P.alpha;
   const int kl = P.klen;
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, B
       const int q = e / kl, kk = e % kl;
       int xk = P.k0 + kk;
       if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
-      xs[q * GEMV_KC + kk] = cbuf<T>(bufs, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
+      xs[q * GEMV_KC + kk] = cbuf<T>(tab, P.sys, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
     }
     __syncthreads();
     for (int ml = warp; ml < 64; ml += 8) {
@@ -203,7 +207,7 @@ __global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, B
         int cm = m;
         if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
         for (int q = 0; q < nr; ++q)
-          atomicAdd(mbuf<T>(bufs, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[q]);
+          atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[q]);
       }
     }
   }
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, B
 }  // namespace
 
 template <typename T>
-void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int smem_elems, cudaStream_t s) {
-  if (nprob <= 0 || nroots <= 0) return;
+void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_elems, cudaStream_t s) {
+  if (nprob <= 0 || t.max_nvec <= 0) return;
   size_t smem = (size_t)smem_elems * sizeof(T);
   static thread_local size_t configured[2] = {0, 0};
   size_t& conf = configured[sizeof(T) == 8];
@@ -221,36 +225,32 @@ void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b,
     PN_CUDA(cudaFuncSetAttribute(k_sandwich<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conf = smem;
   }
-  for (int p0 = 0; p0 < nprob; p0 += 65535 * 16) {
-    int n = std::min(nprob - p0, 65535 * 16);
-    dim3 grid(n, nroots);
-    k_sandwich<T><<<grid, 256, smem, s>>>(d_probs + p0, b);
-  }
+  k_sandwich<T><<<dim3(nprob, t.max_nvec), 256, smem, s>>>(d_probs, t);
   PN_CUDA(cudaGetLastError());
 }
 
 template <typename T>
-void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cudaStream_t s) {
-  if (nprob <= 0 || nroots <= 0) return;
+void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s) {
+  if (nprob <= 0 || t.max_nvec <= 0) return;
   const size_t smem = (size_t)VR * GEMV_KC * sizeof(T);
   static thread_local bool configured[2] = {false, false};
   if (!configured[sizeof(T) == 8]) {
     PN_CUDA(cudaFuncSetAttribute(k_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured[sizeof(T) == 8] = true;
   }
-  k_gemv<T><<<nprob, 256, smem, s>>>(d_probs, b, nroots);
+  k_gemv<T><<<nprob, 256, smem, s>>>(d_probs, t);
   PN_CUDA(cudaGetLastError());
 }
 
 template <typename T>
-void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, int nroots, const Buffers& b,
-                        int dm, int dk1, int dk2, int dn, int roots_per_cta, cudaStream_t s) {
-  if (ngroups <= 0 || nroots <= 0) return;
+void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
+                        int dk2, int dn, int roots_per_cta, cudaStream_t s) {
+  if (ngroups <= 0 || t.max_nvec <= 0) return;
   const size_t base = (size_t)(dm * dk1 + dk2 * dn + dk1 * dk2 + dk1 * dn) * sizeof(T);
   const size_t per_root = (size_t)dm * dn * sizeof(T);
   const size_t limit = 200 * 1024;
   PN_CHECK(base + per_root <= limit, PNOEOM_ERR_UNSUPPORTED, "PNO blocks too large for the grouped sandwich kernel");
-  int rpc = std::max(1, std::min(roots_per_cta, nroots));
+  int rpc = std::max(1, std::min(roots_per_cta, t.max_nvec));
   rpc = (int)std::min<size_t>(rpc, (limit - base) / per_root);
   const size_t smem = base + (size_t)rpc * per_root;
   static thread_local size_t configured[2] = {0, 0};
@@ -259,25 +259,16 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
     PN_CUDA(cudaFuncSetAttribute(k_sandwich_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     conf = smem;
   }
-  const int ychunks = (nroots + rpc - 1) / rpc;
-  for (int y0 = 0; y0 < ychunks; y0 += 65535) {
-    const int ny = std::min(65535, ychunks - y0);
-    Buffers br = b;   // shift the per-root buffers to this launch's first root
-    const int64_t r0 = (int64_t)y0 * rpc;
-    br.rin = (const T*)b.rin + r0 * b.rin_stride;
-    br.work = (T*)b.work + r0 * b.work_stride;
-    br.sout = (T*)b.sout + r0 * b.sout_stride;
-    k_sandwich_small<T><<<dim3(ngroups, ny), 256, smem, s>>>(d_probs, d_group_start, br, rpc, (int)(nroots - r0), dm, dk1,
-                                                             dk2, dn);
-  }
+  const int ychunks = (t.max_nvec + rpc - 1) / rpc;
+  k_sandwich_small<T><<<dim3(ngroups, ychunks), 256, smem, s>>>(d_probs, d_group_start, t, rpc, dm, dk1, dk2, dn);
   PN_CUDA(cudaGetLastError());
 }
 
-template void run_sandwich<double>(const SProb*, int, int, const Buffers&, int, cudaStream_t);
-template void run_sandwich<float>(const SProb*, int, int, const Buffers&, int, cudaStream_t);
-template void run_gemv<double>(const VProb*, int, int, const Buffers&, cudaStream_t);
-template void run_sandwich_small<double>(const SProb*, const int*, int, int, const Buffers&, int, int, int, int, int, cudaStream_t);
-template void run_sandwich_small<float>(const SProb*, const int*, int, int, const Buffers&, int, int, int, int, int, cudaStream_t);
-template void run_gemv<float>(const VProb*, int, int, const Buffers&, cudaStream_t);
+template void run_sandwich<double>(const SProb*, int, const SysTable&, int, cudaStream_t);
+template void run_sandwich<float>(const SProb*, int, const SysTable&, int, cudaStream_t);
+template void run_gemv<double>(const VProb*, int, const SysTable&, cudaStream_t);
+template void run_gemv<float>(const VProb*, int, const SysTable&, cudaStream_t);
+template void run_sandwich_small<double>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, cudaStream_t);
+template void run_sandwich_small<float>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, cudaStream_t);
 
 }  // namespace pnoeom

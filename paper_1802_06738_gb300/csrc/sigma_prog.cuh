@@ -14,6 +14,7 @@ enum BufId : int { B_POOL = 0, B_RIN = 1, B_WORK = 2, B_SOUT = 3, B_NONE = 4 };
 
 struct SProb {
   int64_t a_off, x_off, b_off, c_off;
+  int sys;                            // system index into the SysTable of the launch
   int a_buf, x_buf, b_buf, c_buf;     // a_buf/b_buf == B_NONE: identity
   int M, K1, K2, N;                   // A: M x K1, X: K1 x K2, B: K2 x N, C: M x N
   int lda, ldx, ldb, ldc;
@@ -24,6 +25,7 @@ struct SProb {
 
 struct VProb {
   int64_t a_off, x_off, c_off;
+  int sys;                            // system index into the SysTable of the launch
   int x_buf, c_buf;
   int M, K;                           // A: M x K row-major (lda)
   int lda;
@@ -37,23 +39,35 @@ struct VProb {
 constexpr int GEMV_KC = 1024;         // K chunk staged in shared memory per GEMV tile
 constexpr int SMALL_DIM = 64;         // sandwich problems with all dims <= this use the shared-memory kernel
 
-struct Buffers {
+// Per-system buffers of one launch.  nvec = number of vectors of that system
+// in this call (0: the system takes no part).
+struct SysBuf {
   const void* pool;
   const void* rin; int64_t rin_stride;
   void* work; int64_t work_stride;
   void* sout; int64_t sout_stride;
+  int nvec;
+  int pad;
+};
+constexpr int MAX_SYS = 128;
+// Passed to the kernels by value (__grid_constant__), so no device copy of the
+// table is needed and batches of up to MAX_SYS systems share one launch.
+struct SysTable {
+  int nsys;
+  int max_nvec;
+  SysBuf s[MAX_SYS];
 };
 
 template <typename T>
-void run_sandwich(const SProb* d_probs, int nprob, int nroots, const Buffers& b, int smem_elems, cudaStream_t s);
+void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_elems, cudaStream_t s);
 // all dims <= SMALL_DIM, single tile: A and B staged once, every root in the same CTA.
 // Problems are grouped by output block: group g is probs[group_start[g] .. group_start[g+1]),
 // all with the same C block; the CTA accumulates the group for every root in shared
 // memory and adds it to C once.
 template <typename T>
-void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, int nroots, const Buffers& b,
-                        int dm, int dk1, int dk2, int dn, int roots_per_cta, cudaStream_t s);
+void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
+                        int dk2, int dn, int roots_per_cta, cudaStream_t s);
 template <typename T>
-void run_gemv(const VProb* d_probs, int nprob, int nroots, const Buffers& b, cudaStream_t s);
+void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
 
 }  // namespace pnoeom

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <memory>
 
 namespace pnoeom {
 
@@ -13,21 +14,28 @@ static DBuf<T>& work_of(pnoeom_pno* P);
 template <> DBuf<double>& work_of<double>(pnoeom_pno* P) { return P->work64; }
 template <> DBuf<float>& work_of<float>(pnoeom_pno* P) { return P->work32; }
 
-template <typename T>
-void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s) {
-  if (nvec <= 0) return;
-  DBuf<T>& work = work_of<T>(P);
-  const size_t need = (size_t)nvec * P->work_len;
-  if (work.n < need) work.alloc(need, &P->footprint);
-  PN_CUDA(cudaMemsetAsync(out, 0, (size_t)nvec * P->L * sizeof(T), s));
-  work.zero(s);
-  Buffers b;
-  b.pool = sizeof(T) == 8 ? (const void*)P->pool64.get() : (const void*)P->pool32.get();
+SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32) {
+  SysBuf b{};
+  b.pool = fp32 ? (const void*)P->pool32.get() : (const void*)P->pool64.get();
   b.rin = r; b.rin_stride = P->L;
-  b.work = work.get(); b.work_stride = P->work_len;
+  b.work = work; b.work_stride = P->work_len;
   b.sout = out; b.sout_stride = P->L;
+  b.nvec = nvec;
+  return b;
+}
+
+template <typename T>
+void run_program(const Program& prog, const SysTable& t, const int64_t* out_len, const int64_t* work_len,
+                 cudaStream_t s, pnoeom_pno* timing_owner) {
+  for (int k = 0; k < t.nsys; ++k) {
+    const SysBuf& b = t.s[k];
+    if (b.nvec <= 0) continue;
+    PN_CUDA(cudaMemsetAsync(b.sout, 0, (size_t)b.nvec * out_len[k] * sizeof(T), s));
+    PN_CUDA(cudaMemsetAsync(b.work, 0, (size_t)b.nvec * work_len[k] * sizeof(T), s));
+  }
+  pnoeom_pno* P = timing_owner && timing_owner->timing ? timing_owner : nullptr;
   auto timed = [&](int cls, auto&& launch) {
-    if (!P->timing) { launch(); return; }
+    if (!P) { launch(); return; }
     cudaEvent_t e0, e1;
     PN_CUDA(cudaEventCreate(&e0));
     PN_CUDA(cudaEventCreate(&e1));
@@ -36,23 +44,51 @@ void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s) {
     PN_CUDA(cudaEventRecord(e1, s));
     P->events.push_back({cls, {e0, e1}});
   };
+  const int g = prog.group_choice, rpc = RPC_CAND[prog.rpc_choice];
+  auto small = [&](const SmallSet* sets) {
+    int n = 0;
+    for (int k = 0; k < 3; ++k) {
+      const SmallSet& S = sets[k];
+      if (!S.nprob) continue;
+      run_sandwich_small<T>(S.probs.get(), S.starts[g].get(), S.ngroups[g], t, S.dims[0], S.dims[1], S.dims[2], S.dims[3],
+                            rpc, s);
+      ++n;
+    }
+    return n;
+  };
+  int n0 = 0, n2 = 0;
   timed(0, [&] {
-    run_small_sets<T>(P, P->small1, nvec, b, s);
-    run_sandwich<T>(P->sp_phase1.get(), P->n_sp1, nvec, b, P->smem_elems, s);
+    n0 = small(prog.small1);
+    run_sandwich<T>(prog.gen1.get(), prog.n_gen1, t, prog.smem_elems, s);
   });
-  timed(1, [&] { run_gemv<T>(P->vp_phase1.get(), P->n_vp1, nvec, b, s); });
+  timed(1, [&] { run_gemv<T>(prog.v1.get(), prog.n_v1, t, s); });
   timed(2, [&] {
-    run_small_sets<T>(P, P->small2, nvec, b, s);
-    run_sandwich<T>(P->sp_phase2.get(), P->n_sp2, nvec, b, P->smem_elems, s);
+    n2 = small(prog.small2);
+    run_sandwich<T>(prog.gen2.get(), prog.n_gen2, t, prog.smem_elems, s);
   });
-  timed(3, [&] { run_gemv<T>(P->vp_phase2.get(), P->n_vp2, nvec, b, s); });
-  if (P->timing) {   // kernel launches per class in this call
-    auto nsets = [](const pnoeom_pno::SmallSet* S) { int n = 0; for (int k = 0; k < 3; ++k) n += S[k].nprob > 0; return n; };
-    P->prof_launches[0] += nsets(P->small1) + (P->n_sp1 > 0);
-    P->prof_launches[1] += P->n_vp1 > 0;
-    P->prof_launches[2] += nsets(P->small2) + (P->n_sp2 > 0);
-    P->prof_launches[3] += P->n_vp2 > 0;
+  timed(3, [&] { run_gemv<T>(prog.v2.get(), prog.n_v2, t, s); });
+  if (P) {   // kernel launches per class in this call
+    P->prof_launches[0] += n0 + (prog.n_gen1 > 0);
+    P->prof_launches[1] += prog.n_v1 > 0;
+    P->prof_launches[2] += n2 + (prog.n_gen2 > 0);
+    P->prof_launches[3] += prog.n_v2 > 0;
   }
+}
+template void run_program<double>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*);
+template void run_program<float>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*);
+
+template <typename T>
+void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s) {
+  if (nvec <= 0) return;
+  DBuf<T>& work = work_of<T>(P);
+  const size_t need = (size_t)nvec * P->work_len;
+  if (work.n < need) work.alloc(need, &P->footprint);
+  SysTable t;
+  t.nsys = 1;
+  t.max_nvec = nvec;
+  t.s[0] = sysbuf(P, nvec, r, out, work.get(), sizeof(T) == 4);
+  const int64_t ol = P->L, wl = P->work_len;
+  run_program<T>(P->prog, t, &ol, &wl, s, P);
 }
 template void apply_sigma<double>(pnoeom_pno*, int, const double*, double*, cudaStream_t);
 template void apply_sigma<float>(pnoeom_pno*, int, const float*, float*, cudaStream_t);
@@ -71,8 +107,8 @@ void autotune(pnoeom_pno* P, cudaStream_t s) {
   int pick = 0, pick_r = 0;
   for (int c = 0; c < NGROUP_CAND; ++c)
     for (int rr = 0; rr < NRPC_CAND; ++rr) {
-      P->group_choice = c;
-      P->rpc_choice = rr;
+      P->prog.group_choice = c;
+      P->prog.rpc_choice = rr;
       apply_sigma<float>(P, nv, r.get(), o.get(), s);   // warm-up
       PN_CUDA(cudaEventRecord(e0, s));
       for (int k = 0; k < 3; ++k) apply_sigma<float>(P, nv, r.get(), o.get(), s);
@@ -85,8 +121,8 @@ void autotune(pnoeom_pno* P, cudaStream_t s) {
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  P->group_choice = pick;
-  P->rpc_choice = pick_r;
+  P->prog.group_choice = pick;
+  P->prog.rpc_choice = pick_r;
 }
 
 // ---------------------------------------------------------------------------
@@ -331,45 +367,61 @@ struct Dav {
 };
 }  // namespace
 
-void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaStream_t s, double* energies,
-                  double* res_norms, int* iters, int* converged) {
-  (void)ctx;
-  const int nroots = opts->nroots_solve;
-  PN_CHECK(nroots >= 1 && nroots <= P->nroots_sa, PNOEOM_ERR_INVALID_ARG, "nroots_solve must be in [1, nroots_sa]");
-  const int64_t L = P->L;
-  PN_CHECK(L >= nroots, PNOEOM_ERR_INVALID_ARG, "PNO space smaller than the number of roots");
-  const int maxsub = std::max(opts->max_subspace > 0 ? opts->max_subspace : 8 * nroots, 2 * nroots + 1);
-  const int max_iter = opts->max_iter > 0 ? opts->max_iter : 100;
-  const double res_tol = opts->res_tol > 0 ? opts->res_tol : 1e-7;
-  const double e_tol = opts->e_tol > 0 ? opts->e_tol : 1e-10;
-  Dav D{P, s, L};
-  {
-    std::vector<int64_t> offs; std::vector<int> ns;
+// One system's Davidson solve as a state machine.  iterate() needs sigma of
+// every vector in the pending slot range [p0, p1) of V in S; the driver
+// evaluates those (for many systems at once in a batch) and calls iterate()
+// again.  Sec. 2, PNO-EOM-CCSD Davidson; readings in the header of pnoeom.h.
+struct DavState {
+  pnoeom_pno* P;
+  cudaStream_t s;
+  int64_t L;
+  int nroots, maxsub, max_iter;
+  double res_tol, e_tol, tol_mixed;
+  bool refine;
+  int prec;
+  Dav D;
+  DBuf<double> V, S, X, R;
+  DBuf<float> fin, fout;    // FP32 copies of the pending vectors and their sigma
+  int m = 0, nr = 0, it = 0, p0 = 0, p1 = 0;
+  bool done = false, converged = false;
+  std::vector<double> w, rn, w_old;
+
+  DavState(pnoeom_pno* P_, const pnoeom_opts* opts, cudaStream_t s_) : P(P_), s(s_), L(P_->L), D{P_, s_, P_->L} {
+    nroots = opts->nroots_solve;
+    PN_CHECK(nroots >= 1 && nroots <= P->nroots_sa, PNOEOM_ERR_INVALID_ARG, "nroots_solve must be in [1, nroots_sa]");
+    PN_CHECK(L >= nroots, PNOEOM_ERR_INVALID_ARG, "PNO space smaller than the number of roots");
+    maxsub = std::max(opts->max_subspace > 0 ? opts->max_subspace : 8 * nroots, 2 * nroots + 1);
+    max_iter = opts->max_iter > 0 ? opts->max_iter : 100;
+    res_tol = opts->res_tol > 0 ? opts->res_tol : 1e-7;
+    e_tol = opts->e_tol > 0 ? opts->e_tol : 1e-10;
+    prec = opts->precision == PNOEOM_FP32 ? PNOEOM_FP32 : PNOEOM_FP64;
+    refine = prec == PNOEOM_FP32 && opts->refine_fp64;
+    // in mixed precision, converge to a looser residual first, then refine in FP64
+    tol_mixed = refine ? std::max(res_tol, 1e-4) : res_tol;
+    std::vector<int64_t> offs;
+    std::vector<int> ns;
     for (int p = 0; p < P->npairs; ++p)
       if (P->pair_i[p] == P->pair_j[p] && P->nij[p] > 1) { offs.push_back(P->off_ij[p]); ns.push_back(P->nij[p]); }
     D.nd = (int)offs.size();
     D.dOffs.alloc(std::max<size_t>(1, offs.size())); D.dOffs.upload(offs.data(), offs.size(), s);
     D.dNs.alloc(std::max<size_t>(1, ns.size())); D.dNs.upload(ns.data(), ns.size(), s);
+    V.alloc((size_t)maxsub * L); S.alloc((size_t)maxsub * L);
+    X.alloc((size_t)nroots * L); R.alloc((size_t)nroots * L);
+    for (int k = 0; k < P->nroots_sa && m < nroots; ++k) {   // projected CIS guesses
+      double* t = V.get() + (int64_t)m * L;
+      PN_CUDA(cudaMemcpyAsync(t, P->guesses.get() + (int64_t)k * L, L * 8, cudaMemcpyDeviceToDevice, s));
+      if (D.orth(V.get(), m, t) > 1e-10) ++m;
+    }
+    PN_CHECK(m > 0, PNOEOM_ERR_INVALID_ARG, "no guess vector survives the projection");
+    nr = std::min(nroots, m);
+    p0 = 0; p1 = m;
   }
-  DBuf<double> V((size_t)maxsub * L), S((size_t)maxsub * L), X((size_t)nroots * L), R((size_t)nroots * L), T((size_t)L);
-  int m = 0;
-  for (int k = 0; k < P->nroots_sa && m < nroots; ++k) {   // projected CIS guesses
-    double* t = V.get() + (int64_t)m * L;
-    PN_CUDA(cudaMemcpyAsync(t, P->guesses.get() + (int64_t)k * L, L * 8, cudaMemcpyDeviceToDevice, s));
-    if (D.orth(V.get(), m, t) > 1e-10) ++m;
-  }
-  PN_CHECK(m > 0, PNOEOM_ERR_INVALID_ARG, "no guess vector survives the projection");
-  int prec = opts->precision == PNOEOM_FP32 ? PNOEOM_FP32 : PNOEOM_FP64;
-  const bool refine = prec == PNOEOM_FP32 && opts->refine_fp64;
-  // in mixed precision, converge to a looser residual first, then refine in FP64
-  const double tol_mixed = refine ? std::max(res_tol, 1e-4) : res_tol;
-  D.sigma(V.get(), S.get(), m, prec);
-  std::vector<double> w_old;
-  int nr = std::min(nroots, m);
-  std::vector<double> w(nr), rn(nr);
-  *converged = 0;
-  int it = 0;
-  for (it = 1; it <= max_iter; ++it) {
+
+  double tol_now() const { return prec == PNOEOM_FP32 ? tol_mixed : res_tol; }
+
+  // one Davidson iteration on the current subspace (all sigma available)
+  void iterate() {
+    if (++it > max_iter) { it = max_iter; done = true; return; }
     std::vector<double> G = D.gram(V.get(), m, S.get(), m);   // G[a][b] = <v_a, sigma(v_b)>
     std::vector<double> wr(m), wi(m), VR((size_t)m * m);
     PN_CHECK(small_eig(m, G.data(), wr.data(), wi.data(), VR.data()) == 0, PNOEOM_ERR_NOT_CONVERGED,
@@ -379,7 +431,7 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
     std::sort(ord.begin(), ord.end(), [&](int a, int b) { return wr[a] < wr[b]; });
     nr = std::min(nroots, m);
     w.assign(nr, 0.0);
-    std::vector<double> Cy((size_t)nr * m), Cs((size_t)nr * m);
+    std::vector<double> Cy((size_t)nr * m);
     for (int q = 0; q < nr; ++q) {
       w[q] = wr[ord[q]];
       for (int a = 0; a < m; ++a) Cy[(size_t)q * m + a] = VR[(size_t)a * m + ord[q]];
@@ -388,27 +440,18 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
     D.combine(R.get(), S.get(), Cy, m, nr, 0.0);                  // sigma of Ritz vectors
     for (int q = 0; q < nr; ++q) axpby<double>(R.get() + (int64_t)q * L, X.get() + (int64_t)q * L, -w[q], 1.0, L, s);
     rn.assign(nr, 0.0);
-    for (int q = 0; q < nr; ++q) rn[q] = std::sqrt(std::max(0.0, D.gram(R.get() + (int64_t)q * L, 1, R.get() + (int64_t)q * L, 1)[0]));
+    for (int q = 0; q < nr; ++q)
+      rn[q] = std::sqrt(std::max(0.0, D.gram(R.get() + (int64_t)q * L, 1, R.get() + (int64_t)q * L, 1)[0]));
     double dw = 1e300;
     if ((int)w_old.size() == nr) { dw = 0; for (int q = 0; q < nr; ++q) dw = std::max(dw, std::fabs(w[q] - w_old[q])); }
     w_old = w;
     bool conv = true;
-    const double tol_now = prec == PNOEOM_FP32 ? tol_mixed : res_tol;
-    for (int q = 0; q < nr; ++q) conv = conv && rn[q] < tol_now;
+    for (int q = 0; q < nr; ++q) conv = conv && rn[q] < tol_now();
     conv = conv && (prec == PNOEOM_FP32 && refine ? true : dw < e_tol);
-    if (conv) {
-      if (prec == PNOEOM_FP32 && refine) {   // FP64 refinement: recompute sigma of the subspace in FP64
-        prec = PNOEOM_FP64;
-        D.sigma(V.get(), S.get(), m, prec);
-        w_old.clear();
-        continue;
-      }
-      *converged = 1;
-      break;
-    }
-    // new directions from the preconditioned residuals
+    if (conv) { finish_or_refine(); return; }
     std::vector<int> add;
-    for (int q = 0; q < nr; ++q) if (rn[q] >= tol_now) add.push_back(q);
+    for (int q = 0; q < nr; ++q) if (rn[q] >= tol_now()) add.push_back(q);
+    int first_new = m;
     if (m + (int)add.size() > maxsub) {      // collapse onto the Ritz vectors
       PN_CUDA(cudaMemcpyAsync(V.get(), X.get(), (size_t)nr * L * 8, cudaMemcpyDeviceToDevice, s));
       int mm = 0;
@@ -418,7 +461,7 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
         if (D.orth(V.get(), mm, t) > 1e-10) ++mm;
       }
       m = mm;
-      D.sigma(V.get(), S.get(), m, prec);
+      first_new = 0;                          // the collapsed vectors need sigma again
     }
     int m0 = m;
     for (int q : add) {
@@ -429,27 +472,273 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
       D.symdiag(t);
       if (D.orth(V.get(), m, t) > 1e-8) ++m;
     }
-    if (m == m0) {   // no new direction: converged if every residual is within tolerance
+    if (m == m0 && first_new == m) {   // no new direction: converged if every residual is within tolerance
       bool allres = true;
-      for (int q = 0; q < nr; ++q) allres = allres && rn[q] < tol_now;
-      if (allres && prec == PNOEOM_FP32 && refine) {
-        prec = PNOEOM_FP64;
-        D.sigma(V.get(), S.get(), m, prec);
-        w_old.clear();
-        continue;
-      }
-      *converged = allres ? 1 : 0;
-      break;
+      for (int q = 0; q < nr; ++q) allres = allres && rn[q] < tol_now();
+      if (allres) { finish_or_refine(); return; }
+      done = true;
+      return;
     }
-    D.sigma(V.get() + (int64_t)m0 * L, S.get() + (int64_t)m0 * L, m - m0, prec);
+    p0 = first_new; p1 = m;
   }
-  for (int q = 0; q < nr; ++q) { energies[q] = w[q]; res_norms[q] = rn[q]; }
-  for (int q = nr; q < nroots; ++q) { energies[q] = NAN; res_norms[q] = NAN; }
-  *iters = std::min(it, max_iter);
-  P->last_X.resize((size_t)nr * L);
-  X.download(P->last_X.data(), P->last_X.size(), s);
-  PN_CUDA(cudaStreamSynchronize(s));
-  P->last_nroots = nr;
+
+  void finish_or_refine() {
+    if (prec == PNOEOM_FP32 && refine) {   // FP64 refinement: sigma of the whole subspace again in FP64
+      prec = PNOEOM_FP64;
+      w_old.clear();
+      p0 = 0; p1 = m;
+      return;
+    }
+    converged = true;
+    done = true;
+  }
+
+  void results(double* energies, double* res_norms, int* iters) {
+    for (int q = 0; q < nr; ++q) { energies[q] = w.size() > (size_t)q ? w[q] : NAN; res_norms[q] = rn.size() > (size_t)q ? rn[q] : NAN; }
+    for (int q = nr; q < nroots; ++q) { energies[q] = NAN; res_norms[q] = NAN; }
+    *iters = it;
+    P->last_X.resize((size_t)nr * L);
+    X.download(P->last_X.data(), P->last_X.size(), s);
+    PN_CUDA(cudaStreamSynchronize(s));
+    P->last_nroots = nr;
+  }
+};
+
+// Drives a set of Davidson states in lockstep: in every round, the pending
+// sigma vectors of all states (in chunks of at most `chunk` per state) are
+// evaluated by `eval(states, nvec, prec)`, which must fill S[p0 .. p0+nvec)
+// of each state with nvec > 0; states whose pending range is empty iterate.
+template <typename Eval>
+void drive(std::vector<DavState*>& st, int chunk, Eval&& eval) {
+  for (;;) {
+    bool any = false;
+    for (DavState* d : st)
+      while (!d->done && d->p0 >= d->p1) d->iterate();
+    for (DavState* d : st) any = any || !d->done;
+    if (!any) return;
+    for (int prec : {PNOEOM_FP32, PNOEOM_FP64}) {
+      std::vector<int> nv(st.size(), 0);
+      bool need = false;
+      for (size_t k = 0; k < st.size(); ++k)
+        if (!st[k]->done && st[k]->prec == prec && st[k]->p0 < st[k]->p1) {
+          nv[k] = std::min(chunk, st[k]->p1 - st[k]->p0);
+          need = true;
+        }
+      if (!need) continue;
+      eval(st, nv, prec);
+      for (size_t k = 0; k < st.size(); ++k) st[k]->p0 += nv[k];
+    }
+  }
+}
+
+// sigma of each state's pending chunk through one program launch sequence
+void eval_states(const Program& prog, std::vector<DavState*>& st, const std::vector<int>& nv, int prec,
+                 std::vector<DBuf<double>>* work64, std::vector<DBuf<float>>* work32, cudaStream_t s,
+                 pnoeom_pno* timing_owner) {
+  SysTable t{};
+  t.nsys = (int)st.size();
+  t.max_nvec = 0;
+  std::vector<int64_t> ol(st.size()), wl(st.size());
+  for (size_t k = 0; k < st.size(); ++k) {
+    DavState* d = st[k];
+    ol[k] = d->L; wl[k] = d->P->work_len;
+    const int n = nv[k];
+    t.max_nvec = std::max(t.max_nvec, n);
+    if (!n) { t.s[k] = SysBuf{}; continue; }
+    const size_t need = (size_t)n * d->P->work_len;
+    if (prec == PNOEOM_FP64) {
+      DBuf<double>& w = (*work64)[k];
+      if (w.n < need) w.alloc(need);
+      t.s[k] = sysbuf(d->P, n, d->V.get() + (int64_t)d->p0 * d->L, d->S.get() + (int64_t)d->p0 * d->L, w.get(), false);
+    } else {
+      DBuf<float>& w = (*work32)[k];
+      if (w.n < need) w.alloc(need);
+      const size_t len = (size_t)n * d->L;
+      if (d->fin.n < len) { d->fin.alloc(len); d->fout.alloc(len); }
+      d2f(d->fin.get(), d->V.get() + (int64_t)d->p0 * d->L, len, s);
+      t.s[k] = sysbuf(d->P, n, d->fin.get(), d->fout.get(), w.get(), true);
+    }
+  }
+  if (prec == PNOEOM_FP64) run_program<double>(prog, t, ol.data(), wl.data(), s, timing_owner);
+  else run_program<float>(prog, t, ol.data(), wl.data(), s, timing_owner);
+  if (prec == PNOEOM_FP32)
+    for (size_t k = 0; k < st.size(); ++k)
+      if (nv[k]) f2d(st[k]->S.get() + (int64_t)st[k]->p0 * st[k]->L, st[k]->fout.get(), (size_t)nv[k] * st[k]->L, s);
+}
+
+void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaStream_t s, double* energies,
+                  double* res_norms, int* iters, int* converged) {
+  (void)ctx;
+  DavState d(P, opts, s);
+  std::vector<DavState*> st{&d};
+  std::vector<DBuf<double>> w64(1);
+  std::vector<DBuf<float>> w32(1);
+  drive(st, d.maxsub, [&](std::vector<DavState*>& ss, const std::vector<int>& nv, int prec) {
+    eval_states(P->prog, ss, nv, prec, &w64, &w32, s, nullptr);
+  });
+  d.results(energies, res_norms, iters);
+  *converged = d.converged ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of systems
+
+// Merge the members' programs: every problem keeps its offsets (relative to its
+// own system's buffers) and gets the member index as its system index.
+void batch_build(pnoeom_batch* B, cudaStream_t s) {
+  const int n = (int)B->members.size();
+  PN_CHECK(n >= 1 && n <= MAX_SYS, PNOEOM_ERR_INVALID_ARG, "a batch holds 1.." + std::to_string(MAX_SYS) + " systems");
+  Program& G = B->prog;
+  for (int k = 0; k < n; ++k) {
+    const Program& Pg = B->members[k]->prog;
+    auto add = [&](std::vector<SProb>& dst, const std::vector<SProb>& src) {
+      for (SProb q : src) { q.sys = k; dst.push_back(q); }
+    };
+    auto addv = [&](std::vector<VProb>& dst, const std::vector<VProb>& src) {
+      for (VProb q : src) { q.sys = k; dst.push_back(q); }
+    };
+    add(G.h_gen1, Pg.h_gen1); add(G.h_gen2, Pg.h_gen2);
+    addv(G.h_v1, Pg.h_v1); addv(G.h_v2, Pg.h_v2);
+    G.smem_elems = std::max(G.smem_elems, Pg.smem_elems);
+    for (int phase = 0; phase < 2; ++phase)
+      for (int b = 0; b < 3; ++b) {
+        SmallSet& D = phase == 0 ? G.small1[b] : G.small2[b];
+        const SmallSet& S = phase == 0 ? Pg.small1[b] : Pg.small2[b];
+        const int base = (int)D.h_probs.size();
+        for (SProb q : S.h_probs) { q.sys = k; D.h_probs.push_back(q); }
+        for (int c = 0; c < NGROUP_CAND; ++c) {
+          if (!D.h_starts[c].empty()) D.h_starts[c].pop_back();   // drop the previous end marker
+          for (size_t x = 0; x + 1 < S.h_starts[c].size(); ++x) D.h_starts[c].push_back(base + S.h_starts[c][x]);
+          D.h_starts[c].push_back((int)D.h_probs.size());
+        }
+        for (int d = 0; d < 4; ++d) D.dims[d] = std::max(D.dims[d], S.dims[d]);
+      }
+  }
+  G.upload(s, &B->footprint);
+  B->w64.resize(n);
+  B->w32.resize(n);
+  // autotune the merged program: FP32 sigma of nroots_sa vectors per member
+  std::vector<DBuf<float>> r(n), o(n);
+  std::vector<const void*> rp(n);
+  std::vector<void*> op(n);
+  std::vector<int> nv(n);
+  for (int k = 0; k < n; ++k) {
+    nv[k] = std::max(1, B->members[k]->nroots_sa);
+    r[k].alloc((size_t)nv[k] * B->members[k]->L);
+    o[k].alloc((size_t)nv[k] * B->members[k]->L);
+    r[k].zero(s);
+    rp[k] = r[k].get(); op[k] = o[k].get();
+  }
+  cudaEvent_t e0, e1;
+  PN_CUDA(cudaEventCreate(&e0));
+  PN_CUDA(cudaEventCreate(&e1));
+  double best = 1e300;
+  int pick = 0, pick_r = 0;
+  for (int c = 0; c < NGROUP_CAND; ++c)
+    for (int rr = 0; rr < NRPC_CAND; ++rr) {
+      G.group_choice = c; G.rpc_choice = rr;
+      batch_sigma(B, nv.data(), rp.data(), op.data(), PNOEOM_FP32, s);
+      PN_CUDA(cudaEventRecord(e0, s));
+      for (int q = 0; q < 2; ++q) batch_sigma(B, nv.data(), rp.data(), op.data(), PNOEOM_FP32, s);
+      PN_CUDA(cudaEventRecord(e1, s));
+      PN_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      B->tune_ms[c * NRPC_CAND + rr] = ms / 2;
+      if (ms < best) { best = ms; pick = c; pick_r = rr; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  G.group_choice = pick;
+  G.rpc_choice = pick_r;
+}
+
+// Capture `body` (stream operations on s) as a CUDA graph and launch it, reusing
+// the batch's executable graph through cudaGraphExecUpdate when the topology is
+// unchanged (only kernel parameters and pointers differ between calls).
+template <typename Body>
+void graph_launch(pnoeom_batch* B, cudaStream_t s, Body&& body) {
+  if (!B->use_graph || s == nullptr) { body(); return; }
+  cudaGraph_t g = nullptr;
+  PN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  try {
+    body();
+  } catch (...) {
+    cudaStreamEndCapture(s, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  PN_CUDA(cudaStreamEndCapture(s, &g));
+  bool ok = false;
+  if (B->exec) {
+    cudaGraphExecUpdateResultInfo info;
+    ok = cudaGraphExecUpdate(B->exec, g, &info) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    else ++B->graph_updates;
+  }
+  if (!ok) {
+    PN_CUDA(cudaGraphInstantiate(&B->exec, g, 0));
+    ++B->graph_instantiations;
+  }
+  cudaGraphDestroy(g);
+  PN_CUDA(cudaGraphLaunch(B->exec, s));
+  ++B->graph_launches;
+}
+
+void batch_sigma(pnoeom_batch* B, const int* nvec, const void* const* r, void* const* out, int prec, cudaStream_t s) {
+  const int n = (int)B->members.size();
+  SysTable t{};
+  t.nsys = n;
+  std::vector<int64_t> ol(n), wl(n);
+  for (int k = 0; k < n; ++k) {
+    pnoeom_pno* P = B->members[k];
+    ol[k] = P->L; wl[k] = P->work_len;
+    const int nv = nvec[k];
+    t.max_nvec = std::max(t.max_nvec, nv);
+    if (nv <= 0) { t.s[k] = SysBuf{}; continue; }
+    PN_CHECK(r[k] && out[k], PNOEOM_ERR_INVALID_ARG, "NULL vector in batch sigma");
+    const size_t need = (size_t)nv * P->work_len;
+    void* w;
+    if (prec == PNOEOM_FP64) { if (B->w64[k].n < need) B->w64[k].alloc(need); w = B->w64[k].get(); }
+    else { if (B->w32[k].n < need) B->w32[k].alloc(need); w = B->w32[k].get(); }
+    t.s[k] = sysbuf(P, nv, r[k], out[k], w, prec == PNOEOM_FP32);
+  }
+  graph_launch(B, s, [&] {
+    if (prec == PNOEOM_FP64) run_program<double>(B->prog, t, ol.data(), wl.data(), s, nullptr);
+    else run_program<float>(B->prog, t, ol.data(), wl.data(), s, nullptr);
+  });
+}
+
+void batch_solve(pnoeom_batch* B, const pnoeom_opts* opts, cudaStream_t s, double* energies, double* res_norms,
+                 int* iters, int* converged) {
+  const int n = (int)B->members.size();
+  std::vector<std::unique_ptr<DavState>> own;
+  std::vector<DavState*> st;
+  for (int k = 0; k < n; ++k) {
+    own.emplace_back(new DavState(B->members[k], opts, s));
+    st.push_back(own.back().get());
+  }
+  std::vector<DBuf<double>>& w64 = B->w64;
+  std::vector<DBuf<float>>& w32 = B->w32;
+  drive(st, opts->nroots_solve, [&](std::vector<DavState*>& ss, const std::vector<int>& nv, int prec) {
+    // work buffers first (no allocation inside the captured region)
+    for (size_t k = 0; k < ss.size(); ++k) {
+      if (!nv[k]) continue;
+      const size_t need = (size_t)nv[k] * ss[k]->P->work_len;
+      if (prec == PNOEOM_FP64) { if (w64[k].n < need) w64[k].alloc(need); }
+      else {
+        if (w32[k].n < need) w32[k].alloc(need);
+        const size_t len = (size_t)nv[k] * ss[k]->L;
+        if (ss[k]->fin.n < len) { ss[k]->fin.alloc(len); ss[k]->fout.alloc(len); }
+      }
+    }
+    graph_launch(B, s, [&] { eval_states(B->prog, ss, nv, prec, &w64, &w32, s, nullptr); });
+  });
+  const int nroots = opts->nroots_solve;
+  for (int k = 0; k < n; ++k) {
+    st[k]->results(energies + (size_t)k * nroots, res_norms + (size_t)k * nroots, iters + k);
+    converged[k] = st[k]->converged ? 1 : 0;
+  }
 }
 
 }  // namespace pnoeom
