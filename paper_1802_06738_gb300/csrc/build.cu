@@ -170,6 +170,32 @@ void eig_dense_sym(cusolverDnHandle_t h, cudaStream_t s, double* A, double* W, i
   for (int x : hinfo) PN_CHECK(x == 0, PNOEOM_ERR_CUDA, "eigensolver info != 0: " + std::to_string(x));
 }
 
+// Lowest `nev` eigenpairs of a symmetric n x n matrix (cuSOLVER Xsyevdx, index
+// range 1..nev).  Eigenvalues ascending into W, eigenvectors into the first nev
+// columns (column-major) of A.
+void eig_lowest(cusolverDnHandle_t h, cudaStream_t s, double* A, double* W, int64_t n, int64_t nev) {
+  cusolverDnParams_t params;
+  PN_SOLVER(cusolverDnCreateParams(&params));
+  PN_SOLVER(cusolverDnSetStream(h, s));
+  size_t dws = 0, hws = 0;
+  int64_t found = 0;
+  double vl = 0, vu = 0;
+  PN_SOLVER(cusolverDnXsyevdx_bufferSize(h, params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER,
+                                         n, CUDA_R_64F, A, n, &vl, &vu, 1, nev, &found, CUDA_R_64F, W, CUDA_R_64F, &dws,
+                                         &hws));
+  DBuf<unsigned char> dw(std::max<size_t>(dws, 1));
+  std::vector<unsigned char> hw(std::max<size_t>(hws, 1));
+  DBuf<int> info(1);
+  PN_SOLVER(cusolverDnXsyevdx(h, params, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, n,
+                              CUDA_R_64F, A, n, &vl, &vu, 1, nev, &found, CUDA_R_64F, W, CUDA_R_64F, dw.get(), dws,
+                              hw.data(), hws, info.get()));
+  int hinfo = 0;
+  PN_CUDA(cudaMemcpyAsync(&hinfo, info.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  PN_CUDA(cudaStreamSynchronize(s));
+  cusolverDnDestroyParams(params);
+  PN_CHECK(hinfo == 0 && found >= nev, PNOEOM_ERR_CUDA, "partial eigensolver failed (info " + std::to_string(hinfo) + ")");
+}
+
 }  // namespace
 
 // Pool-block bookkeeping on the host.
@@ -209,6 +235,8 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
   DV dB((size_t)N * nmo * nmo);
   PN_CUDA(cudaMemcpyAsync(dB.get(), sys->B, dB.n * sizeof(double), kind, s));
   bd.sync();
+  StageTimer tm(s);
+  tm.mark("inputs");
   const std::vector<double>& eps = P->eps;
 
   // undressed blocks (CIS, CIS(D), MP1 use the HF Hamiltonian)
@@ -275,6 +303,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
   dB.release();
   Bd.release();
 
+  tm.mark("dressing");
   // ---- T2 --------------------------------------------------------------------
   DV t2((size_t)O * O * V * V);
   if (sys->t2) {
@@ -288,6 +317,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
   bd.perm(t2.get(), u2.get(), {O, O, V, V}, {0, 1, 3, 2}, -1.0, 0.0);
   axpby<double>(u2.get(), t2.get(), 2.0, 1.0, u2.n, s);
 
+  tm.mark("T2");
   // ---- CIS (singlet; A = delta (e_a - e_i) + 2 (ia|jb) - (ij|ab)) ---------------
   const int nr = opts->nroots_sa;
   const int64_t ov = O * V;
@@ -298,7 +328,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     bd.con("Qij", Boo.get(), "Qab", Bvv.get(), "iajb", A.get(), -1.0, 1.0);
     k_cis_diag<<<gsz(ov), 256, 0, s>>>(A.get(), deps.get(), o, v);
     PN_CUDA(cudaGetLastError());
-    eig_dense_sym(ctx->solver, s, A.get(), W.get(), ov, 1);
+    eig_lowest(ctx->solver, s, A.get(), W.get(), ov, nr);
     std::vector<double> w(nr);
     W.download(w.data(), nr, s);
     PN_CUDA(cudaMemcpyAsync(bcis.data(), A.get(), bcis.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -314,6 +344,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     P->cis_b = bcis;
   }
 
+  tm.mark("CIS");
   // ---- CIS(D) doubles and state-averaged pair densities ------------------------
   const int npairs = o * (o + 1) / 2;
   P->npairs = npairs;
@@ -353,6 +384,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     }
   }
 
+  tm.mark("CIS(D) densities");
   // ---- PNOs and OSVs ------------------------------------------------------------
   std::vector<double> occ((size_t)npairs * v);
   {
@@ -458,13 +490,18 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     P->guesses.upload(gs.data(), gs.size(), s);
   }
   Boo.release(); Bov.release(); Bvo.release(); Bvv.release();
+  tm.mark("PNO/OSV eigensolves");
 
   // The rest (intermediates, pool, problem lists) lives in build_program.cu.
   extern void build_program(pnoeom_pno * P, cudaStream_t s, const double* Fd, DV& dBoo, DV& dBov, DV& dBvo, DV& dBvv,
                             DV& t2, DV& u2);
   build_program(P, s, Fd.data(), dBoo, dBov, dBvo, dBvv, t2, u2);
   bd.sync();
+  tm.mark("operator program");
   autotune(P, s);
+  tm.mark("autotune");
+  PN_CUDA(cudaStreamSynchronize(s));
+  pool_trim();   // setup temporaries go back to CUDA
   P->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
 }
 

@@ -165,6 +165,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   const int64_t L1 = P->L1, L = P->L;
   size_t* fp = &P->footprint;
 
+  StageTimer tm(s);
   // ---- dressed Fock blocks ------------------------------------------------------
   std::vector<double> Foo(O * O), Fov(O * V), Fvv(V * V);
   for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) Foo[i * o + j] = Fd[i * nmo + j];
@@ -189,6 +190,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   const double* t = t2.get();
   const double* u = u2.get();
 
+  tm.mark("  integral blocks");
   // ---- R-independent intermediates ------------------------------------------------
   DV W(O * O * O * O);       // W[k,i,l,j] = (ki|lj) + sum_cd t^{cd}_{ij} (kc|ld)
   PN_CUDA(cudaMemcpyAsync(W.get(), g_oooo.get(), W.n * 8, cudaMemcpyDeviceToDevice, s));
@@ -227,21 +229,38 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     PN_CUDA(cudaGetLastError());
     G.sync();
   }
+  tm.mark("  o^2v^2 intermediates");
   // v^3 o blocks
   DV g_vvov(V * V * O * V);    // (ad|kc) at [a,d,k,c]
   G.con("Qad", dBvv.get(), "Qkc", dBov.get(), "adkc", g_vvov.get());
   DV Y1(O * O * O * V), Y2(O * O * V * O);
   G.con("ijcd", t, "bdkc", g_vvov.get(), "ijkb", Y1.get());
   G.con("ijcd", t, "ackd", g_vvov.get(), "ijak", Y2.get());
-  DV Qa(O * V * V * V), Q1(O * V * V * V);   // [j,d,a,b]
-  G.con("ackd", g_vvov.get(), "kjbc", t, "jdab", Q1.get());
+  // Singles -> doubles couplings through the v^3 o integrals, contracted with r1 (OSV index D):
+  //   Qa[y; d,a,b] = sum_kc [(ad|kc) - 1/2 (ac|kd)] u[y,k,b,c] - 1/2 sum_kc (ac|kd) t[k,y,b,c]
+  //   Q1[x; d,a,b] = sum_kc (ac|kd) t[k,x,b,c]
+  // are only needed projected (d on an OSV space, a and b on a pair's PNO space), so the OSV
+  // projection of d is applied to the integrals first (per occupied z):
+  //   Gz[a,D,k,c] = sum_d U^z[d,D] ((ad|kc) - 1/2 (ac|kd)),  Hz[a,D,k,c] = sum_d U^z[d,D] (ac|kd),
+  // and the PNO projection of b to the amplitudes (per pair), see the pair loop below.
+  std::vector<DV> Gz(O), Hz(O);
   {
     DV G34(g_vvov.n);
     G.perm(g_vvov.get(), G34.get(), {V, V, O, V}, {0, 3, 2, 1}, -0.5);
     axpby<double>(G34.get(), g_vvov.get(), 1.0, 1.0, G34.n, s);
-    G.con("adkc", G34.get(), "jkbc", u, "jdab", Qa.get());
+    for (int z = 0; z < o; ++z) {
+      const int nz = G.no(z);
+      if (!nz) continue;
+      Dims d = G.dm;
+      d['D'] = nz;
+      Gz[z].alloc((size_t)V * nz * O * V);
+      Hz[z].alloc((size_t)V * nz * O * V);
+      G.con(d, "adkc", G34.get(), "dD", G.Uo(z), "aDkc", Gz[z].get());
+      G.con(d, "ackd", g_vvov.get(), "dD", G.Uo(z), "aDkc", Hz[z].get());
+    }
   }
-  axpby<double>(Qa.get(), Q1.get(), -0.5, 1.0, Qa.n, s);
+  DV tY(O * O * V * V);   // tY[y][k][b][c] = t[k,y,b,c]
+  G.perm(t, tY.get(), {O, O, V, V}, {1, 0, 2, 3});
   DV Qb(O * O * O * V);
   {
     DV Q2(Qb.n), Q5(Qb.n), Q6(Qb.n);
@@ -291,6 +310,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   G.perm(Wd.get(), Wdp.get(), {V, O, O, V}, {1, 2, 0, 3});
   G.sync();
 
+  tm.mark("  v^3 o intermediates");
   // ---- pool layout ------------------------------------------------------------------
   auto nP = [&](int p) { return (int64_t)P->nij[p]; };
   int64_t pool = 0;
@@ -336,6 +356,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   }
   auto Sblk = [&](int p, int q) { return offS[(size_t)p * npairs + q]; };
 
+  tm.mark("  overlaps");
   // ---- mixed-pair ring blocks -------------------------------------------------------------
   {
     std::vector<Prog::PJ> jobs;
@@ -352,6 +373,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     }
     G.project(jobs);
   }
+  tm.mark("  ring blocks");
   // ---- E3 / E4 blocks ---------------------------------------------------------------------------
   {
     std::vector<GemmProb<double>> pr;
@@ -393,6 +415,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     }
   }
 
+  tm.mark("  global-term blocks");
   // R1 column blocks shared by all pairs: Lv1[b,c,(m,D)] = sum_d (2 (bc|md) - (bd|mc)) U^m[d,D],
   // GamAll[y][k][(m,D)] = sum_d (2 (ky|md) - (kd|my)) U^m[d,D]
   DV Lv1(std::max<int64_t>(1, V * V * L1)), GamAll(std::max<int64_t>(1, O * O * L1));
@@ -490,18 +513,28 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       DV Yc(nn * nn * std::max<int64_t>(1, L1));
       Yc.zero(s);
       d['L'] = L1;
-      // Qa (OSV x), -Q1 (OSV y)
-      for (int side = 0; side < 2; ++side) {
-        const int z = side == 0 ? x : y;
-        const int nz = G.no(z);
-        if (!nz) continue;
-        d['D'] = nz;
-        const double* Qsrc = side == 0 ? Qa.get() + (int64_t)y * V * V * V : Q1.get() + (int64_t)x * V * V * V;
-        DV T1(nz * V * V), T2(nz * nn * V), K3(nn * nn * nz);
-        G.con(d, "dab", Qsrc, "dD", G.Uo(z), "Dab", T1.get());
-        G.con(d, "Dab", T1.get(), "aA", Up, "DAb", T2.get());
-        G.con(d, "DAb", T2.get(), "bB", Up, "ABD", K3.get());
-        G.add_block(Yc.get() + P->off_i[z], L1, K3.get(), nz, nn * nn, nz, side == 0 ? 1.0 : -1.0);
+      // Qa (OSV x) and -Q1 (OSV y), projected: PNO projection of b on the amplitudes,
+      // ut[k,c,B] = sum_b U[b,B] u[y,k,b,c], ty[k,c,B] = sum_b U[b,B] t[k,y,b,c], tx likewise for x
+      {
+        DV ut((size_t)O * V * nn), ty((size_t)O * V * nn), tx((size_t)O * V * nn);
+        G.con(d, "kbc", u + (int64_t)y * O * V * V, "bB", Up, "kcB", ut.get());
+        G.con(d, "kbc", tY.get() + (int64_t)y * O * V * V, "bB", Up, "kcB", ty.get());
+        G.con(d, "kbc", tY.get() + (int64_t)x * O * V * V, "bB", Up, "kcB", tx.get());
+        for (int side = 0; side < 2; ++side) {
+          const int z = side == 0 ? x : y;
+          const int nz = G.no(z);
+          if (!nz) continue;
+          d['D'] = nz;
+          DV T1((size_t)V * nz * nn), K3((size_t)nn * nn * nz);
+          if (side == 0) {
+            G.con(d, "aDkc", Gz[z].get(), "kcB", ut.get(), "aDB", T1.get());
+            G.con(d, "aDkc", Hz[z].get(), "kcB", ty.get(), "aDB", T1.get(), -0.5, 1.0);
+          } else {
+            G.con(d, "aDkc", Hz[z].get(), "kcB", tx.get(), "aDB", T1.get(), -1.0, 0.0);
+          }
+          G.con(d, "aDB", T1.get(), "aA", Up, "ABD", K3.get());
+          G.add_block(Yc.get() + P->off_i[z], L1, K3.get(), nz, nn * nn, nz, 1.0);
+        }
       }
       d['D'] = nn;
       if (L1 > 0) {
@@ -550,6 +583,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     G.sync();
   }
 
+  tm.mark("  pair loop (D, A_DS)");
   // ---- singles rows A_S_i (n_i x L) --------------------------------------------------------------
   for (int i = 0; i < o; ++i) {
     const int ni = G.no(i);
@@ -628,6 +662,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   }
   G.sync();
 
+  tm.mark("  singles rows");
   // ---- problem lists ------------------------------------------------------------------------------
   P->work_fvr = 0;
   P->work_for = V * V;

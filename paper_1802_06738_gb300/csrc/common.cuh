@@ -39,7 +39,15 @@ struct Error : std::runtime_error {
 #define PN_CHECK(cond, code, msg)                                                  \
   do { if (!(cond)) throw ::pnoeom::Error((code), (msg)); } while (0)
 
-// Owning device buffer (cudaMalloc/cudaFree).  Counts bytes into a shared
+// Per-host-thread caching device allocator.  Freed blocks are kept and reused
+// by later allocations of the same thread; every thread of the library keeps to
+// one stream for its device work, so a reused block is stream-ordered after the
+// work that used it before.  trim() returns the cache to CUDA.
+void* pool_get(size_t bytes);
+void pool_put(void* p, size_t bytes);
+void pool_trim();
+
+// Owning device buffer (cached allocator, see pool_get).  Counts bytes into a shared
 // footprint counter so handles can report their device footprint.
 template <typename T>
 struct DBuf {
@@ -52,11 +60,11 @@ struct DBuf {
     release();
     n = count;
     counter = ctr;
-    if (count) PN_CUDA(cudaMalloc((void**)&p, count * sizeof(T)));
+    if (count) p = (T*)pool_get(count * sizeof(T));
     if (counter) *counter += count * sizeof(T);
   }
   void release() {
-    if (p) cudaFree(p);
+    if (p) pool_put(p, n * sizeof(T));
     if (counter) *counter -= n * sizeof(T);
     p = nullptr; n = 0; counter = nullptr;
   }
@@ -76,6 +84,16 @@ struct DBuf {
   void download(T* h, size_t count, cudaStream_t s) const {
     if (count) PN_CUDA(cudaMemcpyAsync(h, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
   }
+};
+
+// Stage timer for tracing: when the environment variable PNOEOM_LOG_TIMING is
+// set, mark() synchronises the stream and prints the seconds since the last mark.
+struct StageTimer {
+  cudaStream_t s;
+  bool on;
+  double t0;
+  explicit StageTimer(cudaStream_t st);
+  void mark(const char* what);
 };
 
 }  // namespace pnoeom

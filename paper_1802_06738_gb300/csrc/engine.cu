@@ -2,8 +2,77 @@
 #include "engine.cuh"
 #include <algorithm>
 #include <numeric>
+#include <map>
+#include <chrono>
+#include <cstdlib>
 
 namespace pnoeom {
+
+namespace {
+struct ThreadPool {
+  std::multimap<size_t, void*> free_blocks;
+  ~ThreadPool() {
+    for (auto& b : free_blocks) cudaFree(b.second);
+  }
+};
+thread_local ThreadPool t_pool;
+
+size_t round_size(size_t bytes) {
+  if (bytes <= 256) return 256;
+  if (bytes >= ((size_t)1 << 20)) return (bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+  size_t r = 256;
+  while (r < bytes) r <<= 1;
+  return r;
+}
+}  // namespace
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+StageTimer::StageTimer(cudaStream_t st) : s(st), on(std::getenv("PNOEOM_LOG_TIMING") != nullptr), t0(now_s()) {}
+void StageTimer::mark(const char* what) {
+  if (!on) return;
+  cudaStreamSynchronize(s);
+  double t = now_s();
+  std::fprintf(stderr, "[pnoeom] %-28s %8.3f s\n", what, t - t0);
+  t0 = t;
+}
+
+void* pool_get(size_t bytes) {
+  const size_t sz = round_size(bytes);
+  auto& fb = t_pool.free_blocks;
+  auto it = fb.lower_bound(sz);
+  if (it != fb.end() && it->first <= sz + sz / 4) {
+    void* p = it->second;
+    fb.erase(it);
+    return p;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, sz);
+  if (e != cudaSuccess) {   // out of memory: return the cache to CUDA and retry once
+    cudaGetLastError();
+    pool_trim();
+    e = cudaMalloc(&p, sz);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(e == cudaErrorMemoryAllocation ? PNOEOM_ERR_NOMEM : PNOEOM_ERR_CUDA,
+                  "device allocation of " + std::to_string(sz) + " bytes failed: " + cudaGetErrorString(e));
+    }
+  }
+  return p;
+}
+
+void pool_put(void* p, size_t bytes) {
+  if (p) t_pool.free_blocks.insert({round_size(bytes), p});
+}
+
+void pool_trim() {
+  auto& fb = t_pool.free_blocks;
+  if (fb.empty()) return;
+  cudaDeviceSynchronize();
+  for (auto& b : fb) cudaFree(b.second);
+  fb.clear();
+}
 
 namespace {
 constexpr int TM = 64, TN = 64, TK = 16;
@@ -12,13 +81,68 @@ struct TileRef { int prob, m0, n0; };
 
 // One 64x64 tile of one problem per CTA; 256 threads as 16x16, each 4x4
 // outputs; K staged through shared memory in chunks of 16.
+// One BM x BN output tile, 256 threads, each MR x NR outputs; K staged through
+// shared memory in chunks of TK.
+template <typename T, int BM, int BN, int MR, int NR>
+__device__ __forceinline__ void gemm_tile(const GemmProb<T>& P, const TileRef tr, T (*As)[BM + 1], T (*Bs)[BN + 1]) {
+  static_assert((BM / MR) * (BN / NR) == 256, "256 threads");
+  constexpr int TX = BN / NR;   // threads along N
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  T acc[MR][NR];
+#pragma unroll
+  for (int i = 0; i < MR; ++i)
+#pragma unroll
+    for (int j = 0; j < NR; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < P.K; k0 += TK) {
+    for (int e = threadIdx.x; e < BM * TK; e += 256) {
+      int m, k;
+      if (P.ta) { m = e % BM; k = e / BM; } else { k = e % TK; m = e / TK; }
+      int gm = tr.m0 + m, gk = k0 + k;
+      T val = T(0);
+      if (gm < P.M && gk < P.K) val = P.ta ? P.a[(int64_t)gk * P.lda + gm] : P.a[(int64_t)gm * P.lda + gk];
+      As[k][m] = val;
+    }
+    for (int e = threadIdx.x; e < BN * TK; e += 256) {
+      int n, k;
+      if (P.tb) { k = e % TK; n = e / TK; } else { n = e % BN; k = e / BN; }
+      int gn = tr.n0 + n, gk = k0 + k;
+      T val = T(0);
+      if (gn < P.N && gk < P.K) val = P.tb ? P.b[(int64_t)gn * P.ldb + gk] : P.b[(int64_t)gk * P.ldb + gn];
+      Bs[k][n] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < TK; ++k) {
+      T a[MR], b[NR];
+#pragma unroll
+      for (int i = 0; i < MR; ++i) a[i] = As[k][ty + (BM / MR) * i];
+#pragma unroll
+      for (int j = 0; j < NR; ++j) b[j] = Bs[k][tx + TX * j];
+#pragma unroll
+      for (int i = 0; i < MR; ++i)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < MR; ++i) {
+    int gm = tr.m0 + ty + (BM / MR) * i;
+    if (gm >= P.M) continue;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      int gn = tr.n0 + tx + TX * j;
+      if (gn >= P.N) continue;
+      T* c = P.c + (int64_t)gm * P.ldc + gn;
+      *c = (P.beta == T(0)) ? P.alpha * acc[i][j] : P.alpha * acc[i][j] + P.beta * (*c);
+    }
+  }
+}
+
+// One 64x64 tile of one problem per CTA; 256 threads as 16x16, each 4x4
+// outputs; K staged through shared memory in chunks of 16.
 template <typename T>
-__global__ void __launch_bounds__(256) k_grouped_gemm(const GemmProb<T>* __restrict__ probs,
-                                                      const TileRef* __restrict__ tiles) {
-  __shared__ T As[TK][TM + 1];
-  __shared__ T Bs[TK][TN + 1];
-  const TileRef tr = tiles[blockIdx.x];
-  const GemmProb<T> P = probs[tr.prob];
+__device__ __forceinline__ void gemm_tile(const GemmProb<T>& P, const TileRef tr, T (*As)[TM + 1], T (*Bs)[TN + 1]) {
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   T acc[4][4];
 #pragma unroll
@@ -71,6 +195,44 @@ __global__ void __launch_bounds__(256) k_grouped_gemm(const GemmProb<T>* __restr
   }
 }
 
+// One 64x64 tile of one problem per CTA; 256 threads as 16x16, each 4x4
+// outputs; K staged through shared memory in chunks of 16.
+template <typename T>
+__global__ void __launch_bounds__(256) k_grouped_gemm(const GemmProb<T>* __restrict__ probs,
+                                                      const TileRef* __restrict__ tiles) {
+  __shared__ T As[TK][TM + 1];
+  __shared__ T Bs[TK][TN + 1];
+  const TileRef tr = tiles[blockIdx.x];
+  gemm_tile<T, TM, TN, 4, 4>(probs[tr.prob], tr, As, Bs);
+}
+
+// Small groups: problems and tile offsets passed by value (no descriptor upload,
+// hence no implicit synchronisation of pageable host-to-device copies).
+constexpr int NPV = 160;
+template <typename T>
+struct GemmParams {
+  int nprob;
+  int tile_start[NPV + 1];
+  GemmProb<T> probs[NPV];
+};
+
+template <typename T, int BM, int BN, int MR, int NR>
+__global__ void __launch_bounds__(256) k_grouped_gemm_v(const __grid_constant__ GemmParams<T> gp) {
+  __shared__ T As[TK][BM + 1];
+  __shared__ T Bs[TK][BN + 1];
+  int lo = 0, hi = gp.nprob - 1;
+  const int tile = blockIdx.x;
+  while (lo < hi) {   // problem of this tile: last p with tile_start[p] <= tile
+    int mid = (lo + hi + 1) / 2;
+    if (gp.tile_start[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  const GemmProb<T>& P = gp.probs[lo];
+  const int local = tile - gp.tile_start[lo];
+  const int ntn = (P.N + BN - 1) / BN;
+  TileRef tr{lo, (local / ntn) * BM, (local % ntn) * BN};
+  gemm_tile<T, BM, BN, MR, NR>(P, tr, As, Bs);
+}
+
 constexpr int PMAX = 8;
 struct PermArgs {
   int nd;
@@ -117,6 +279,47 @@ inline unsigned grid_for(size_t n) {
 template <typename T>
 void grouped_gemm(const std::vector<GemmProb<T>>& probs, cudaStream_t s) {
   if (probs.empty()) return;
+  // by-value path: up to NPV problems per launch
+  size_t i0 = 0;
+  bool small = true;
+  {
+    size_t nonempty = 0;
+    for (auto& P : probs) nonempty += (P.M > 0 && P.N > 0);
+    small = nonempty <= (size_t)4 * NPV;
+  }
+  if (small) {
+    // shape classes: skinny problems (one side <= 16) use 128 x 16 or 16 x 128 tiles,
+    // the others 64 x 64
+    std::vector<GemmProb<T>> wide, skinny_n, skinny_m;
+    for (const auto& P0 : probs) {
+      if (P0.M <= 0 || P0.N <= 0) continue;
+      if (P0.N <= 16 && P0.M > 16) skinny_n.push_back(P0);
+      else if (P0.M <= 16 && P0.N > 16) skinny_m.push_back(P0);
+      else wide.push_back(P0);
+    }
+    auto launch = [&](const std::vector<GemmProb<T>>& L, int bm, int bn) {
+      GemmParams<T> gp;
+      size_t j = 0;
+      while (j < L.size()) {
+        gp.nprob = 0;
+        int tiles = 0;
+        for (; j < L.size() && gp.nprob < NPV; ++j) {
+          gp.tile_start[gp.nprob] = tiles;
+          gp.probs[gp.nprob++] = L[j];
+          tiles += ((L[j].M + bm - 1) / bm) * ((L[j].N + bn - 1) / bn);
+        }
+        gp.tile_start[gp.nprob] = tiles;
+        if (bn == 16) k_grouped_gemm_v<T, 128, 16, 8, 1><<<tiles, 256, 0, s>>>(gp);
+        else if (bm == 16) k_grouped_gemm_v<T, 16, 128, 1, 8><<<tiles, 256, 0, s>>>(gp);
+        else k_grouped_gemm_v<T, TM, TN, 4, 4><<<tiles, 256, 0, s>>>(gp);
+        PN_CUDA(cudaGetLastError());
+      }
+    };
+    launch(wide, TM, TN);
+    launch(skinny_n, 128, 16);
+    launch(skinny_m, 16, 128);
+    return;
+  }
   std::vector<TileRef> tiles;
   for (int p = 0; p < (int)probs.size(); ++p) {
     const auto& P = probs[p];
@@ -129,12 +332,9 @@ void grouped_gemm(const std::vector<GemmProb<T>>& probs, cudaStream_t s) {
   DBuf<TileRef> dt(tiles.size());
   dp.upload(probs.data(), probs.size(), s);
   dt.upload(tiles.data(), tiles.size(), s);
-  for (size_t t0 = 0; t0 < tiles.size(); t0 += 2147483647u) {
-    size_t nt = std::min<size_t>(tiles.size() - t0, 2147483647u);
-    k_grouped_gemm<T><<<(unsigned)nt, 256, 0, s>>>(dp.get(), dt.get() + t0);
-  }
+  k_grouped_gemm<T><<<(unsigned)tiles.size(), 256, 0, s>>>(dp.get(), dt.get());
   PN_CUDA(cudaGetLastError());
-  PN_CUDA(cudaStreamSynchronize(s));   // the descriptor buffers are freed on return
+  // the descriptor buffers go back to this thread's cache; later reuse is ordered on the same stream
 }
 
 template <typename T>
@@ -222,7 +422,6 @@ void contract(const std::map<char, int64_t>& dims, TView<T> A, TView<T> B, TView
     std::vector<int> perm;
     for (char c : C.idx) perm.push_back((int)cord.find(c));
     permute<T>(pc, C.p, din, perm, alpha, beta, s);
-    PN_CUDA(cudaStreamSynchronize(s));
   }
 }
 

@@ -335,7 +335,6 @@ struct Dav {
     dC.upload(C.data(), C.size(), s);
     k_combine<<<gsz((size_t)nq * L), 256, 0, s>>>(out, V, dC.get(), m, nq, L, beta);
     PN_CUDA(cudaGetLastError());
-    PN_CUDA(cudaStreamSynchronize(s));
   }
   void symdiag(double* x) {
     if (nd) k_symdiag<<<nd, 256, 0, s>>>(x, dOffs.get(), dNs.get(), nd);
