@@ -180,6 +180,40 @@ int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, co
 int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* opts, void* cuda_stream,
                        double* energies, double* res_norms, int* iters, int* converged);
 
+/* Serving (continuous batching of excited-state solves).  A server owns two
+ * threads: a builder that admits queued requests in arrival order when their
+ * estimated setup footprint fits the HBM budget (0 = no budget) and runs
+ * pno_build on its own stream, and a solver that keeps every built request's
+ * PNOs, operator blocks and Davidson subspace resident and runs lockstep
+ * Davidson rounds over all of them through one merged sigma program (a CUDA
+ * graph).  Requests that finish building join at the next round boundary;
+ * finished ones leave and free their memory, so requests that arrive while
+ * others run overlap with them on the device.  At most max_active requests
+ * are solved together. */
+typedef struct pnoeom_server pnoeom_server;
+enum { PNOEOM_REQ_QUEUED = 0, PNOEOM_REQ_BUILDING = 1, PNOEOM_REQ_RUNNING = 2, PNOEOM_REQ_DONE = 3,
+       PNOEOM_REQ_FAILED = 4 };
+int pnoeom_server_create(pnoeom_ctx* ctx, size_t hbm_budget_bytes, int max_active, pnoeom_server** out);
+/* Stops both threads (queued requests are not run) and frees all state. */
+void pnoeom_server_destroy(pnoeom_server* srv);
+/* Queue one solve.  Inputs must be host memory; they are copied.  A request
+ * whose estimated footprint exceeds the budget fails at once with
+ * PNOEOM_ERR_NOMEM (visible through poll). */
+int pnoeom_server_submit(pnoeom_server* srv, const pnoeom_system* sys, const pnoeom_opts* opts, int64_t* id);
+/* Non-blocking status of request `id`; when DONE, energies and res_norms
+ * (nroots_solve each), iters and sigma_evals are filled (any may be NULL).
+ * times (4 doubles, may be NULL): submitted, admitted, built, finished, in
+ * seconds since the server started (0 when not reached). */
+int pnoeom_server_poll(pnoeom_server* srv, int64_t id, int* status, double* energies, double* res_norms,
+                       int* iters, int64_t* sigma_evals, double* times);
+/* Block until request `id` is DONE or FAILED, or timeout_s elapses
+ * (PNOEOM_ERR_TIMEOUT). */
+int pnoeom_server_wait(pnoeom_server* srv, int64_t id, double timeout_s);
+/* Counters: device bytes held for admitted requests, queued / building-or-built
+ * / running requests, lockstep rounds, program merges, sigma-evals done. */
+int pnoeom_server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int* running, int64_t* rounds,
+                        int64_t* merges, int64_t* sigma_evals);
+
 /* Eigenvectors of the last davidson_solve on this handle, as packed FP64
  * vectors on the host (nroots_solve * vec_len doubles). */
 int pno_get_eigenvectors(const pnoeom_pno* pno, double* X);

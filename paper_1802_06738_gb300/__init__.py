@@ -50,7 +50,9 @@ EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", 
            "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
            "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds",
            "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info",
-           "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve"]
+           "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve",
+           "pnoeom_server_create", "pnoeom_server_destroy", "pnoeom_server_submit", "pnoeom_server_poll",
+           "pnoeom_server_wait", "pnoeom_server_stats"]
 
 
 def lib():
@@ -75,6 +77,13 @@ def lib():
         L.pnoeom_batch_destroy.argtypes = [vp]; L.pnoeom_batch_destroy.restype = None
         L.pnoeom_batch_sigma.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
         L.pnoeom_batch_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip, ip]
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        L.pnoeom_server_create.argtypes = [vp, ctypes.c_size_t, i, ctypes.POINTER(vp)]
+        L.pnoeom_server_destroy.argtypes = [vp]; L.pnoeom_server_destroy.restype = None
+        L.pnoeom_server_submit.argtypes = [vp, ctypes.POINTER(System), ctypes.POINTER(Opts), i64p]
+        L.pnoeom_server_poll.argtypes = [vp, ctypes.c_int64, ip, dp, dp, ip, i64p, dp]
+        L.pnoeom_server_wait.argtypes = [vp, ctypes.c_int64, d]
+        L.pnoeom_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ip, ip, i64p, i64p, i64p]
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
         L.pno_get_cis.argtypes = [vp, dp]
@@ -302,3 +311,65 @@ class Batch:
         _check(lib().pnoeom_batch_solve(self.ctx.h, self.h, ctypes.byref(opts), _stream_ptr(stream), _dptr(e), _dptr(rn),
                                         it, cv), allow=(ERR_NOT_CONVERGED,))
         return e, rn, list(it), [bool(x) for x in cv]
+
+
+QUEUED, BUILDING, RUNNING, DONE, FAILED = 0, 1, 2, 3, 4
+
+
+class Server:
+    """pnoeom_server_*: continuous-batching request loop (native threads)."""
+
+    def __init__(self, ctx, hbm_budget_bytes=0, max_active=16):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        _check(lib().pnoeom_server_create(ctx.h, hbm_budget_bytes, max_active, ctypes.byref(h)))
+        self.h = h
+        self.nroots = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pnoeom_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, eps, B, o, opts, t1=None, t2=None):
+        import numpy as np
+        eps = np.ascontiguousarray(eps, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        t1 = None if t1 is None else np.ascontiguousarray(t1, dtype=np.float64)
+        t2 = None if t2 is None else np.ascontiguousarray(t2, dtype=np.float64)
+        ptr = lambda x: None if x is None else x.ctypes.data
+        sysd = System(o, len(eps) - o, B.shape[0], ptr(eps), ptr(B), ptr(t1), ptr(t2), HOST)
+        rid = ctypes.c_int64()
+        _check(lib().pnoeom_server_submit(self.h, ctypes.byref(sysd), ctypes.byref(opts), ctypes.byref(rid)))
+        self.nroots[rid.value] = opts.nroots_solve
+        return rid.value
+
+    def poll(self, rid):
+        """dict(status, energies, res_norms, iters, sigma_evals, times, error)."""
+        import numpy as np
+        n = self.nroots.get(rid, 16)
+        st, it, se = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        e, rn, tm = np.full(n, np.nan), np.full(n, np.nan), np.zeros(4)
+        rc = lib().pnoeom_server_poll(self.h, rid, ctypes.byref(st), _dptr(e), _dptr(rn), ctypes.byref(it),
+                                      ctypes.byref(se), _dptr(tm))
+        err = None if rc == OK else (rc, lib().pnoeom_last_error().decode())
+        if rc != OK and st.value != FAILED:
+            raise PnoeomError(rc, err[1])
+        return dict(status=st.value, energies=e, res_norms=rn, iters=it.value, sigma_evals=se.value, times=tm, error=err)
+
+    def wait(self, rid, timeout_s=600.0):
+        return lib().pnoeom_server_wait(self.h, rid, timeout_s)
+
+    def stats(self):
+        ub, q, r = ctypes.c_size_t(), ctypes.c_int(), ctypes.c_int()
+        ro, me, se = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pnoeom_server_stats(self.h, ctypes.byref(ub), ctypes.byref(q), ctypes.byref(r), ctypes.byref(ro),
+                                         ctypes.byref(me), ctypes.byref(se)))
+        return dict(used_bytes=ub.value, queued=q.value, running=r.value, rounds=ro.value, merges=me.value,
+                    sigma_evals=se.value)

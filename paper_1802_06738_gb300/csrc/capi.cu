@@ -2,6 +2,8 @@
 #include "pno.cuh"
 #include <cmath>
 #include <functional>
+#include <chrono>
+#include <mutex>
 
 namespace pnoeom { int small_eig(int n, const double* A, double* wr, double* wi, double* VR); }
 
@@ -244,6 +246,45 @@ int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* 
     return PNOEOM_ERR_NOT_CONVERGED;
   }
   return rc;
+}
+
+int pnoeom_server_create(pnoeom_ctx* ctx, size_t hbm_budget_bytes, int max_active, pnoeom_server** out) {
+  return guard([&] {
+    PN_CHECK(ctx && out && max_active >= 1 && max_active <= pnoeom::MAX_SYS, PNOEOM_ERR_INVALID_ARG, "bad arguments");
+    auto* S = new pnoeom_server();
+    S->device = ctx->device;
+    S->budget = hbm_budget_bytes;
+    S->max_active = max_active;
+    pnoeom::server_start(S);
+    *out = S;
+  });
+}
+
+void pnoeom_server_destroy(pnoeom_server* srv) {
+  if (!srv) return;
+  pnoeom::server_stop(srv);
+  delete srv;
+}
+
+int pnoeom_server_submit(pnoeom_server* srv, const pnoeom_system* sys, const pnoeom_opts* opts, int64_t* id) {
+  return guard([&] {
+    PN_CHECK(srv && id, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    *id = pnoeom::server_submit(srv, sys, opts);
+  });
+}
+
+int pnoeom_server_poll(pnoeom_server* srv, int64_t id, int* status, double* energies, double* res_norms, int* iters,
+                       int64_t* sigma_evals, double* times) {
+  return guard([&] { pnoeom::server_poll(srv, id, status, energies, res_norms, iters, sigma_evals, times); });
+}
+
+int pnoeom_server_wait(pnoeom_server* srv, int64_t id, double timeout_s) {
+  return guard([&] { pnoeom::server_wait(srv, id, timeout_s); });
+}
+
+int pnoeom_server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int* running, int64_t* rounds,
+                        int64_t* merges, int64_t* sigma_evals) {
+  return guard([&] { pnoeom::server_stats(srv, used_bytes, queued, running, rounds, merges, sigma_evals); });
 }
 
 int pno_get_eigenvectors(const pnoeom_pno* pno, double* X) {

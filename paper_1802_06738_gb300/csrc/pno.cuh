@@ -3,6 +3,13 @@
 #include "common.cuh"
 #include "engine.cuh"
 #include "sigma_prog.cuh"
+#include <functional>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
 
 namespace pnoeom {
 constexpr int NGROUP_CAND = 4;
@@ -98,9 +105,37 @@ struct pnoeom_batch {
   ~pnoeom_batch() { if (exec) cudaGraphExecDestroy(exec); }
 };
 
+namespace pnoeom { struct Request; }
+struct pnoeom_server {
+  int device = 0;
+  size_t budget = 0;
+  int max_active = 0;
+  double t0 = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::map<int64_t, std::shared_ptr<pnoeom::Request>> reqs;
+  std::deque<std::shared_ptr<pnoeom::Request>> queued, built;
+  size_t used = 0;          // estimated or measured device bytes of admitted requests
+  int64_t next_id = 1;
+  bool stop = false;
+  int64_t rounds = 0, merges = 0, total_sigma_evals = 0;
+  std::thread builder, solver;
+  std::string fatal;
+};
+
 namespace pnoeom {
 void autotune(pnoeom_pno* P, cudaStream_t s);
 void batch_build(pnoeom_batch* B, cudaStream_t s);
+void batch_merge(pnoeom_batch* B, cudaStream_t s, bool tune);
+int guard_call(const std::function<void()>& f);
+void server_start(pnoeom_server* S);
+void server_stop(pnoeom_server* S);
+int64_t server_submit(pnoeom_server* S, const pnoeom_system* sys, const pnoeom_opts* opts);
+void server_poll(pnoeom_server* srv, int64_t id, int* status, double* energies, double* res_norms, int* iters,
+                 int64_t* sigma_evals, double* times);
+void server_wait(pnoeom_server* srv, int64_t id, double timeout_s);
+void server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int* running, int64_t* rounds,
+                  int64_t* merges, int64_t* sigma_evals);
 void batch_sigma(pnoeom_batch* B, const int* nvec, const void* const* r, void* const* out, int prec, cudaStream_t s);
 void batch_solve(pnoeom_batch* B, const pnoeom_opts* opts, cudaStream_t s, double* energies, double* res_norms,
                  int* iters, int* converged);

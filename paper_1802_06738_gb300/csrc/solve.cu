@@ -4,6 +4,12 @@
 #include <cmath>
 #include <complex>
 #include <memory>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
 
 namespace pnoeom {
 
@@ -382,6 +388,7 @@ struct DavState {
   DBuf<double> V, S, X, R;
   DBuf<float> fin, fout;    // FP32 copies of the pending vectors and their sigma
   int m = 0, nr = 0, it = 0, p0 = 0, p1 = 0;
+  int64_t sigma_evals = 0;
   bool done = false, converged = false;
   std::vector<double> w, rn, w_old;
 
@@ -525,8 +532,28 @@ void drive(std::vector<DavState*>& st, int chunk, Eval&& eval) {
         }
       if (!need) continue;
       eval(st, nv, prec);
-      for (size_t k = 0; k < st.size(); ++k) st[k]->p0 += nv[k];
+      for (size_t k = 0; k < st.size(); ++k) { st[k]->p0 += nv[k]; st[k]->sigma_evals += nv[k]; }
     }
+  }
+}
+
+// One round of the lockstep driver (continuous batching): states with an empty
+// pending range iterate, then every state's pending chunk is evaluated.
+template <typename Eval>
+void drive_round(std::vector<DavState*>& st, int chunk, Eval&& eval) {
+  for (DavState* d : st)
+    while (!d->done && d->p0 >= d->p1) d->iterate();
+  for (int prec : {PNOEOM_FP32, PNOEOM_FP64}) {
+    std::vector<int> nv(st.size(), 0);
+    bool need = false;
+    for (size_t k = 0; k < st.size(); ++k)
+      if (!st[k]->done && st[k]->prec == prec && st[k]->p0 < st[k]->p1) {
+        nv[k] = std::min(chunk, st[k]->p1 - st[k]->p0);
+        need = true;
+      }
+    if (!need) continue;
+    eval(st, nv, prec);
+    for (size_t k = 0; k < st.size(); ++k) { st[k]->p0 += nv[k]; st[k]->sigma_evals += nv[k]; }
   }
 }
 
@@ -584,9 +611,12 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
 
 // Merge the members' programs: every problem keeps its offsets (relative to its
 // own system's buffers) and gets the member index as its system index.
-void batch_build(pnoeom_batch* B, cudaStream_t s) {
+void batch_build(pnoeom_batch* B, cudaStream_t s) { batch_merge(B, s, true); }
+
+void batch_merge(pnoeom_batch* B, cudaStream_t s, bool tune) {
   const int n = (int)B->members.size();
   PN_CHECK(n >= 1 && n <= MAX_SYS, PNOEOM_ERR_INVALID_ARG, "a batch holds 1.." + std::to_string(MAX_SYS) + " systems");
+  B->prog = Program();
   Program& G = B->prog;
   for (int k = 0; k < n; ++k) {
     const Program& Pg = B->members[k]->prog;
@@ -616,6 +646,9 @@ void batch_build(pnoeom_batch* B, cudaStream_t s) {
   G.upload(s, &B->footprint);
   B->w64.resize(n);
   B->w32.resize(n);
+  G.group_choice = B->members[0]->prog.group_choice;
+  G.rpc_choice = B->members[0]->prog.rpc_choice;
+  if (!tune) return;
   // autotune the merged program: FP32 sigma of nroots_sa vectors per member
   std::vector<DBuf<float>> r(n), o(n);
   std::vector<const void*> rp(n);
@@ -739,5 +772,308 @@ void batch_solve(pnoeom_batch* B, const pnoeom_opts* opts, cudaStream_t s, doubl
     converged[k] = st[k]->converged ? 1 : 0;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of Davidson solves (a12)
+
+struct Request {
+  int64_t id = 0;
+  int o = 0, v = 0, naux = 0;
+  std::vector<double> eps, B, t1, t2;
+  bool has_t1 = false, has_t2 = false;
+  pnoeom_opts opts{};
+  int status = PNOEOM_REQ_QUEUED;
+  int error = 0;
+  std::string message;
+  size_t est_bytes = 0, resident_bytes = 0;
+  double t_submit = 0, t_admit = 0, t_built = 0, t_done = 0;
+  pnoeom_pno* pno = nullptr;
+  std::unique_ptr<DavState> dav;
+  std::vector<double> energies, res_norms;
+  int iters = 0;
+  int64_t sigma_evals = 0;
+};
+
+static double wall_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Upper estimate of the device memory a build of (o, v, naux) needs at its peak:
+// the DF factors, the v^3 o integral blocks and their projected copies, and the
+// o^2 v^2 amplitude-sized intermediates.
+size_t estimate_build_bytes(int o, int v, int naux) {
+  const double O = o, Vv = v, nmo = o + v;
+  return (size_t)(8.0 * (2.0 * naux * nmo * nmo + 6.0 * O * Vv * Vv * Vv + 16.0 * O * O * Vv * Vv) + 256e6);
+}
+
+}  // namespace pnoeom
+
+
+namespace pnoeom {
+
+static void server_builder(pnoeom_server* S) {
+  cudaSetDevice(S->device);
+  pnoeom_ctx bctx;
+  bctx.device = S->device;
+  if (cusolverDnCreate(&bctx.solver) != CUSOLVER_STATUS_SUCCESS) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->fatal = "builder: cusolverDnCreate failed";
+    S->stop = true;
+    S->cv.notify_all();
+    return;
+  }
+  cudaStream_t bs;
+  cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+  for (;;) {
+    std::shared_ptr<Request> r;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] {
+        if (S->stop) return true;
+        for (auto& q : S->queued)
+          if (!S->budget || S->used + q->est_bytes <= S->budget) return true;
+        return false;
+      });
+      if (S->stop) break;
+      for (auto it = S->queued.begin(); it != S->queued.end(); ++it)   // oldest request that fits
+        if (!S->budget || S->used + (*it)->est_bytes <= S->budget) { r = *it; S->queued.erase(it); break; }
+      if (!r) continue;
+      S->used += r->est_bytes;
+      r->status = PNOEOM_REQ_BUILDING;
+      r->t_admit = wall_s() - S->t0;
+    }
+    pnoeom_system sys{r->o, r->v, r->naux, r->eps.data(), r->B.data(), r->has_t1 ? r->t1.data() : nullptr,
+                      r->has_t2 ? r->t2.data() : nullptr, PNOEOM_HOST};
+    auto* P = new pnoeom_pno();
+    int code = guard_call([&] { build_system(&bctx, &sys, &r->opts, bs, P); });
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->used -= r->est_bytes;
+    r->B.clear(); r->B.shrink_to_fit(); r->t2.clear(); r->t2.shrink_to_fit();
+    if (code != PNOEOM_OK) {
+      delete P;
+      r->status = PNOEOM_REQ_FAILED;
+      r->error = code;
+      r->message = "build failed";
+      r->t_done = wall_s() - S->t0;
+    } else {
+      r->pno = P;
+      r->resident_bytes = P->footprint;
+      S->used += r->resident_bytes;
+      r->t_built = wall_s() - S->t0;
+      S->built.push_back(r);
+    }
+    S->cv.notify_all();
+  }
+  cudaStreamDestroy(bs);
+  cusolverDnDestroy(bctx.solver);
+}
+
+static void server_solver(pnoeom_server* S) {
+  cudaSetDevice(S->device);
+  cudaStream_t ss;
+  cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+  std::vector<std::shared_ptr<Request>> active;
+  pnoeom_batch B;
+  bool dirty = true;
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv.wait(lk, [&] { return S->stop || !active.empty() || !S->built.empty(); });
+      if (S->stop) break;
+      while (!S->built.empty() && (int)active.size() < S->max_active) {   // join at the round boundary
+        auto r = S->built.front();
+        S->built.pop_front();
+        r->status = PNOEOM_REQ_RUNNING;
+        active.push_back(r);
+        dirty = true;
+      }
+    }
+    // Davidson states of new members (outside the lock: device work)
+    for (auto& r : active) {
+      if (r->dav) continue;
+      int code = guard_call([&] { r->dav.reset(new DavState(r->pno, &r->opts, ss)); });
+      if (code != PNOEOM_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r->status = PNOEOM_REQ_FAILED; r->error = code; r->message = "solver setup failed";
+      }
+    }
+    // drop failed ones
+    active.erase(std::remove_if(active.begin(), active.end(), [&](auto& r) {
+                   if (r->status != PNOEOM_REQ_FAILED) return false;
+                   std::lock_guard<std::mutex> lk(S->mu);
+                   S->used -= r->resident_bytes;
+                   delete r->pno; r->pno = nullptr;
+                   r->t_done = wall_s() - S->t0;
+                   dirty = true;
+                   S->cv.notify_all();
+                   return true;
+                 }),
+                 active.end());
+    if (active.empty()) continue;
+    int code = guard_call([&] {
+      if (dirty) {
+        B.members.clear();
+        for (auto& r : active) B.members.push_back(r->pno);
+        if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+        batch_merge(&B, ss, false);
+        dirty = false;
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->merges;
+      }
+      std::vector<DavState*> st;
+      for (auto& r : active) st.push_back(r->dav.get());
+      int chunk = 1;
+      for (auto& r : active) chunk = std::max(chunk, r->opts.nroots_solve);
+      drive_round(st, chunk, [&](std::vector<DavState*>& xs, const std::vector<int>& nv, int prec) {
+        for (size_t k = 0; k < xs.size(); ++k) {
+          if (!nv[k]) continue;
+          const size_t need = (size_t)nv[k] * xs[k]->P->work_len;
+          if (prec == PNOEOM_FP64) { if (B.w64[k].n < need) B.w64[k].alloc(need); }
+          else {
+            if (B.w32[k].n < need) B.w32[k].alloc(need);
+            const size_t len = (size_t)nv[k] * xs[k]->L;
+            if (xs[k]->fin.n < len) { xs[k]->fin.alloc(len); xs[k]->fout.alloc(len); }
+          }
+        }
+        graph_launch(&B, ss, [&] { eval_states(B.prog, xs, nv, prec, &B.w64, &B.w32, ss, nullptr); });
+      });
+      // retire finished requests
+      std::vector<std::shared_ptr<Request>> keep;
+      for (auto& r : active) {
+        if (!r->dav->done) { keep.push_back(r); continue; }
+        const int nr = r->opts.nroots_solve;
+        r->energies.assign(nr, NAN); r->res_norms.assign(nr, NAN);
+        r->dav->results(r->energies.data(), r->res_norms.data(), &r->iters);
+        r->sigma_evals = r->dav->sigma_evals;
+        const bool ok = r->dav->converged;
+        r->dav.reset();
+        delete r->pno; r->pno = nullptr;
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->used -= r->resident_bytes;
+        S->total_sigma_evals += r->sigma_evals;
+        r->status = ok ? PNOEOM_REQ_DONE : PNOEOM_REQ_FAILED;
+        if (!ok) { r->error = PNOEOM_ERR_NOT_CONVERGED; r->message = "Davidson did not converge"; }
+        r->t_done = wall_s() - S->t0;
+        dirty = true;
+        S->cv.notify_all();
+      }
+      if (keep.size() != active.size()) pool_trim();   // return retired memory to CUDA
+      active.swap(keep);
+      std::lock_guard<std::mutex> lk(S->mu);
+      ++S->rounds;
+    });
+    if (code != PNOEOM_OK) {   // a round failed: fail every active request
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto& r : active) {
+        r->status = PNOEOM_REQ_FAILED; r->error = code; r->message = "solver round failed";
+        r->dav.reset(); delete r->pno; r->pno = nullptr;
+        S->used -= r->resident_bytes;
+        r->t_done = wall_s() - S->t0;
+      }
+      active.clear();
+      dirty = true;
+      S->cv.notify_all();
+    }
+  }
+  for (auto& r : active) { r->dav.reset(); delete r->pno; r->pno = nullptr; }
+  if (B.exec) { cudaGraphExecDestroy(B.exec); B.exec = nullptr; }
+  cudaStreamDestroy(ss);
+}
+
+void server_start(pnoeom_server* S) {
+  S->t0 = wall_s();
+  S->builder = std::thread(server_builder, S);
+  S->solver = std::thread(server_solver, S);
+}
+
+void server_stop(pnoeom_server* S) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->builder.joinable()) S->builder.join();
+  if (S->solver.joinable()) S->solver.join();
+}
+
+int64_t server_submit(pnoeom_server* S, const pnoeom_system* sys, const pnoeom_opts* opts) {
+  PN_CHECK(sys && opts && sys->eps && sys->B && sys->mem_space == PNOEOM_HOST, PNOEOM_ERR_INVALID_ARG,
+           "server requests take host inputs");
+  PN_CHECK(sys->o >= 1 && sys->v >= 1 && sys->naux >= 1, PNOEOM_ERR_INVALID_ARG, "o, v and naux must be positive");
+  auto r = std::make_shared<Request>();
+  const size_t nmo = sys->o + sys->v;
+  r->o = sys->o; r->v = sys->v; r->naux = sys->naux;
+  r->eps.assign(sys->eps, sys->eps + nmo);
+  r->B.assign(sys->B, sys->B + (size_t)sys->naux * nmo * nmo);
+  if (sys->t1) { r->has_t1 = true; r->t1.assign(sys->t1, sys->t1 + (size_t)sys->o * sys->v); }
+  if (sys->t2) { r->has_t2 = true; r->t2.assign(sys->t2, sys->t2 + (size_t)sys->o * sys->o * sys->v * sys->v); }
+  r->opts = *opts;
+  r->est_bytes = estimate_build_bytes(sys->o, sys->v, sys->naux);
+  std::lock_guard<std::mutex> lk(S->mu);
+  PN_CHECK(S->fatal.empty(), PNOEOM_ERR_CUDA, S->fatal);
+  r->id = S->next_id++;
+  r->t_submit = wall_s() - S->t0;
+  S->reqs[r->id] = r;
+  if (S->budget && r->est_bytes > S->budget) {   // can never be admitted
+    r->status = PNOEOM_REQ_FAILED;
+    r->error = PNOEOM_ERR_NOMEM;
+    r->message = "estimated footprint " + std::to_string(r->est_bytes) + " bytes exceeds the server budget";
+    r->t_done = r->t_submit;
+  } else {
+    S->queued.push_back(r);
+  }
+  S->cv.notify_all();
+  return r->id;
+}
+
+void server_poll(pnoeom_server* srv, int64_t id, int* status, double* energies, double* res_norms, int* iters,
+                 int64_t* sigma_evals, double* times) {
+    PN_CHECK(srv, PNOEOM_ERR_INVALID_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    PN_CHECK(it != srv->reqs.end(), PNOEOM_ERR_INVALID_ARG, "unknown request id");
+    const auto& r = *it->second;
+    if (status) *status = r.status;
+    if (r.status == PNOEOM_REQ_DONE) {
+      for (size_t q = 0; q < r.energies.size(); ++q) {
+        if (energies) energies[q] = r.energies[q];
+        if (res_norms) res_norms[q] = r.res_norms[q];
+      }
+      if (iters) *iters = r.iters;
+      if (sigma_evals) *sigma_evals = r.sigma_evals;
+    }
+    if (times) { times[0] = r.t_submit; times[1] = r.t_admit; times[2] = r.t_built; times[3] = r.t_done; }
+    if (r.status == PNOEOM_REQ_FAILED)
+      throw Error(r.error ? r.error : PNOEOM_ERR_CUDA, "request failed: " + r.message);
+  }
+
+void server_wait(pnoeom_server* srv, int64_t id, double timeout_s) {
+    PN_CHECK(srv, PNOEOM_ERR_INVALID_ARG, "NULL server");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    PN_CHECK(it != srv->reqs.end(), PNOEOM_ERR_INVALID_ARG, "unknown request id");
+    auto r = it->second;
+    bool ok = srv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+      return r->status == PNOEOM_REQ_DONE || r->status == PNOEOM_REQ_FAILED || !srv->fatal.empty();
+    });
+    PN_CHECK(ok, PNOEOM_ERR_TIMEOUT, "request " + std::to_string(id) + " not finished within the timeout");
+  }
+
+void server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int* running, int64_t* rounds,
+                  int64_t* merges, int64_t* sigma_evals) {
+    PN_CHECK(srv, PNOEOM_ERR_INVALID_ARG, "NULL server");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (used_bytes) *used_bytes = srv->used;
+    int q = 0, r = 0;
+    for (auto& kv : srv->reqs) {
+      q += kv.second->status == PNOEOM_REQ_QUEUED;
+      r += kv.second->status == PNOEOM_REQ_BUILDING || kv.second->status == PNOEOM_REQ_RUNNING;
+    }
+    if (queued) *queued = q;
+    if (running) *running = r;
+    if (rounds) *rounds = srv->rounds;
+    if (merges) *merges = srv->merges;
+    if (sigma_evals) *sigma_evals = srv->total_sigma_evals;
+  }
 
 }  // namespace pnoeom
