@@ -46,6 +46,13 @@ def parse():
     ap.add_argument("--workload", default="medium", choices=list(WORKLOADS))
     ap.add_argument("--solves", type=int, default=3, help="repeated Davidson solves for latency percentiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="sigma", choices=["sigma", "batched", "serving"],
+                    help="sigma: medium-workload sigma throughput (default); batched: many systems in one "
+                         "launch sequence; serving: Poisson request stream through the continuous-batching server")
+    ap.add_argument("--nsys", type=int, default=16, help="batched: number of systems (sample of the 64-system workload)")
+    ap.add_argument("--omax", type=int, default=14, help="batched/serving: cap on o of the sampled systems")
+    ap.add_argument("--nreq", type=int, default=40, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
     return ap.parse_args()
 
 
@@ -182,11 +189,137 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, ws, rank, local):
+    """Many systems in one launch sequence (a sample of the 64-system workload)."""
+    import numpy as np
+    import torch
+    import paper_1802_06738_gb300 as pkg
+    from synthetic import make_system, batched_sizes
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        pkg.build()
+    barrier(ws)
+    sizes = [x for x in batched_sizes(64, 4) if x[0] <= args.omax][: args.nsys]
+    ctx = pkg.Context(local)
+    stream = torch.cuda.Stream(dev)
+    h = stream.cuda_stream
+    t0 = time.perf_counter()
+    pnos = []
+    for (o, v, naux, seed) in sizes:
+        sd = make_system(o, v, naux, seed + 1000 * rank)
+        pnos.append(pkg.PNO(ctx, sd["eps"], sd["B"], o, opts=pkg.make_opts(t_pno=1e-7, nroots=6, precision=pkg.FP32,
+                                                                          refine_fp64=1), stream=h))
+    build_s = time.perf_counter() - t0
+    batch = pkg.Batch(ctx, pnos, stream=h)
+    nr = 6
+    rng = np.random.default_rng(3)
+    rs = [torch.tensor(rng.standard_normal((nr, p.length)), dtype=torch.float32, device=dev) for p in pnos]
+    outs = [torch.empty_like(r) for r in rs]
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            batch.sigma(rs, outs, precision=pkg.FP32, stream=h)
+        stream.synchronize()
+        barrier(ws)
+        ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+        with Clocks(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                batch.sigma(rs, outs, precision=pkg.FP32, stream=h)
+            ev1.record(stream)
+            stream.synchronize()
+    t_sig = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    # lockstep batched solve (mixed + FP64 refinement) vs the same systems one after another
+    t0 = time.perf_counter()
+    e, rn, it, cv = batch.solve(pkg.make_opts(t_pno=1e-7, nroots=nr, precision=pkg.FP32, refine_fp64=1), stream=h)
+    t_batch_solve = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for p in pnos:
+        p.davidson_solve(pkg.make_opts(t_pno=1e-7, nroots=nr, precision=pkg.FP32, refine_fp64=1), stream=h)
+    t_serial_solve = time.perf_counter() - t0
+    if rank != 0:
+        return
+    line = {"metric": "batched PNO-EOM-CCSD sigma-evals/s (all systems in one launch sequence, mixed FP32 sigma)",
+            "value": ws * len(pnos) * nr * args.steps / t_sig, "unit": "sigma-evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_sig / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched sample: {len(pnos)} systems of the 64-system stream (o <= {args.omax}), "
+                                   "v=10o, naux=3v, 6 roots, T_PNO=1e-7, MP1 T2",
+                       "o_values": [x[0] for x in sizes], "vec_len_total": int(sum(p.length for p in pnos))},
+            "solve": {"batched_lockstep_s": t_batch_solve, "one_after_another_s": t_serial_solve,
+                      "converged": int(sum(cv)), "iterations": it, "build_total_s": build_s},
+            "clocks": clk.summary(), "gpu_launches": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, ws, rank, local):
+    """Poisson request stream through the continuous-batching server."""
+    import numpy as np
+    import torch
+    import paper_1802_06738_gb300 as pkg
+    from synthetic import make_system, poisson_requests
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        pkg.build()
+    barrier(ws)
+    reqs = [r for r in poisson_requests(600, args.rate, 5) if r["o"] <= args.omax][: args.nreq]
+    # rescale arrival times to keep the stream's rate after the size filter
+    gaps = np.random.default_rng(50).exponential(1.0 / args.rate, size=len(reqs))
+    arrivals = np.cumsum(gaps)
+    systems = [make_system(r["o"], r["v"], r["naux"], r["seed"] + 1000 * rank) for r in reqs]
+    ctx = pkg.Context(local)
+    srv = pkg.Server(ctx, hbm_budget_bytes=200 << 30, max_active=32)
+    barrier(ws)
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        ids = []
+        for k, r in enumerate(reqs):
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            opts = pkg.make_opts(t_pno=r["t_pno"], nroots=r["nroots"], precision=pkg.FP32, refine_fp64=1)
+            ids.append(srv.submit(systems[k]["eps"], systems[k]["B"], r["o"], opts))
+        for rid in ids:
+            srv.wait(rid, 3600.0)
+        wall = time.perf_counter() - t0
+    res = [srv.poll(rid) for rid in ids]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([x["times"][3] - x["times"][0] for x in res])
+    queue = np.array([x["times"][1] - x["times"][0] for x in res])
+    build = np.array([x["times"][2] - x["times"][1] for x in res])
+    solve = np.array([x["times"][3] - x["times"][2] for x in res])
+    done = sum(1 for x in res if x["status"] == pkg.DONE)
+    sev = sum(x["sigma_evals"] for x in res)
+    wall = max_over_ranks(wall, ws, dev)
+    if rank != 0:
+        return
+    pct = lambda a: {"p50_s": float(np.percentile(a, 50)), "p99_s": float(np.percentile(a, 99))}
+    line = {"metric": "served PNO-EOM-CCSD solves: latency p50/p99 and sigma-evals/s (mixed FP32 sigma + FP64 refinement)",
+            "value": ws * sev / wall, "unit": "sigma-evals/s", "n_gpus": ws, "steps": len(reqs), "warmup": 0,
+            "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving sample: {len(reqs)} requests of the Poisson stream (o <= {args.omax}), "
+                                   f"rate {args.rate}/s, v=10o, naux=3v, roots in {{3,6,10}}, T_PNO in {{1e-6,1e-7}}",
+                       "o_values": [r["o"] for r in reqs]},
+            "latency": pct(lat), "queueing": pct(queue), "build": pct(build), "solve": pct(solve),
+            "offered_rate_per_s": args.rate, "achieved_rate_per_s": len(reqs) / wall, "completed": done,
+            "server": st, "clocks": clk.summary(), "gpu_launches": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.mode == "batched":
+        run_batched(args, ws, rank, local)
+        return
+    if args.mode == "serving":
+        run_serving(args, ws, rank, local)
         return
     import numpy as np
     import torch

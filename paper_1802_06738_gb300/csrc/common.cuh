@@ -2,6 +2,7 @@
 // the device context (stream + cuSOLVER handle).
 #pragma once
 #include <cuda_runtime.h>
+#include <mutex>
 #include <cusolverDn.h>
 #include <cstdio>
 #include <cstdint>
@@ -42,10 +43,13 @@ struct Error : std::runtime_error {
 // Per-host-thread caching device allocator.  Freed blocks are kept and reused
 // by later allocations of the same thread; every thread of the library keeps to
 // one stream for its device work, so a reused block is stream-ordered after the
-// work that used it before.  trim() returns the cache to CUDA.
+// work that used it before.  trim() frees the calling thread's cached blocks; the caller must first
+// synchronise the stream its device work runs on.  Allocation and trimming
+// never overlap a CUDA-graph capture of another thread (capture_mutex).
 void* pool_get(size_t bytes);
 void pool_put(void* p, size_t bytes);
 void pool_trim();
+std::recursive_mutex& capture_mutex();
 
 // Owning device buffer (cached allocator, see pool_get).  Counts bytes into a shared
 // footprint counter so handles can report their device footprint.

@@ -12,6 +12,8 @@ namespace {
 struct ThreadPool {
   std::multimap<size_t, void*> free_blocks;
   ~ThreadPool() {
+    if (free_blocks.empty()) return;
+    std::lock_guard<std::recursive_mutex> lk(capture_mutex());
     for (auto& b : free_blocks) cudaFree(b.second);
   }
 };
@@ -38,6 +40,11 @@ void StageTimer::mark(const char* what) {
   t0 = t;
 }
 
+std::recursive_mutex& capture_mutex() {
+  static std::recursive_mutex m;
+  return m;
+}
+
 void* pool_get(size_t bytes) {
   const size_t sz = round_size(bytes);
   auto& fb = t_pool.free_blocks;
@@ -47,11 +54,14 @@ void* pool_get(size_t bytes) {
     fb.erase(it);
     return p;
   }
+  std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, sz);
-  if (e != cudaSuccess) {   // out of memory: return the cache to CUDA and retry once
+  if (e != cudaSuccess) {   // out of memory: return this thread's cache to CUDA and retry once
     cudaGetLastError();
-    pool_trim();
+    cudaDeviceSynchronize();
+    for (auto& b : fb) cudaFree(b.second);
+    fb.clear();
     e = cudaMalloc(&p, sz);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -69,7 +79,7 @@ void pool_put(void* p, size_t bytes) {
 void pool_trim() {
   auto& fb = t_pool.free_blocks;
   if (fb.empty()) return;
-  cudaDeviceSynchronize();
+  std::lock_guard<std::recursive_mutex> lk(capture_mutex());
   for (auto& b : fb) cudaFree(b.second);
   fb.clear();
 }

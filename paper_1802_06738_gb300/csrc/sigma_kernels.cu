@@ -1,4 +1,6 @@
 // Kernels of the sigma program (see sigma_prog.cuh).
+#include <map>
+#include <mutex>
 #include "sigma_prog.cuh"
 
 namespace pnoeom {
@@ -215,16 +217,28 @@ __global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, c
 
 }  // namespace
 
+// The dynamic shared-memory limit of a kernel is one attribute per function
+// and device for the whole process, so several host threads must agree on it:
+// it is only ever raised, under one lock, to the largest size any launch needed.
+static void ensure_dynamic_smem(const void* func, size_t smem) {
+  if (smem <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> configured;
+  int dev = 0;
+  PN_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& conf = configured[{dev, func}];
+  if (smem > conf) {
+    PN_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    conf = smem;
+  }
+}
+
 template <typename T>
 void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_elems, cudaStream_t s) {
   if (nprob <= 0 || t.max_nvec <= 0) return;
   size_t smem = (size_t)smem_elems * sizeof(T);
-  static thread_local size_t configured[2] = {0, 0};
-  size_t& conf = configured[sizeof(T) == 8];
-  if (smem > 48 * 1024 && smem > conf) {
-    PN_CUDA(cudaFuncSetAttribute(k_sandwich<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conf = smem;
-  }
+  ensure_dynamic_smem((const void*)k_sandwich<T>, smem);
   k_sandwich<T><<<dim3(nprob, t.max_nvec), 256, smem, s>>>(d_probs, t);
   PN_CUDA(cudaGetLastError());
 }
@@ -233,11 +247,7 @@ template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s) {
   if (nprob <= 0 || t.max_nvec <= 0) return;
   const size_t smem = (size_t)VR * GEMV_KC * sizeof(T);
-  static thread_local bool configured[2] = {false, false};
-  if (!configured[sizeof(T) == 8]) {
-    PN_CUDA(cudaFuncSetAttribute(k_gemv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured[sizeof(T) == 8] = true;
-  }
+  ensure_dynamic_smem((const void*)k_gemv<T>, smem);
   k_gemv<T><<<nprob, 256, smem, s>>>(d_probs, t);
   PN_CUDA(cudaGetLastError());
 }
@@ -253,12 +263,7 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
   int rpc = std::max(1, std::min(roots_per_cta, t.max_nvec));
   rpc = (int)std::min<size_t>(rpc, (limit - base) / per_root);
   const size_t smem = base + (size_t)rpc * per_root;
-  static thread_local size_t configured[2] = {0, 0};
-  size_t& conf = configured[sizeof(T) == 8];
-  if (smem > 48 * 1024 && smem > conf) {
-    PN_CUDA(cudaFuncSetAttribute(k_sandwich_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    conf = smem;
-  }
+  ensure_dynamic_smem((const void*)k_sandwich_small<T>, smem);
   const int ychunks = (t.max_nvec + rpc - 1) / rpc;
   k_sandwich_small<T><<<dim3(ngroups, ychunks), 256, smem, s>>>(d_probs, d_group_start, t, rpc, dm, dk1, dk2, dn);
   PN_CUDA(cudaGetLastError());

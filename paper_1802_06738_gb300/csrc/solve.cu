@@ -4,6 +4,7 @@
 #include <cmath>
 #include <complex>
 #include <memory>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -390,6 +391,7 @@ struct DavState {
   int m = 0, nr = 0, it = 0, p0 = 0, p1 = 0;
   int64_t sigma_evals = 0;
   bool done = false, converged = false;
+  bool trace = std::getenv("PNOEOM_LOG_DAVIDSON") != nullptr;
   std::vector<double> w, rn, w_old;
 
   DavState(pnoeom_pno* P_, const pnoeom_opts* opts, cudaStream_t s_) : P(P_), s(s_), L(P_->L), D{P_, s_, P_->L} {
@@ -451,6 +453,12 @@ struct DavState {
     double dw = 1e300;
     if ((int)w_old.size() == nr) { dw = 0; for (int q = 0; q < nr; ++q) dw = std::max(dw, std::fabs(w[q] - w_old[q])); }
     w_old = w;
+    if (trace) {   // PNOEOM_LOG_DAVIDSON: one line per iteration
+      double rmax = 0;
+      for (double x : rn) rmax = std::max(rmax, x);
+      std::fprintf(stderr, "[davidson] L=%lld it=%d m=%d prec=%s max|r|=%.3e dw=%.3e w0=%.10f\n", (long long)L, it, m,
+                   prec == PNOEOM_FP32 ? "fp32" : "fp64", rmax, dw, w.empty() ? 0.0 : w[0]);
+    }
     bool conv = true;
     for (int q = 0; q < nr; ++q) conv = conv && rn[q] < tol_now();
     conv = conv && (prec == PNOEOM_FP32 && refine ? true : dw < e_tol);
@@ -692,15 +700,19 @@ template <typename Body>
 void graph_launch(pnoeom_batch* B, cudaStream_t s, Body&& body) {
   if (!B->use_graph || s == nullptr) { body(); return; }
   cudaGraph_t g = nullptr;
-  PN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-  try {
-    body();
-  } catch (...) {
-    cudaStreamEndCapture(s, &g);
-    if (g) cudaGraphDestroy(g);
-    throw;
+  {
+    // no allocation, free or trim of another library thread during the capture
+    std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+    PN_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    PN_CUDA(cudaStreamEndCapture(s, &g));
   }
-  PN_CUDA(cudaStreamEndCapture(s, &g));
   bool ok = false;
   if (B->exec) {
     cudaGraphExecUpdateResultInfo info;
@@ -846,6 +858,7 @@ static void server_builder(pnoeom_server* S) {
                       r->has_t2 ? r->t2.data() : nullptr, PNOEOM_HOST};
     auto* P = new pnoeom_pno();
     int code = guard_call([&] { build_system(&bctx, &sys, &r->opts, bs, P); });
+    const std::string why = code == PNOEOM_OK ? "" : std::string(pnoeom_last_error());
     std::lock_guard<std::mutex> lk(S->mu);
     S->used -= r->est_bytes;
     r->B.clear(); r->B.shrink_to_fit(); r->t2.clear(); r->t2.shrink_to_fit();
@@ -853,7 +866,7 @@ static void server_builder(pnoeom_server* S) {
       delete P;
       r->status = PNOEOM_REQ_FAILED;
       r->error = code;
-      r->message = "build failed";
+      r->message = "build failed: " + why;
       r->t_done = wall_s() - S->t0;
     } else {
       r->pno = P;
