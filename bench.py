@@ -147,6 +147,46 @@ def oracle_setup(w):
     return sp, pno.PNOSigma(sig, sp)
 
 
+def nvtx_push(name):
+    try:
+        import torch
+        torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
+def nvtx_pop():
+    try:
+        import torch
+        torch.cuda.nvtx.range_pop()
+    except Exception:
+        pass
+
+
+# FP32 FMA issue rate of a GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA per clock
+FP32_FLOPS_PER_CLOCK = 152 * 128 * 2
+
+
+def roofline(dom, steps, peaks, clk):
+    """Roofline entry of the dominant kernel class: HBM-bound or FP32-ALU-bound by its
+    arithmetic intensity against the ridge of the two peaks."""
+    hbm, src = (peaks.get("hbm_gbs"), "of measured") if peaks.get("hbm_gbs") else (6800.0, "of fallback")
+    mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    alu_tflops = FP32_FLOPS_PER_CLOCK * mhz * 1e6 / 1e12
+    avg_ms = dom["ms"] / steps
+    intensity = dom["flops"] / max(dom["bytes"], 1.0)
+    ridge = alu_tflops * 1e12 / (hbm * 1e9)
+    common = {"kernel": dom["name"], "algorithmic_bytes_per_call": dom["bytes"], "algorithmic_flops_per_call": dom["flops"],
+              "avg_ms_per_call": avg_ms, "launches_per_call": dom["launches"] / steps,
+              "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge}
+    if intensity > ridge:
+        ach = dom["flops"] / (avg_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": alu_tflops, "unit": "TFLOP/s", "frac": ach / alu_tflops,
+                "peak_source": f"derived: FP32 FMA, 152 SMs x 128 lanes x 2 x {mhz:.0f} MHz", **common}
+    ach = dom["bytes"] / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src, **common}
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -367,11 +407,13 @@ def main():
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
+        nvtx_push("sigma_timed")   # lets a profiler select exactly the timed launches
         ev0.record()
         for _ in range(args.steps):
             gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
         ev1.record()
         torch.cuda.synchronize()
+        nvtx_pop()
     barrier(ws)
     t_mixed = ev0.elapsed_time(ev1) / 1e3
     prof = gp.sigma_timing(nr, pkg.FP32)
@@ -419,14 +461,14 @@ def main():
     pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pf):
         peaks = json.load(open(pf))
-    hbm_peak, peak_src = (peaks.get("hbm_gbs"), "of measured") if peaks.get("hbm_gbs") else (6800.0, "of fallback")
     dom = max(prof, key=lambda d: d["ms"])
-    avg_ms = dom["ms"] / args.steps          # per sigma call (the class's launches of one call)
-    achieved_gbs = dom["bytes"] / (avg_ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    roof = roofline(dom, args.steps, peaks, clocks)
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tf):
         traffic = json.load(open(tf)).get(dom["name"])
+    roof["traffic"] = traffic
     cpu = None
     if not args.no_cpu_baseline and args.gpus == 1:
         t0 = time.time()
@@ -465,14 +507,11 @@ def main():
         "energy_check": golden,
         "e2e": {"value": ws * nr * args.steps / t_e2e, "unit": "sigma-evals/s",
                 "h2d_bytes_per_step": int(Rh.numel() * 4), "d2h_bytes_per_step": int(Sh.numel() * 4)},
-        "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": achieved_gbs / hbm_peak, "peak_source": peak_src,
-                     "traffic": traffic, "algorithmic_bytes_per_call": dom["bytes"], "avg_ms_per_call": avg_ms,
-                     "launches_per_call": dom["launches"] / args.steps},
+        "roofline": roof,
         "kernels": prof,
         "autotune": dict(zip(["candidates_group_rpc_ms", "choice"], gp.autotune_info())),
         "gpu_launches": int(sum(d["launches"] for d in prof)),
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
