@@ -241,10 +241,11 @@ int pnoeom_small_eig(int n, const double* A, double* wr, double* wi, double* VR)
 /* Tracing of sigma.  pno_set_timing(pno, 1) clears the counters and makes
  * every later sigma call on this handle record CUDA events, on the stream it
  * launches on, around each of its kernels; 0 stops recording.
- * pno_sigma_timing reports, for kernel class `k` (0: ring/ladder sandwich
- * products into the R-dependent intermediates, 1: dense blocks into those
- * intermediates, 2: sandwich products into sigma, 3: dense blocks into
- * sigma), the number of kernel launches recorded, their summed device time
+ * pno_sigma_timing reports, for kernel class `k` (0: sandwich products
+ * into the R-dependent intermediates, 1: dense GEMV blocks into those
+ * intermediates, 2: sandwich products into sigma, 3: dense GEMV blocks into
+ * sigma, 4: GEMM tiles into the intermediates (FvR), 5: GEMM tiles of the
+ * E3 term (Z = FvR^T U_cat and its products into sigma)), the number of kernel launches recorded, their summed device time
  * in ms, the algorithmic bytes one sigma call's launches of that class move
  * for nvec vectors (operator blocks
  * read once, vector blocks read and written once per vector, at the element

@@ -19,6 +19,10 @@ HOST, DEVICE = 0, 1
 FP64, FP32 = 0, 1
 
 
+# kernel classes of the sigma program reported by pno_sigma_timing
+SIGMA_CLASSES = 6
+
+
 class PnoeomError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"pnoeom error {code}: {msg}")
@@ -258,7 +262,7 @@ class PNO:
     def sigma_timing(self, nvec, precision=FP64):
         """Per kernel class: dict(name, launches, ms, bytes, flops) of the recorded sigma calls."""
         out = []
-        for k in range(4):
+        for k in range(SIGMA_CLASSES):
             nm, n = ctypes.c_char_p(), ctypes.c_int()
             ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
             _check(lib().pno_sigma_timing(self.h, k, nvec, precision, ctypes.byref(nm), ctypes.byref(n), ctypes.byref(ms),

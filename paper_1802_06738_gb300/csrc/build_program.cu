@@ -93,6 +93,7 @@ struct Prog {
   Dims dm;
   std::vector<SProb> sp1, sp2;
   std::vector<VProb> vp1, vp2;
+  std::vector<DProb> dp1, dp2, dp3;
   int smem = 1;
 
   const double* U(int x, int y) const { return P->U.get() + P->Uoff_pair[P->pidx[x][y]]; }
@@ -157,7 +158,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
                    DV& u2) {
   const int o = P->o, v = P->v, naux = P->naux, nmo = o + v;
   const int64_t O = o, V = v, N = naux;
-  Prog G{P, s, o, v, naux, {}, {}, {}, {}, {}, 1};
+  Prog G{P, s, o, v, naux, {}, {}, {}, {}, {}, {}, {}, {}, 1};
   for (char c : std::string("ijklmxyz")) G.dm[c] = O;
   for (char c : std::string("abcd")) G.dm[c] = V;
   G.dm['Q'] = N;
@@ -316,6 +317,11 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   int64_t pool = 0;
   auto take = [&](int64_t n) { int64_t off = pool; pool += n; return off; };
   const int64_t off_U = take(P->U.n);
+  // U_cat = [U_p for every stored pair p] (v x sum n_p): one matrix for the global E3 products
+  std::vector<int64_t> zc(npairs + 1, 0);
+  for (int p = 0; p < npairs; ++p) zc[p + 1] = zc[p] + nP(p);
+  const int64_t nsum = zc[npairs];
+  const int64_t off_Ucat = take(V * nsum);
   std::vector<int64_t> offS((size_t)npairs * npairs);
   for (int p = 0; p < npairs; ++p) for (int q = 0; q < npairs; ++q) offS[(size_t)p * npairs + q] = take(nP(p) * nP(q));
   auto idx3 = [&](int a, int b, int c) { return ((size_t)a * o + b) * o + c; };
@@ -342,6 +348,10 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   P->pool64.zero(s);
   double* pl = P->pool64.get();
   PN_CUDA(cudaMemcpyAsync(pl + off_U, P->U.get(), P->U.n * 8, cudaMemcpyDeviceToDevice, s));
+  for (int p = 0; p < npairs; ++p)
+    if (nP(p))
+      PN_CUDA(cudaMemcpy2DAsync(pl + off_Ucat + zc[p], nsum * 8, P->U.get() + P->Uoff_pair[p], nP(p) * 8, nP(p) * 8, V,
+                                cudaMemcpyDeviceToDevice, s));
 
   // ---- overlaps S(p,q) = U_p^T U_q ----------------------------------------------------
   {
@@ -664,14 +674,17 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
 
   tm.mark("  singles rows");
   // ---- problem lists ------------------------------------------------------------------------------
+  // per-vector work: FvR (v x v), FoR (o x o), Y (sum n_p x v), Z (v x sum n_p)
   P->work_fvr = 0;
   P->work_for = V * V;
-  P->work_len = V * V + O * O;
+  P->work_y = P->work_for + O * O;
+  P->work_z = P->work_y + nsum * V;
+  P->work_len = P->work_z + V * nsum;
   auto blk = [&](int x, int y) { return P->pidx[x][y]; };
   // sandwich helper: C(stored out pair, transposed?) += al * A * X(stored q, tx) * B
   auto add_sw = [&](std::vector<SProb>& L_, int cbuf, int64_t coff, int ldc, int tc, int M, int Nn, int abuf, int64_t aoff,
                     int lda, int ta, int K1, int xbuf, int64_t xoff, int ldx, int tx, int K2, int bbuf, int64_t boff,
-                    int ldb, int tb, double al) {
+                    int ldb, int tb, double al, double xb = 0.0) {
     if (M <= 0 || Nn <= 0 || K1 <= 0 || K2 <= 0 || al == 0.0) return;
     for (int m0 = 0; m0 < M; m0 += 64)
       for (int n0 = 0; n0 < Nn; n0 += 64) {
@@ -681,7 +694,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         q.M = M; q.K1 = K1; q.K2 = K2; q.N = Nn;
         q.lda = lda; q.ldx = ldx; q.ldb = ldb; q.ldc = ldc;
         q.ta = ta; q.tx = tx; q.tb = tb; q.tc = tc;
-        q.m0 = m0; q.n0 = n0; q.alpha = al;
+        q.m0 = m0; q.n0 = n0; q.alpha = al; q.xb = xb;
         L_.push_back(q);
         int tr = abuf == B_NONE ? std::min(64, M - m0) : K1;
         G.smem = std::max(G.smem, tr * std::min(64, Nn - n0));
@@ -701,18 +714,35 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         L_.push_back(q);
       }
   };
+  // dense helper: C += al opA(A) opB(B), tiles of `tile`, K split in chunks of kchunk
+  auto add_dense = [&](std::vector<DProb>& L_, int tile, int kchunk, int cbuf, int64_t coff, int ldc, int tc, int M,
+                       int Nn, int abuf, int64_t aoff, int lda, int ta, int K, int bbuf, int64_t boff, int ldb, int tb,
+                       double al) {
+    if (M <= 0 || Nn <= 0 || K <= 0 || al == 0.0) return;
+    for (int m0 = 0; m0 < M; m0 += tile)
+      for (int n0 = 0; n0 < Nn; n0 += tile)
+        for (int k0 = 0; k0 < K; k0 += kchunk) {
+          DProb q{};
+          q.a_off = aoff; q.b_off = boff; q.c_off = coff;
+          q.a_buf = abuf; q.b_buf = bbuf; q.c_buf = cbuf;
+          q.M = M; q.N = Nn; q.K = K;
+          q.lda = lda; q.ldb = ldb; q.ldc = ldc;
+          q.ta = ta; q.tb = tb; q.tc = tc;
+          q.m0 = m0; q.n0 = n0; q.k0 = k0; q.klen = std::min(kchunk, K - k0); q.alpha = al;
+          L_.push_back(q);
+        }
+  };
   auto Ro = [&](int x, int y) { return P->off_ij[blk(x, y)]; };          // stored block offset
   auto Rt = [&](int x, int y) { return x > y ? 1 : 0; };                  // R^{xy} = stored^T ?
-  // Phase 1: E3 virtual intermediate FvR (v x v) and E4 occupied intermediate FoR (o x o)
+  // Phase 1: E3 virtual intermediate FvR (v x v) and E4 occupied intermediate FoR (o x o).
+  // FvR = -sum_kl U^{kl} (2 R^{kl} - R^{kl T}) Gh[k,l] = -U_cat Y, where the rows of Y that
+  // belong to stored pair q collect (2 R^{kl} - R^{kl T}) Gh[k,l] over the ordered (k,l) of q.
   for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
     const int nn = G.n(k, l);
     if (!nn) continue;
-    const int64_t uo = off_U + P->Uoff_pair[blk(k, l)];
-    // FvR += -U^{kl} (2 R^{kl} - R^{kl T}) Gh[k,l]
-    add_sw(G.sp1, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, uo, nn, 0, nn, B_RIN, Ro(k, l), nn, Rt(k, l), nn, B_POOL,
-           offGh[k * o + l], v, 0, -2.0);
-    add_sw(G.sp1, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, uo, nn, 0, nn, B_RIN, Ro(k, l), nn, 1 - Rt(k, l), nn, B_POOL,
-           offGh[k * o + l], v, 0, 1.0);
+    const int q = blk(k, l);
+    add_sw(G.sp1, B_WORK, P->work_y + zc[q] * V, v, 0, nn, v, B_NONE, 0, 0, 0, nn, B_RIN, Ro(k, l), nn, Rt(k, l), nn,
+           B_POOL, offGh[k * o + l], v, 0, 2.0, -0.5);
     // FoR[:, j] += G4[(l,j)] vec(2 R^{lj} - R^{lj T})   (here (l, j) = (k, l))
     const int lj_l = k, lj_j = l;
     add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? nn : 0, B_WORK,
@@ -720,6 +750,11 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? 0 : nn, B_WORK,
              P->work_for + lj_j, o, 0, -1.0);
   }
+  add_dense(G.dp1, 64, 256, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, off_Ucat, (int)nsum, 0, (int)nsum, B_WORK, P->work_y, v,
+            0, -1.0);
+  // Phase 2 prologue: Z = FvR^T U_cat (v x sum n_p), read by the E3 products below
+  add_dense(G.dp2, 64, 1 << 30, B_WORK, P->work_z, (int)nsum, 0, v, (int)nsum, B_WORK, P->work_fvr, v, 1, v, B_POOL, off_Ucat,
+            (int)nsum, 0, 1.0);
   // Phase 2
   for (int p = 0; p < npairs; ++p) {
     const int nn = (int)nP(p);
@@ -744,9 +779,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       const int64_t co = P->off_ij[pij];
       // E4 phase 2: -sum_k FoR[k,j] vec(tb3[i,k,j])
       add_gemv(G.vp2, offT4[i * o + j], nij * nij, o, o, B_WORK, P->work_for + j, o, 0, B_SOUT, co, 1, tc ? nij : 0, -1.0);
-      // E3 phase 2: Th[i,j] FvR^T U(i,j)
-      add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offTh[i * o + j], v, 0, v, B_WORK, P->work_fvr, v, 1, v, B_POOL,
-             off_U + P->Uoff_pair[pij], nij, 0, 1.0);
+      // E3 phase 2: Th[i,j] FvR^T U(i,j) = Th[i,j] Z[:, columns of pair {i,j}]
+      add_dense(G.dp3, 32, 1 << 30, B_SOUT, co, nij, tc, nij, nij, B_POOL, offTh[i * o + j], v, 0, v, B_WORK,
+                P->work_z + zc[pij], (int)nsum, 0, 1.0);
       for (int k = 0; k < o; ++k) {
         const int nkj = G.n(k, j), nki = G.n(k, i), njk = G.n(j, k), nik = G.n(i, k);
         const int pkj = blk(k, j), pki = blk(k, i), pjk = blk(j, k), pik = blk(i, k);
@@ -764,34 +799,47 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
                nkj, B_POOL, offMZ[idx3(k, j, i)], nij, 0, 0.5);
         // D1: MD[i,j,k] (R^{jk T} - 1/2 R^{jk}) S(jk,ij)
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMD[idx3(i, j, k)], njk, 0, njk, B_RIN, Ro(j, k), njk,
-               1 - Rt(j, k), njk, B_POOL, Sblk(pjk, pij), nij, 0, 1.0);
-        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMD[idx3(i, j, k)], njk, 0, njk, B_RIN, Ro(j, k), njk,
-               Rt(j, k), njk, B_POOL, Sblk(pjk, pij), nij, 0, -0.5);
+               1 - Rt(j, k), njk, B_POOL, Sblk(pjk, pij), nij, 0, 1.0, -0.5);
         // D2: S(ij,ik) (1/2 R^{ik} - 1/4 R^{ik T}) MZd[k,i,j]
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik, Rt(i, k),
-               nik, B_POOL, offMZd[idx3(k, i, j)], nij, 0, 0.5);
-        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik,
-               1 - Rt(i, k), nik, B_POOL, offMZd[idx3(k, i, j)], nij, 0, -0.25);
+               nik, B_POOL, offMZd[idx3(k, i, j)], nij, 0, 0.5, -0.5);
         // E2: -Foo~[k,j] S(ij,ik) R^{ik} S(ik,ij)
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik, Rt(i, k),
                nik, B_POOL, Sblk(pik, pij), nij, 0, -FooI_h[k * o + j]);
       }
     }
   }
-  // occupied ladder (not symmetrised): stored (i,j) += sum_kl W[k,i,l,j] S(ij,kl) R^{kl} S(kl,ij)
+  // occupied ladder (not symmetrised): stored (i,j) += sum_kl W[k,i,l,j] S(ij,kl) R^{kl} S(kl,ij);
+  // (k,l) and (l,k) share the stored block q = {k,l} and its overlaps: one problem with
+  // X_eff = W[k,i,l,j] R^q + W[l,i,k,j] R^{q T}
   std::vector<double> W_h(W.n);
   W.download(W_h.data(), W_h.size(), s);
   G.sync();
   for (int p = 0; p < npairs; ++p) {
     const int i = P->pair_i[p], j = P->pair_j[p], nij = (int)nP(p);
     if (!nij) continue;
-    for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
+    for (int k = 0; k < o; ++k) for (int l = k; l < o; ++l) {
       const int q = blk(k, l), nq = (int)nP(q);
       if (!nq) continue;
-      add_sw(G.sp2, B_SOUT, P->off_ij[p], nij, 0, nij, nij, B_POOL, Sblk(p, q), nq, 0, nq, B_RIN, P->off_ij[q], nq, Rt(k, l),
-             nq, B_POOL, Sblk(q, p), nij, 0, W_h[(((size_t)k * o + i) * o + l) * o + j]);
+      const double w1 = W_h[(((size_t)k * o + i) * o + l) * o + j];
+      const double w2 = k == l ? 0.0 : W_h[(((size_t)l * o + i) * o + k) * o + j];
+      // stored block q is R^{kl} (k <= l); R^{lk} = R^{kl T}
+      if (w1 != 0.0)
+        add_sw(G.sp2, B_SOUT, P->off_ij[p], nij, 0, nij, nij, B_POOL, Sblk(p, q), nq, 0, nq, B_RIN, P->off_ij[q], nq, 0, nq,
+               B_POOL, Sblk(q, p), nij, 0, w1, w2 / w1);
+      else
+        add_sw(G.sp2, B_SOUT, P->off_ij[p], nij, 0, nij, nij, B_POOL, Sblk(p, q), nq, 0, nq, B_RIN, P->off_ij[q], nq, 1, nq,
+               B_POOL, Sblk(q, p), nij, 0, w2);
     }
   }
+  // per-problem extents of the small kernel: tile rows, staged X rows and columns, tile columns
+  auto extents = [](const SProb& q, int e[4]) {
+    const int Mt = std::min(64, q.M - q.m0), Nt = std::min(64, q.N - q.n0);
+    e[0] = Mt;
+    e[1] = q.a_buf != B_NONE ? q.K1 : Mt;
+    e[2] = q.b_buf != B_NONE ? q.K2 : Nt;
+    e[3] = Nt;
+  };
   // algorithmic traffic and flops of each kernel class (tracing / roofline):
   // operator blocks counted once per launch (distinct blocks), vector blocks
   // once per vector (distinct ranges), flops as issued
@@ -804,8 +852,10 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         if (q.b_buf == B_POOL) pool_blocks.insert({q.b_off, (int64_t)q.K2 * q.N});
         if (q.x_buf != B_POOL) vec_blocks.insert({q.x_off + ((int64_t)q.x_buf << 40), (int64_t)q.K1 * q.K2});
         vec_blocks.insert({q.c_off + ((int64_t)q.c_buf << 40), (int64_t)q.M * q.N});
-        const int Mt = std::min(64, q.M - q.m0), Nt = std::min(64, q.N - q.n0);
-        fl += 2.0 * q.K1 * Nt * q.K2 + 2.0 * Mt * Nt * q.K1;
+        int e[4];
+        extents(q, e);
+        if (q.b_buf != B_NONE) fl += 2.0 * e[1] * e[2] * e[3];
+        if (q.a_buf != B_NONE) fl += 2.0 * e[0] * e[1] * e[3];
       }
       double pe = 0, ve = 0;
       for (auto& b : pool_blocks) pe += b.second;
@@ -826,12 +876,36 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       for (auto& b : vec_blocks) ve += b.second;
       P->prof_pool_elems[cls] = pe; P->prof_vec_elems[cls] = ve; P->prof_flops[cls] = fl;
     };
+    auto acc_d = [&](std::initializer_list<const std::vector<DProb>*> lists, int cls) {
+      std::set<std::pair<int64_t, int64_t>> pool_blocks, vec_blocks;
+      double fl = 0;
+      for (const auto* Lst : lists)
+        for (const DProb& q : *Lst) {
+          const int64_t asz = (int64_t)q.M * q.K, bsz = (int64_t)q.K * q.N;
+          if (q.a_buf == B_POOL) pool_blocks.insert({q.a_off, asz});
+          else vec_blocks.insert({q.a_off + ((int64_t)q.a_buf << 40), asz});
+          if (q.b_buf == B_POOL) pool_blocks.insert({q.b_off, bsz});
+          else vec_blocks.insert({q.b_off + ((int64_t)q.b_buf << 40), bsz});
+          vec_blocks.insert({q.c_off + ((int64_t)q.c_buf << 40), (int64_t)q.M * q.N});
+          fl += 2.0 * std::min(64, q.M - q.m0) * std::min(64, q.N - q.n0) * q.klen;
+        }
+      double pe = 0, ve = 0;
+      for (auto& b : pool_blocks) pe += b.second;
+      for (auto& b : vec_blocks) ve += b.second;
+      P->prof_pool_elems[cls] = pe; P->prof_vec_elems[cls] = ve; P->prof_flops[cls] = fl;
+    };
     acc_sw(G.sp1, 0); acc_v(G.vp1, 1); acc_sw(G.sp2, 2); acc_v(G.vp2, 3);
+    acc_d({&G.dp1}, 4);
+    acc_d({&G.dp2, &G.dp3}, 5);
   }
   // split each sandwich list: problems with every dim <= SMALL_DIM (single tile) go to the
   // shared-memory kernel, bucketed by their largest dim
-  auto bucket_of = [](const SProb& q) {
-    int d = std::max(std::max(q.M, q.N), std::max(q.K1, q.K2));
+  auto bucket_of = [&](const SProb& q) {
+    if (q.a_buf != B_NONE && q.K1 > SMALL_DIM) return -1;
+    if (q.b_buf != B_NONE && q.K2 > SMALL_DIM) return -1;
+    int e[4];
+    extents(q, e);
+    const int d = std::max(std::max(e[0], e[1]), std::max(e[2], e[3]));
     return d <= 16 ? 0 : d <= 32 ? 1 : d <= SMALL_DIM ? 2 : -1;
   };
   // order by output block (heaviest blocks first); group boundaries for every candidate size
@@ -841,10 +915,13 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       if (a.c_off != b.c_off) return a.c_off < b.c_off;
       if (a.tc != b.tc) return a.tc < b.tc;
       if (a.M != b.M) return a.M < b.M;
-      return a.N < b.N;
+      if (a.N != b.N) return a.N < b.N;
+      if (a.m0 != b.m0) return a.m0 < b.m0;
+      return a.n0 < b.n0;
     };
     auto same = [](const SProb& a, const SProb& b) {
-      return a.c_buf == b.c_buf && a.c_off == b.c_off && a.tc == b.tc && a.M == b.M && a.N == b.N;
+      return a.c_buf == b.c_buf && a.c_off == b.c_off && a.tc == b.tc && a.M == b.M && a.N == b.N && a.m0 == b.m0 &&
+             a.n0 == b.n0;
     };
     std::stable_sort(Lst.begin(), Lst.end(), key_less);
     std::vector<std::pair<double, std::pair<size_t, size_t>>> blocks;
@@ -852,7 +929,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       size_t j = i;
       double work = 0;
       while (j < Lst.size() && same(Lst[j], Lst[i])) {
-        work += (double)Lst[j].K1 * Lst[j].N * Lst[j].K2 + (double)Lst[j].M * Lst[j].N * Lst[j].K1;
+        int e[4];
+        extents(Lst[j], e);
+        work += (double)e[1] * e[2] * e[3] + (double)e[0] * e[1] * e[3];
         ++j;
       }
       blocks.push_back({work, {i, j}});
@@ -877,8 +956,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     for (int k = 0; k < 3; ++k) {
       SmallSet& S = sets[k];
       for (const SProb& q : b[k]) {
-        S.dims[0] = std::max(S.dims[0], q.M); S.dims[1] = std::max(S.dims[1], q.K1);
-        S.dims[2] = std::max(S.dims[2], q.K2); S.dims[3] = std::max(S.dims[3], q.N);
+        int e[4];
+        extents(q, e);
+        for (int d = 0; d < 4; ++d) S.dims[d] = std::max(S.dims[d], e[d]);
       }
       auto ranges = order_by_output(b[k]);
       S.nprob = (int)b[k].size();
@@ -898,6 +978,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   make_sets(G.sp2, PR.small2, PR.h_gen2);
   PR.h_v1 = G.vp1;
   PR.h_v2 = G.vp2;
+  PR.h_d1 = G.dp1;
+  PR.h_d2 = G.dp2;
+  PR.h_d3 = G.dp3;
   PR.smem_elems = G.smem;
   PR.upload(s, fp);
   // FP32 copy of the pool for the mixed-precision sigma
@@ -913,6 +996,10 @@ void Program::upload(cudaStream_t s, size_t* fp) {
   gen2.alloc(std::max<size_t>(1, h_gen2.size()), fp); gen2.upload(h_gen2.data(), h_gen2.size(), s);
   v1.alloc(std::max<size_t>(1, h_v1.size()), fp); v1.upload(h_v1.data(), h_v1.size(), s);
   v2.alloc(std::max<size_t>(1, h_v2.size()), fp); v2.upload(h_v2.data(), h_v2.size(), s);
+  n_d1 = (int)h_d1.size(); n_d2 = (int)h_d2.size(); n_d3 = (int)h_d3.size();
+  d1.alloc(std::max<size_t>(1, h_d1.size()), fp); d1.upload(h_d1.data(), h_d1.size(), s);
+  d2.alloc(std::max<size_t>(1, h_d2.size()), fp); d2.upload(h_d2.data(), h_d2.size(), s);
+  d3.alloc(std::max<size_t>(1, h_d3.size()), fp); d3.upload(h_d3.data(), h_d3.size(), s);
   for (SmallSet* sets : {small1, small2})
     for (int k = 0; k < 3; ++k) {
       SmallSet& S = sets[k];

@@ -116,9 +116,10 @@ int pno_set_timing(pnoeom_pno* pno, int enable) {
 
 int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, const char** name, int* launches,
                      double* ms, double* bytes, double* flops) {
-  static const char* names[4] = {"sandwich->intermediates", "dense->intermediates", "sandwich->sigma", "dense->sigma"};
+  static const char* names[pnoeom_pno::NCLS] = {"sandwich->intermediates", "dense->intermediates", "sandwich->sigma",
+                                                "dense->sigma", "gemm->intermediates", "gemm->sigma"};
   return guard([&] {
-    PN_CHECK(pno && k >= 0 && k < 4, PNOEOM_ERR_INVALID_ARG, "bad arguments");
+    PN_CHECK(pno && k >= 0 && k < pnoeom_pno::NCLS, PNOEOM_ERR_INVALID_ARG, "bad arguments");
     int n = 0;
     double t = 0;
     for (const auto& e : pno->events) {

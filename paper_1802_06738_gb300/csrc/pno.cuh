@@ -34,12 +34,14 @@ struct SmallSet {
 struct Program {
   DBuf<SProb> gen1, gen2;          // generic sandwich problems (phase 1: intermediates, phase 2: sigma)
   DBuf<VProb> v1, v2;              // dense GEMV tiles
-  int n_gen1 = 0, n_gen2 = 0, n_v1 = 0, n_v2 = 0;
+  DBuf<DProb> d1, d2, d3;          // dense GEMM tiles: FvR (phase 1), Z, E3 products (phase 2)
+  int n_gen1 = 0, n_gen2 = 0, n_v1 = 0, n_v2 = 0, n_d1 = 0, n_d2 = 0, n_d3 = 0;
   SmallSet small1[3], small2[3];   // small sandwich problems per size bucket
   int smem_elems = 1;
   int group_choice = 0, rpc_choice = 0;
   std::vector<SProb> h_gen1, h_gen2;
   std::vector<VProb> h_v1, h_v2;
+  std::vector<DProb> h_d1, h_d2, h_d3;
   void upload(cudaStream_t s, size_t* fp);
 };
 }  // namespace pnoeom
@@ -66,10 +68,11 @@ struct pnoeom_pno {
   pnoeom::DBuf<float> pool32;
   pnoeom::Program prog;
   double tune_ms[pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND] = {0};
-  int prof_launches[4] = {0, 0, 0, 0};
+  static constexpr int NCLS = 6;             // kernel classes of the sigma program (timing)
+  int prof_launches[NCLS] = {0};
   int smem_elems = 0;
-  int64_t work_len = 0;                      // FvR (v*v) + FoR (o*o)
-  int64_t work_fvr = 0, work_for = 0;
+  int64_t work_len = 0;                      // FvR (v*v) + FoR (o*o) + Y + Z (2 v sum n_p)
+  int64_t work_fvr = 0, work_for = 0, work_y = 0, work_z = 0;
   // Davidson data
   pnoeom::DBuf<double> denom_base;           // f_ii (+ f_jj) - fbar_a (- fbar_b), packed
   pnoeom::DBuf<double> guesses;              // projected CIS vectors, nroots_sa x L
@@ -81,7 +84,7 @@ struct pnoeom_pno {
   pnoeom::DBuf<double> work64; pnoeom::DBuf<float> work32;
   // tracing: per kernel class, operator elements read once per launch,
   // vector elements read+written per vector, flops per vector
-  double prof_pool_elems[4] = {0, 0, 0, 0}, prof_vec_elems[4] = {0, 0, 0, 0}, prof_flops[4] = {0, 0, 0, 0};
+  double prof_pool_elems[NCLS] = {0}, prof_vec_elems[NCLS] = {0}, prof_flops[NCLS] = {0};
   bool timing = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
   size_t footprint = 0;

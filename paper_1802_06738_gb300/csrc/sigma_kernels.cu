@@ -22,10 +22,18 @@ __device__ __forceinline__ T* mbuf(const SysTable& t, int sys, int id, int r) {
   return id == B_WORK ? (T*)b.work + (int64_t)r * b.work_stride : (T*)b.sout + (int64_t)r * b.sout_stride;
 }
 
-// One (problem, root) per CTA.  T_s = opX(X) * opB(B) restricted to the
+// Element (a, b) of opX(X) + xb opX(X)^T (opX: X or X^T by tx; the xb term needs square X).
+template <typename T>
+__device__ __forceinline__ T xeff(const T* X, int ldx, int tx, T xb, int a, int b) {
+  T v = tx ? X[(int64_t)b * ldx + a] : X[(int64_t)a * ldx + b];
+  if (xb != T(0)) v += xb * (tx ? X[(int64_t)a * ldx + b] : X[(int64_t)b * ldx + a]);
+  return v;
+}
+
+// One (problem, root) per CTA.  T_s = X_eff * opB(B) restricted to the
 // output tile's columns is formed in shared memory, then C_tile += alpha *
 // opA(A)[tile rows] * T_s.  Accumulation into C is atomic because many
-// problems share an output block.
+// problems share an output block.  Used for blocks with a dim above SMALL_DIM.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
   extern __shared__ unsigned char smem_raw[];
@@ -37,6 +45,7 @@ __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ prob
   const T* A = P.a_buf == B_NONE ? nullptr : cbuf<T>(tab, P.sys, P.a_buf, r) + P.a_off;
   const T* Bm = P.b_buf == B_NONE ? nullptr : cbuf<T>(tab, P.sys, P.b_buf, r) + P.b_off;
   T* C = mbuf<T>(tab, P.sys, P.c_buf, r) + P.c_off;
+  const T xb = (T)P.xb;
   const int Mt = min(64, P.M - P.m0), Nt = min(64, P.N - P.n0);
   // rows of T_s: K1 if A is present, else the tile's rows of X (K1 == M)
   const int trow0 = A ? 0 : P.m0;
@@ -46,12 +55,11 @@ __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ prob
     T acc = T(0);
     if (Bm) {
       for (int k2 = 0; k2 < P.K2; ++k2) {
-        T xv = P.tx ? X[(int64_t)k2 * P.ldx + k1] : X[(int64_t)k1 * P.ldx + k2];
         T bv = P.tb ? Bm[(int64_t)n * P.ldb + k2] : Bm[(int64_t)k2 * P.ldb + n];
-        acc += xv * bv;
+        acc += xeff(X, P.ldx, P.tx, xb, k1, k2) * bv;
       }
     } else {
-      acc = P.tx ? X[(int64_t)n * P.ldx + k1] : X[(int64_t)k1 * P.ldx + n];
+      acc = xeff(X, P.ldx, P.tx, xb, k1, n);
     }
     Ts[e] = acc;
   }
@@ -74,91 +82,276 @@ __global__ void __launch_bounds__(256) k_sandwich(const SProb* __restrict__ prob
   }
 }
 
-// Small sandwich, grouped by output block: one group of problems sharing the
-// same C block per CTA, all roots in the CTA.  Per problem, A (M x K1) and B
-// (K2 x N) are staged once in shared memory; per root X is staged, T = X B is
-// formed, and alpha A T is accumulated into a shared-memory copy of the C
-// block of that root.  After the group, the accumulators are added to C
-// (atomic: several groups may share a C block).
-template <typename T>
-__global__ void __launch_bounds__(256) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
-                                                        const __grid_constant__ SysTable tab, int nroots, int dm,
-                                                        int dk1, int dk2, int dn) {
-  extern __shared__ unsigned char smem_raw[];
-  T* As = reinterpret_cast<T*>(smem_raw);     // dm x dk1
-  T* Bs = As + dm * dk1;                      // dk2 x dn
-  T* Xs = Bs + dk2 * dn;                      // dk1 x dk2
-  T* Ts = Xs + dk1 * dk2;                     // dk1 x dn
-  T* Cs = Ts + dk1 * dn;                      // nroots x dm x dn accumulators
+// 16-byte shared-memory vectors of four elements
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 q0 = reinterpret_cast<const double2*>(p)[0], q1 = reinterpret_cast<const double2*>(p)[1];
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ void st4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
+// floor(e / d) for 0 <= e, e + d < 2^22, given rd = 1.0f / d: (e + 1/2) / d lies at
+// least 1/(2d) from an integer and the two roundings move it by less than that.
+__device__ __forceinline__ int fdiv(int e, float rd) { return __float2int_rz(((float)e + 0.5f) * rd); }
+
+__host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
+
+// Grouped small sandwich (see run_sandwich_small).  Shared memory, with the set's
+// bounds dm, dk1 (rows of the staged X block), dk2 (its columns), dn padded to 4:
+//   As [dk1][Mp]        A^T (tile rows)
+//   Bs [dk2][Np]        B (tile columns)
+//   Xs [dk2][R * K1p]   X_eff^T of the R vectors side by side
+//   Ts [K1p][R * Np]    alpha X_eff B of the R vectors side by side
+// Product 1: Ts = alpha Xs^T Bs, rows (vector, a) x columns n, 4 x 4 register tiles.
+// Product 2: C[m][(vector, n)] += As^T Ts, 4 x 4 register tiles that each thread
+// keeps for the whole group (MAXT tiles per thread).
+template <typename T, int NT, int MAXT>
+__global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
+                                                       const __grid_constant__ SysTable tab, int rpc, int dm, int dk1,
+                                                       int dk2, int dn) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Mp = pad4(dm), K1p = pad4(dk1), Np = pad4(dn);
+  const int xld = rpc * K1p, tld = rpc * Np;
+  T* As = reinterpret_cast<T*>(smem_raw);
+  T* Bs = As + dk1 * Mp;
+  T* Xs = Bs + dk2 * Np;
+  T* Ts = Xs + dk2 * xld;
+  const int total = dk1 * Mp + dk2 * Np + dk2 * xld + K1p * tld;
+  const int tid = threadIdx.x;
   const int g0 = gstart[blockIdx.x], g1 = gstart[blockIdx.x + 1];
   const SProb P0 = probs[g0];
-  // this CTA's roots: [blockIdx.y * nroots, ...) (nroots = roots per CTA), within the system's vectors
-  const int rbase = blockIdx.y * nroots;
-  nroots = min(nroots, tab.s[P0.sys].nvec - rbase);
-  if (nroots <= 0) return;
-  const int M = P0.M, N = P0.N;
-  for (int e = threadIdx.x; e < nroots * M * N; e += blockDim.x) Cs[e] = T(0);
+  const int rbase = blockIdx.y * rpc;
+  const int nr = min(rpc, tab.s[P0.sys].nvec - rbase);
+  if (nr <= 0) return;
+  const int Mt = min(64, P0.M - P0.m0), Nt = min(64, P0.N - P0.n0);
+  const int nt4 = (Nt + 3) >> 2;
+  const int nct = ((Mt + 3) >> 2) * nr * nt4;
+  // padding is read (never stored) by the 4-wide tiles: keep it finite
+  for (int e = tid; e < total; e += NT) As[e] = T(0);
+  int cm4[MAXT], cr[MAXT], cn4[MAXT];
+  T acc[MAXT][4][4];
+#pragma unroll
+  for (int j = 0; j < MAXT; ++j) {
+    const int t = tid + j * NT;
+    cn4[j] = t % nt4;
+    cr[j] = (t / nt4) % nr;
+    cm4[j] = t / (nt4 * nr);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[j][a][b] = T(0);
+  }
   for (int g = g0; g < g1; ++g) {
     const SProb P = probs[g];
-    const int K1 = P.K1, K2 = P.K2;
     const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
+    const int K1 = P.K1;
+    const int kr = hasA ? K1 : Mt;       // rows of the staged X block (= rows of T)
+    const int kc = hasB ? P.K2 : Nt;     // its columns
+    const int xr0 = hasA ? 0 : P.m0, xc0 = hasB ? 0 : P.n0;
+    const T alpha = (T)P.alpha, xb = (T)P.xb;
     __syncthreads();
     if (hasA) {
       const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
-      for (int e = threadIdx.x; e < M * K1; e += blockDim.x) {
-        const int m = e / K1, k = e % K1;
-        As[m * dk1 + k] = P.ta ? A[(int64_t)k * P.lda + m] : A[(int64_t)m * P.lda + k];
+      if (P.ta) {   // stored K1 x M: element (m, k) at A[k lda + m]
+        const float rd = 1.0f / (float)Mt;
+        for (int e = tid; e < Mt * K1; e += NT) {
+          const int k = fdiv(e, rd), m = e - k * Mt;
+          As[k * Mp + m] = A[(int64_t)k * P.lda + P.m0 + m];
+        }
+      } else {
+        const float rd = 1.0f / (float)K1;
+        for (int e = tid; e < Mt * K1; e += NT) {
+          const int m = fdiv(e, rd), k = e - m * K1;
+          As[k * Mp + m] = A[(int64_t)(P.m0 + m) * P.lda + k];
+        }
       }
     }
     if (hasB) {
       const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, 0) + P.b_off;
-      for (int e = threadIdx.x; e < K2 * N; e += blockDim.x) {
-        const int k = e / N, n = e % N;
-        Bs[k * dn + n] = P.tb ? Bm[(int64_t)n * P.ldb + k] : Bm[(int64_t)k * P.ldb + n];
+      const int K2 = P.K2;
+      if (P.tb) {   // stored N x K2
+        const float rd = 1.0f / (float)K2;
+        for (int e = tid; e < K2 * Nt; e += NT) {
+          const int n = fdiv(e, rd), k = e - n * K2;
+          Bs[k * Np + n] = Bm[(int64_t)(P.n0 + n) * P.ldb + k];
+        }
+      } else {
+        const float rd = 1.0f / (float)Nt;
+        for (int e = tid; e < K2 * Nt; e += NT) {
+          const int k = fdiv(e, rd), n = e - k * Nt;
+          Bs[k * Np + n] = Bm[(int64_t)k * P.ldb + P.n0 + n];
+        }
       }
     }
-    const T alpha = (T)P.alpha;
-    for (int r = 0; r < nroots; ++r) {
-      const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
-      __syncthreads();
-      for (int e = threadIdx.x; e < K1 * K2; e += blockDim.x) {
-        const int a = e / K2, b = e % K2;
-        Xs[a * dk2 + b] = P.tx ? X[(int64_t)b * P.ldx + a] : X[(int64_t)a * P.ldx + b];
+    {
+      const int per = kr * kc;
+      const float rd_per = 1.0f / (float)per, rd_kr = 1.0f / (float)kr;
+      for (int e = tid; e < nr * per; e += NT) {
+        const int r = fdiv(e, rd_per), rem = e - r * per;
+        const int b = fdiv(rem, rd_kr), a = rem - b * kr;
+        const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
+        Xs[b * xld + r * K1p + a] = xeff(X, P.ldx, P.tx, xb, xr0 + a, xc0 + b);
       }
-      __syncthreads();
-      if (hasB) {
-        for (int e = threadIdx.x; e < K1 * N; e += blockDim.x) {
-          const int a = e / N, n = e % N;
-          T acc = T(0);
-          for (int k = 0; k < K2; ++k) acc += Xs[a * dk2 + k] * Bs[k * dn + n];
-          Ts[a * dn + n] = acc;
+    }
+    __syncthreads();
+    {   // product 1
+      const int ka4 = (kr + 3) >> 2;
+      const int n1 = nr * ka4 * nt4;
+      for (int t = tid; t < n1; t += NT) {
+        const int n4 = t % nt4, rest = t / nt4;
+        const int a4 = rest % ka4, r = rest / ka4;
+        T c[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[a][b] = T(0);
+        const T* xp = Xs + r * K1p + a4 * 4;
+        if (hasB) {
+          const T* bp = Bs + n4 * 4;
+          for (int b = 0; b < kc; ++b) {
+            T xv[4], bv[4];
+            ld4(xp + b * xld, xv);
+            ld4(bp + b * Np, bv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int q = 0; q < 4; ++q) c[a][q] += xv[a] * bv[q];
+          }
+        } else {   // T = X_eff on the tile's columns
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (n4 * 4 + q < kc) {
+              T xv[4];
+              ld4(xp + (n4 * 4 + q) * xld, xv);
+#pragma unroll
+              for (int a = 0; a < 4; ++a) c[a][q] = xv[a];
+            }
         }
-        __syncthreads();
+        T* tp = Ts + (a4 * 4) * tld + r * Np + n4 * 4;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T o[4] = {alpha * c[a][0], alpha * c[a][1], alpha * c[a][2], alpha * c[a][3]};
+          st4(tp + a * tld, o);
+        }
       }
-      T* Cr = Cs + (size_t)r * M * N;
-      for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
-        const int m = e / N, n = e % N;
-        T acc = T(0);
-        if (hasA) {
-          if (hasB) for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Ts[k * dn + n];
-          else for (int k = 0; k < K1; ++k) acc += As[m * dk1 + k] * Xs[k * dk2 + n];
-        } else {
-          acc = hasB ? Ts[m * dn + n] : Xs[m * dk2 + n];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < MAXT; ++j) {   // product 2, into the register tiles
+      if (tid + j * NT >= nct) continue;
+      const T* tp = Ts + cr[j] * Np + cn4[j] * 4;
+      if (hasA) {
+        const T* ap = As + cm4[j] * 4;
+        for (int k = 0; k < K1; ++k) {
+          T av[4], tv[4];
+          ld4(ap + k * Mp, av);
+          ld4(tp + k * tld, tv);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[j][a][q] += av[a] * tv[q];
         }
-        Cr[e] += alpha * acc;
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          T tv[4];
+          ld4(tp + (cm4[j] * 4 + a) * tld, tv);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[j][a][q] += tv[q];
+        }
       }
     }
   }
-  __syncthreads();
-  for (int r = 0; r < nroots; ++r) {
-    T* C = mbuf<T>(tab, P0.sys, P0.c_buf, rbase + r) + P0.c_off;
-    const T* Cr = Cs + (size_t)r * M * N;
-    for (int e = threadIdx.x; e < M * N; e += blockDim.x) {
-      const int m = e / N, n = e % N;
-      T* c = P0.tc ? C + (int64_t)n * P0.ldc + m : C + (int64_t)m * P0.ldc + n;
-      atomicAdd(c, Cr[e]);
+  // one atomic add per element of the group's C tile (other groups may share it)
+#pragma unroll
+  for (int j = 0; j < MAXT; ++j) {
+    if (tid + j * NT >= nct) continue;
+    T* C = mbuf<T>(tab, P0.sys, P0.c_buf, rbase + cr[j]) + P0.c_off;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = cm4[j] * 4 + a, n = cn4[j] * 4 + q;
+        if (m < Mt && n < Nt) {
+          const int64_t gm = P0.m0 + m, gn = P0.n0 + n;
+          atomicAdd(P0.tc ? C + gn * P0.ldc + gm : C + gm * P0.ldc + gn, acc[j][a][q]);
+        }
+      }
+  }
+}
+
+// Dense product tile: C[m0.., n0..] += alpha opA(A) opB(B) over K in [k0, k0 + klen).
+// BT x BT output tile, (BT/4)^2 threads with 4 x 4 register tiles, K staged in
+// chunks of 16 (A^T and B in shared memory, zero-filled outside the operands).
+template <typename T, int BT>
+__global__ void __launch_bounds__((BT / 4) * (BT / 4)) k_dense(const DProb* __restrict__ probs,
+                                                              const __grid_constant__ SysTable tab) {
+  constexpr int NT = (BT / 4) * (BT / 4), KC = 16, LD = BT + 4;
+  __shared__ __align__(16) T As[KC * LD];
+  __shared__ __align__(16) T Bs[KC * LD];
+  const DProb P = probs[blockIdx.x];
+  const int r = blockIdx.y;
+  if (r >= tab.s[P.sys].nvec) return;
+  const T* A = cbuf<T>(tab, P.sys, P.a_buf, r) + P.a_off;
+  const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, r) + P.b_off;
+  const int Mt = min(BT, P.M - P.m0), Nt = min(BT, P.N - P.n0);
+  const int tx = threadIdx.x % (BT / 4), ty = threadIdx.x / (BT / 4);
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int kk = 0; kk < P.klen; kk += KC) {
+    const int kn = min(KC, P.klen - kk), kb = P.k0 + kk;
+    __syncthreads();
+    for (int e = threadIdx.x; e < KC * BT; e += NT) {
+      int k, m;
+      if (P.ta) { k = e / BT; m = e % BT; } else { m = e / KC; k = e % KC; }
+      T v = T(0);
+      if (k < kn && m < Mt)
+        v = P.ta ? A[(int64_t)(kb + k) * P.lda + P.m0 + m] : A[(int64_t)(P.m0 + m) * P.lda + kb + k];
+      As[k * LD + m] = v;
+    }
+    for (int e = threadIdx.x; e < KC * BT; e += NT) {
+      int k, n;
+      if (P.tb) { n = e / KC; k = e % KC; } else { k = e / BT; n = e % BT; }
+      T v = T(0);
+      if (k < kn && n < Nt)
+        v = P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n];
+      Bs[k * LD + n] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < kn; ++k) {
+      T av[4], bv[4];
+      ld4(As + k * LD + ty * 4, av);
+      ld4(Bs + k * LD + tx * 4, bv);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
     }
   }
+  T* C = mbuf<T>(tab, P.sys, P.c_buf, r) + P.c_off;
+  const T alpha = (T)P.alpha;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int m = ty * 4 + a, n = tx * 4 + b;
+      if (m < Mt && n < Nt) {
+        const int64_t gm = P.m0 + m, gn = P.n0 + n;
+        atomicAdd(P.tc ? C + gn * P.ldc + gm : C + gm * P.ldc + gn, alpha * acc[a][b]);
+      }
+    }
 }
 
 constexpr int VR = 8;   // roots per pass inside a GEMV CTA
@@ -252,20 +445,46 @@ void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s
   PN_CUDA(cudaGetLastError());
 }
 
+template <typename T, int NT, int MAXT>
+static void launch_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
+                         int dk2, int dn, int rpc, cudaStream_t s) {
+  const int Mp = pad4(dm), K1p = pad4(dk1), Np = pad4(dn);
+  // C register tiles per vector: rows/4 x cols/4; at most NT * MAXT per CTA
+  const int tiles = (Mp / 4) * (Np / 4);
+  rpc = std::max(1, std::min(rpc, std::min(t.max_nvec, NT * MAXT / tiles)));
+  auto smem_of = [&](int r) { return (size_t)(dk1 * Mp + dk2 * Np + dk2 * r * K1p + K1p * r * Np) * sizeof(T); };
+  const size_t limit = 200 * 1024;
+  while (rpc > 1 && smem_of(rpc) > limit) --rpc;
+  PN_CHECK(smem_of(rpc) <= limit && tiles <= NT * MAXT, PNOEOM_ERR_UNSUPPORTED,
+           "PNO blocks too large for the grouped sandwich kernel");
+  const size_t smem = smem_of(rpc);
+  ensure_dynamic_smem((const void*)k_sandwich_small<T, NT, MAXT>, smem);
+  const int ychunks = (t.max_nvec + rpc - 1) / rpc;
+  k_sandwich_small<T, NT, MAXT><<<dim3(ngroups, ychunks), NT, smem, s>>>(d_probs, d_group_start, t, rpc, dm, dk1, dk2, dn);
+  PN_CUDA(cudaGetLastError());
+}
+
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
                         int dk2, int dn, int roots_per_cta, cudaStream_t s) {
   if (ngroups <= 0 || t.max_nvec <= 0) return;
-  const size_t base = (size_t)(dm * dk1 + dk2 * dn + dk1 * dk2 + dk1 * dn) * sizeof(T);
-  const size_t per_root = (size_t)dm * dn * sizeof(T);
-  const size_t limit = 200 * 1024;
-  PN_CHECK(base + per_root <= limit, PNOEOM_ERR_UNSUPPORTED, "PNO blocks too large for the grouped sandwich kernel");
-  int rpc = std::max(1, std::min(roots_per_cta, t.max_nvec));
-  rpc = (int)std::min<size_t>(rpc, (limit - base) / per_root);
-  const size_t smem = base + (size_t)rpc * per_root;
-  ensure_dynamic_smem((const void*)k_sandwich_small<T>, smem);
-  const int ychunks = (t.max_nvec + rpc - 1) / rpc;
-  k_sandwich_small<T><<<dim3(ngroups, ychunks), 256, smem, s>>>(d_probs, d_group_start, t, rpc, dm, dk1, dk2, dn);
+  const int big = std::max(std::max(dm, dn), std::max(dk1, dk2));
+  PN_CHECK(big <= SMALL_DIM, PNOEOM_ERR_UNSUPPORTED, "block too large for the grouped sandwich kernel");
+  if (big <= 16)
+    launch_small<T, 128, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
+  else if (big <= 32 || sizeof(T) == 8)
+    launch_small<T, 256, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
+  else
+    launch_small<T, 256, 4>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
+}
+
+template <typename T>
+void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cudaStream_t s) {
+  if (nprob <= 0 || t.max_nvec <= 0) return;
+  if (tile == 64)
+    k_dense<T, 64><<<dim3(nprob, t.max_nvec), 256, 0, s>>>(d_probs, t);
+  else
+    k_dense<T, 32><<<dim3(nprob, t.max_nvec), 64, 0, s>>>(d_probs, t);
   PN_CUDA(cudaGetLastError());
 }
 
@@ -275,5 +494,7 @@ template void run_gemv<double>(const VProb*, int, const SysTable&, cudaStream_t)
 template void run_gemv<float>(const VProb*, int, const SysTable&, cudaStream_t);
 template void run_sandwich_small<double>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, cudaStream_t);
 template void run_sandwich_small<float>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, cudaStream_t);
+template void run_dense<double>(const DProb*, int, const SysTable&, int, cudaStream_t);
+template void run_dense<float>(const DProb*, int, const SysTable&, int, cudaStream_t);
 
 }  // namespace pnoeom

@@ -1,6 +1,7 @@
 // The sigma program: R-independent PNO-space operator blocks (the "pool")
-// plus two problem lists applied to a batch of packed vectors.
-//   * Sandwich problems  C += alpha * opA(A) * opX(X) * opB(B)   (small blocks)
+// plus problem lists applied to a batch of packed vectors.
+//   * Sandwich problems  C += alpha * opA(A) * (opX(X) + xb opX(X)^T) * opB(B)   (small blocks)
+//   * Dense problems     C += alpha * opA(A) * opB(B)   (GEMM tiles, split K)
 //   * GEMV problems      c += alpha * A * x   (dense blocks; all roots per CTA)
 // Operands are addressed by (buffer, offset).  Buffers: POOL (shared by all
 // roots), RIN (input vector of the root), WORK (per-root intermediates),
@@ -20,6 +21,19 @@ struct SProb {
   int lda, ldx, ldb, ldc;
   int ta, tx, tb, tc;                 // transposed storage flags; tc: C^T is stored
   int m0, n0;                         // output tile origin (tiles of at most 64 x 64)
+  double alpha;
+  double xb;                          // coefficient of opX(X)^T (square X); 0: opX(X) alone
+};
+
+// One output tile (tile x tile) and K chunk of a dense product.
+struct DProb {
+  int64_t a_off, b_off, c_off;
+  int sys;
+  int a_buf, b_buf, c_buf;
+  int M, N, K;                        // A: M x K, B: K x N, C: M x N
+  int lda, ldb, ldc;
+  int ta, tb, tc;
+  int m0, n0, k0, klen;
   double alpha;
 };
 
@@ -60,14 +74,20 @@ struct SysTable {
 
 template <typename T>
 void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_elems, cudaStream_t s);
-// all dims <= SMALL_DIM, single tile: A and B staged once, every root in the same CTA.
-// Problems are grouped by output block: group g is probs[group_start[g] .. group_start[g+1]),
-// all with the same C block; the CTA accumulates the group for every root in shared
-// memory and adds it to C once.
+// Output tiles and operands with every dim <= SMALL_DIM.  Problems are grouped by
+// output tile: group g is probs[group_start[g] .. group_start[g+1]), all with the same
+// C tile; a CTA takes one group and up to roots_per_cta vectors, stages A and B once
+// per problem, stacks the vectors' X blocks so both products of the sandwich are one
+// register-tiled GEMM each, keeps the C tile of every vector in registers over the
+// group and adds it to C once.  dm, dk1, dk2, dn bound the tile rows, the rows and
+// columns of the staged X block, and the tile columns of every problem of the set.
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
                         int dk2, int dn, int roots_per_cta, cudaStream_t s);
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
+// tile = 64 (256 threads) or 32 (64 threads): the edge of the output tiles of the list.
+template <typename T>
+void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cudaStream_t s);
 
 }  // namespace pnoeom

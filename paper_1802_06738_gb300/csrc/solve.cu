@@ -63,12 +63,19 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     }
     return n;
   };
+  // launch order: Y products -> FvR GEMM; FoR; Z GEMM -> E3 products; the sigma classes
+  // (all accumulate into sigma, in any order)
   int n0 = 0, n2 = 0;
   timed(0, [&] {
     n0 = small(prog.small1);
     run_sandwich<T>(prog.gen1.get(), prog.n_gen1, t, prog.smem_elems, s);
   });
+  timed(4, [&] { run_dense<T>(prog.d1.get(), prog.n_d1, t, 64, s); });
   timed(1, [&] { run_gemv<T>(prog.v1.get(), prog.n_v1, t, s); });
+  timed(5, [&] {
+    run_dense<T>(prog.d2.get(), prog.n_d2, t, 64, s);
+    run_dense<T>(prog.d3.get(), prog.n_d3, t, 32, s);
+  });
   timed(2, [&] {
     n2 = small(prog.small2);
     run_sandwich<T>(prog.gen2.get(), prog.n_gen2, t, prog.smem_elems, s);
@@ -79,6 +86,8 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     P->prof_launches[1] += prog.n_v1 > 0;
     P->prof_launches[2] += n2 + (prog.n_gen2 > 0);
     P->prof_launches[3] += prog.n_v2 > 0;
+    P->prof_launches[4] += prog.n_d1 > 0;
+    P->prof_launches[5] += (prog.n_d2 > 0) + (prog.n_d3 > 0);
   }
 }
 template void run_program<double>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*);
@@ -634,8 +643,12 @@ void batch_merge(pnoeom_batch* B, cudaStream_t s, bool tune) {
     auto addv = [&](std::vector<VProb>& dst, const std::vector<VProb>& src) {
       for (VProb q : src) { q.sys = k; dst.push_back(q); }
     };
+    auto addd = [&](std::vector<DProb>& dst, const std::vector<DProb>& src) {
+      for (DProb q : src) { q.sys = k; dst.push_back(q); }
+    };
     add(G.h_gen1, Pg.h_gen1); add(G.h_gen2, Pg.h_gen2);
     addv(G.h_v1, Pg.h_v1); addv(G.h_v2, Pg.h_v2);
+    addd(G.h_d1, Pg.h_d1); addd(G.h_d2, Pg.h_d2); addd(G.h_d3, Pg.h_d3);
     G.smem_elems = std::max(G.smem_elems, Pg.smem_elems);
     for (int phase = 0; phase < 2; ++phase)
       for (int b = 0; b < 3; ++b) {
