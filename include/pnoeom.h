@@ -255,11 +255,13 @@ int pno_set_timing(pnoeom_pno* pno, int enable);
 int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, const char** name, int* launches,
                      double* ms, double* bytes, double* flops);
 
-/* Autotuner record: pno_build times sigma for every candidate (group size of
- * the output-grouped small-block kernel x vectors per CTA) and keeps the
- * fastest.  Writes up to `ncand` candidates (group size, vectors per CTA, ms
- * per sigma of nroots_sa vectors) and the chosen index in *choice.  Any
- * pointer may be NULL. */
+/* Autotuner record: pno_build times every launch of the output-grouped
+ * small-block kernel (one per size bucket and phase) for every candidate
+ * (group size x vectors per CTA) on nroots_sa FP32 vectors, and each launch
+ * keeps its own fastest candidate.  Writes up to `ncand` candidates (group
+ * size, vectors per CTA, summed ms of all those launches under that
+ * candidate) and in *choice the index of the candidate with the smallest
+ * sum.  Any pointer may be NULL. */
 int pno_autotune_info(const pnoeom_pno* pno, int ncand, int* group_sizes, int* roots_per_cta, double* ms, int* choice);
 
 /* Seconds spent in the last pno_build of this handle (setup time). */

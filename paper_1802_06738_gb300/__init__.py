@@ -246,14 +246,15 @@ class PNO:
         return e, rn, it.value, rc == OK
 
     def autotune_info(self):
-        """Candidates [(group size, vectors per CTA, ms per sigma)] and the chosen index."""
+        """Candidates [(group size, vectors per CTA, summed ms of the small-block launches)] and the index
+        of the candidate fastest over all launches together (each launch keeps its own fastest)."""
         import numpy as np
-        gs = (ctypes.c_int * 32)()
-        rp = (ctypes.c_int * 32)()
-        ms = np.zeros(32)
+        gs = (ctypes.c_int * 64)()
+        rp = (ctypes.c_int * 64)()
+        ms = np.zeros(64)
         ch = ctypes.c_int()
-        _check(lib().pno_autotune_info(self.h, 32, gs, rp, _dptr(ms), ctypes.byref(ch)))
-        n = sum(1 for k in range(32) if gs[k] > 0)
+        _check(lib().pno_autotune_info(self.h, 64, gs, rp, _dptr(ms), ctypes.byref(ch)))
+        n = sum(1 for k in range(64) if gs[k] > 0)
         return [(gs[k], rp[k], float(ms[k])) for k in range(n)], ch.value
 
     def set_timing(self, enable=True):

@@ -905,6 +905,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     if (q.b_buf != B_NONE && q.K2 > SMALL_DIM) return -1;
     int e[4];
     extents(q, e);
+    // the small kernel forms X + xb X^T in shared memory: the staged block must be all of square X
+    const int xr0 = q.a_buf != B_NONE ? 0 : q.m0, xc0 = q.b_buf != B_NONE ? 0 : q.n0;
+    if (q.xb != 0.0 && (e[1] != e[2] || xr0 != xc0 || e[1] != q.K1)) return -1;
     const int d = std::max(std::max(e[0], e[1]), std::max(e[2], e[3]));
     return d <= 16 ? 0 : d <= 32 ? 1 : d <= SMALL_DIM ? 2 : -1;
   };

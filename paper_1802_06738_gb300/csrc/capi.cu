@@ -94,7 +94,7 @@ double pno_build_seconds(const pnoeom_pno* pno) { return pno ? pno->build_second
 int pno_autotune_info(const pnoeom_pno* pno, int ncand, int* group_sizes, int* roots_per_cta, double* ms, int* choice) {
   return guard([&] {
     PN_CHECK(pno, PNOEOM_ERR_INVALID_ARG, "pno is NULL");
-    const int total = pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND;
+    const int total = pnoeom::NTUNE;
     for (int c = 0; c < std::min(ncand, total); ++c) {
       if (group_sizes) group_sizes[c] = pnoeom::GROUP_CAND[c / pnoeom::NRPC_CAND];
       if (roots_per_cta) roots_per_cta[c] = pnoeom::RPC_CAND[c % pnoeom::NRPC_CAND];

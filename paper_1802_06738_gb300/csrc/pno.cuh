@@ -12,10 +12,11 @@
 #include <thread>
 
 namespace pnoeom {
-constexpr int NGROUP_CAND = 4;
-constexpr int GROUP_CAND[NGROUP_CAND] = {1, 2, 4, 8};
-constexpr int NRPC_CAND = 3;
-constexpr int RPC_CAND[NRPC_CAND] = {1, 2, 8};
+constexpr int NGROUP_CAND = 5;
+constexpr int GROUP_CAND[NGROUP_CAND] = {2, 4, 8, 16, 32};
+constexpr int NRPC_CAND = 6;
+constexpr int RPC_CAND[NRPC_CAND] = {1, 2, 3, 4, 6, 8};
+constexpr int NTUNE = NGROUP_CAND * NRPC_CAND;
 
 // Small sandwich problems of one size bucket: ordered by output block, with one
 // group-boundary list per candidate group size.
@@ -25,6 +26,8 @@ struct SmallSet {
   int ngroups[NGROUP_CAND] = {0};
   int dims[4] = {1, 1, 1, 1};   // max M, K1, K2, N
   int nprob = 0;
+  int gchoice = 2, rchoice = NRPC_CAND - 1;       // tuned (group size, vectors per CTA) of this set
+  double tune_ms[NTUNE] = {0};
   std::vector<SProb> h_probs;                      // host copies (batch merging)
   std::vector<int> h_starts[NGROUP_CAND];
 };
@@ -38,7 +41,7 @@ struct Program {
   int n_gen1 = 0, n_gen2 = 0, n_v1 = 0, n_v2 = 0, n_d1 = 0, n_d2 = 0, n_d3 = 0;
   SmallSet small1[3], small2[3];   // small sandwich problems per size bucket
   int smem_elems = 1;
-  int group_choice = 0, rpc_choice = 0;
+  int group_choice = 2, rpc_choice = NRPC_CAND - 1;   // fastest single candidate for every set (reported)
   std::vector<SProb> h_gen1, h_gen2;
   std::vector<VProb> h_v1, h_v2;
   std::vector<DProb> h_d1, h_d2, h_d3;
@@ -67,7 +70,7 @@ struct pnoeom_pno {
   pnoeom::DBuf<double> pool64;
   pnoeom::DBuf<float> pool32;
   pnoeom::Program prog;
-  double tune_ms[pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND] = {0};
+  double tune_ms[pnoeom::NTUNE] = {0};
   static constexpr int NCLS = 6;             // kernel classes of the sigma program (timing)
   int prof_launches[NCLS] = {0};
   int smem_elems = 0;
@@ -103,7 +106,7 @@ struct pnoeom_batch {
   cudaGraphExec_t exec = nullptr;
   bool use_graph = true;
   int graph_launches = 0, graph_updates = 0, graph_instantiations = 0;
-  double tune_ms[pnoeom::NGROUP_CAND * pnoeom::NRPC_CAND] = {0};
+  double tune_ms[pnoeom::NTUNE] = {0};
   size_t footprint = 0;
   ~pnoeom_batch() { if (exec) cudaGraphExecDestroy(exec); }
 };

@@ -105,12 +105,24 @@ __device__ __forceinline__ int fdiv(int e, float rd) { return __float2int_rz(((f
 
 __host__ __device__ constexpr int pad4(int x) { return (x + 3) & ~3; }
 
+// Asynchronous global -> shared copy of one element (cp.async, no register round trip).
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T* dst, const T* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(sizeof(T)));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
 // Grouped small sandwich (see run_sandwich_small).  Shared memory, with the set's
-// bounds dm, dk1 (rows of the staged X block), dk2 (its columns), dn padded to 4:
+// bounds dm, dk1 (rows of the staged X block), dk2 (its columns), dn padded to 4,
+// and two copies (problem g and g + 1) of the staged operands:
 //   As [dk1][Mp]        A^T (tile rows)
 //   Bs [dk2][Np]        B (tile columns)
-//   Xs [dk2][R * K1p]   X_eff^T of the R vectors side by side
-//   Ts [K1p][R * Np]    alpha X_eff B of the R vectors side by side
+//   Xs [dk2][R * K1p]   opX(X)^T of the R vectors side by side (X_eff after the merge pass)
+// and one copy of
+//   Ts [K1p][R * Np]    alpha X_eff B of the R vectors side by side.
+// The operands of problem g + 1 are copied with cp.async while problem g computes.
 // Product 1: Ts = alpha Xs^T Bs, rows (vector, a) x columns n, 4 x 4 register tiles.
 // Product 2: C[m][(vector, n)] += As^T Ts, 4 x 4 register tiles that each thread
 // keeps for the whole group (MAXT tiles per thread).
@@ -121,11 +133,11 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Mp = pad4(dm), K1p = pad4(dk1), Np = pad4(dn);
   const int xld = rpc * K1p, tld = rpc * Np;
-  T* As = reinterpret_cast<T*>(smem_raw);
-  T* Bs = As + dk1 * Mp;
-  T* Xs = Bs + dk2 * Np;
-  T* Ts = Xs + dk2 * xld;
-  const int total = dk1 * Mp + dk2 * Np + dk2 * xld + K1p * tld;
+  const int asz = dk1 * Mp, bsz = dk2 * Np, xsz = dk2 * xld;
+  const int stage = asz + bsz + xsz;   // one copy of the staged operands (a multiple of 4)
+  T* S0 = reinterpret_cast<T*>(smem_raw);
+  T* Ts = S0 + 2 * stage;
+  const int total = 2 * stage + K1p * tld;
   const int tid = threadIdx.x;
   const int g0 = gstart[blockIdx.x], g1 = gstart[blockIdx.x + 1];
   const SProb P0 = probs[g0];
@@ -136,7 +148,7 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
   const int nt4 = (Nt + 3) >> 2;
   const int nct = ((Mt + 3) >> 2) * nr * nt4;
   // padding is read (never stored) by the 4-wide tiles: keep it finite
-  for (int e = tid; e < total; e += NT) As[e] = T(0);
+  for (int e = tid; e < total; e += NT) S0[e] = T(0);
   int cm4[MAXT], cr[MAXT], cn4[MAXT];
   T acc[MAXT][4][4];
 #pragma unroll
@@ -150,28 +162,28 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[j][a][b] = T(0);
   }
-  for (int g = g0; g < g1; ++g) {
-    const SProb P = probs[g];
+  // issue the copies of problem P into stage buffer `buf`
+  auto issue = [&](const SProb& P, int buf) {
+    T* As = S0 + buf * stage;
+    T* Bs = As + asz;
+    T* Xs = Bs + bsz;
     const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
     const int K1 = P.K1;
-    const int kr = hasA ? K1 : Mt;       // rows of the staged X block (= rows of T)
-    const int kc = hasB ? P.K2 : Nt;     // its columns
+    const int kr = hasA ? K1 : Mt, kc = hasB ? P.K2 : Nt;
     const int xr0 = hasA ? 0 : P.m0, xc0 = hasB ? 0 : P.n0;
-    const T alpha = (T)P.alpha, xb = (T)P.xb;
-    __syncthreads();
     if (hasA) {
       const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
       if (P.ta) {   // stored K1 x M: element (m, k) at A[k lda + m]
         const float rd = 1.0f / (float)Mt;
         for (int e = tid; e < Mt * K1; e += NT) {
           const int k = fdiv(e, rd), m = e - k * Mt;
-          As[k * Mp + m] = A[(int64_t)k * P.lda + P.m0 + m];
+          cp_async_el(As + k * Mp + m, A + (int64_t)k * P.lda + P.m0 + m);
         }
       } else {
         const float rd = 1.0f / (float)K1;
         for (int e = tid; e < Mt * K1; e += NT) {
           const int m = fdiv(e, rd), k = e - m * K1;
-          As[k * Mp + m] = A[(int64_t)(P.m0 + m) * P.lda + k];
+          cp_async_el(As + k * Mp + m, A + (int64_t)(P.m0 + m) * P.lda + k);
         }
       }
     }
@@ -182,27 +194,63 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
         const float rd = 1.0f / (float)K2;
         for (int e = tid; e < K2 * Nt; e += NT) {
           const int n = fdiv(e, rd), k = e - n * K2;
-          Bs[k * Np + n] = Bm[(int64_t)(P.n0 + n) * P.ldb + k];
+          cp_async_el(Bs + k * Np + n, Bm + (int64_t)(P.n0 + n) * P.ldb + k);
         }
       } else {
         const float rd = 1.0f / (float)Nt;
         for (int e = tid; e < K2 * Nt; e += NT) {
           const int k = fdiv(e, rd), n = e - k * Nt;
-          Bs[k * Np + n] = Bm[(int64_t)k * P.ldb + P.n0 + n];
+          cp_async_el(Bs + k * Np + n, Bm + (int64_t)k * P.ldb + P.n0 + n);
         }
       }
     }
-    {
+    {   // opX(X)[xr0 + a][xc0 + b] -> Xs[b][r K1p + a]
       const int per = kr * kc;
       const float rd_per = 1.0f / (float)per, rd_kr = 1.0f / (float)kr;
       for (int e = tid; e < nr * per; e += NT) {
         const int r = fdiv(e, rd_per), rem = e - r * per;
         const int b = fdiv(rem, rd_kr), a = rem - b * kr;
         const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
-        Xs[b * xld + r * K1p + a] = xeff(X, P.ldx, P.tx, xb, xr0 + a, xc0 + b);
+        const int xa = xr0 + a, xbb = xc0 + b;
+        cp_async_el(Xs + b * xld + r * K1p + a, P.tx ? X + (int64_t)xbb * P.ldx + xa : X + (int64_t)xa * P.ldx + xbb);
       }
     }
-    __syncthreads();
+    cp_async_commit();
+  };
+  __syncthreads();   // zero fill done before the first copies land
+  issue(P0, 0);
+  for (int g = g0; g < g1; ++g) {
+    const int buf = (g - g0) & 1;
+    cp_async_wait_all();
+    __syncthreads();   // problem g staged; every thread is done with problem g - 1
+    if (g + 1 < g1) issue(probs[g + 1], buf ^ 1);
+    const SProb P = probs[g];
+    T* As = S0 + buf * stage;
+    T* Bs = As + asz;
+    T* Xs = Bs + bsz;
+    const bool hasA = P.a_buf != B_NONE, hasB = P.b_buf != B_NONE;
+    const int K1 = P.K1;
+    const int kr = hasA ? K1 : Mt, kc = hasB ? P.K2 : Nt;
+    const T alpha = (T)P.alpha, xb = (T)P.xb;
+    if (xb != T(0)) {   // X_eff = opX(X) + xb opX(X)^T, in place on pairs (a <= b) of the square block
+      const int per = kr * kr;
+      const float rd_per = 1.0f / (float)per, rd_kr = 1.0f / (float)kr;
+      for (int e = tid; e < nr * per; e += NT) {
+        const int r = fdiv(e, rd_per), rem = e - r * per;
+        const int b = fdiv(rem, rd_kr), a = rem - b * kr;
+        if (a > b) continue;
+        T* xab = Xs + b * xld + r * K1p + a;   // opX(X)[a][b]
+        T* xba = Xs + a * xld + r * K1p + b;   // opX(X)[b][a]
+        const T u = *xab, w = *xba;
+        if (a == b) {
+          *xab = u + xb * u;
+        } else {
+          *xab = u + xb * w;
+          *xba = w + xb * u;
+        }
+      }
+      __syncthreads();
+    }
     {   // product 1
       const int ka4 = (kr + 3) >> 2;
       const int n1 = nr * ka4 * nt4;
@@ -452,7 +500,7 @@ static void launch_small(const SProb* d_probs, const int* d_group_start, int ngr
   // C register tiles per vector: rows/4 x cols/4; at most NT * MAXT per CTA
   const int tiles = (Mp / 4) * (Np / 4);
   rpc = std::max(1, std::min(rpc, std::min(t.max_nvec, NT * MAXT / tiles)));
-  auto smem_of = [&](int r) { return (size_t)(dk1 * Mp + dk2 * Np + dk2 * r * K1p + K1p * r * Np) * sizeof(T); };
+  auto smem_of = [&](int r) { return (size_t)(2 * (dk1 * Mp + dk2 * Np + dk2 * r * K1p) + K1p * r * Np) * sizeof(T); };
   const size_t limit = 200 * 1024;
   while (rpc > 1 && smem_of(rpc) > limit) --rpc;
   PN_CHECK(smem_of(rpc) <= limit && tiles <= NT * MAXT, PNOEOM_ERR_UNSUPPORTED,

@@ -32,6 +32,51 @@ SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* wor
 }
 
 template <typename T>
+static void run_small_set(const SmallSet& S, int c, int rr, const SysTable& t, cudaStream_t s) {
+  run_sandwich_small<T>(S.probs.get(), S.starts[c].get(), S.ngroups[c], t, S.dims[0], S.dims[1], S.dims[2], S.dims[3],
+                        RPC_CAND[rr], s);
+}
+
+// Time every small-sandwich set of the program alone for every (group size, vectors
+// per CTA) candidate (CUDA events on s) and keep each set's fastest.  sum_ms[c] is the
+// summed time of all sets under candidate c; the program's reported choice is the
+// candidate with the smallest sum.
+template <typename T>
+static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* sum_ms) {
+  cudaEvent_t e0, e1;
+  PN_CUDA(cudaEventCreate(&e0));
+  PN_CUDA(cudaEventCreate(&e1));
+  for (int c = 0; c < NTUNE; ++c) sum_ms[c] = 0;
+  for (SmallSet* sets : {prog.small1, prog.small2})
+    for (int k = 0; k < 3; ++k) {
+      SmallSet& S = sets[k];
+      if (!S.nprob) continue;
+      double best = 1e300;
+      for (int c = 0; c < NGROUP_CAND; ++c)
+        for (int rr = 0; rr < NRPC_CAND; ++rr) {
+          run_small_set<T>(S, c, rr, t, s);   // warm-up
+          PN_CUDA(cudaEventRecord(e0, s));
+          for (int q = 0; q < 3; ++q) run_small_set<T>(S, c, rr, t, s);
+          PN_CUDA(cudaEventRecord(e1, s));
+          PN_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          const int idx = c * NRPC_CAND + rr;
+          S.tune_ms[idx] = ms / 3;
+          sum_ms[idx] += ms / 3;
+          if (ms < best) { best = ms; S.gchoice = c; S.rchoice = rr; }
+        }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int pick = 0;
+  for (int c = 1; c < NTUNE; ++c)
+    if (sum_ms[c] < sum_ms[pick]) pick = c;
+  prog.group_choice = pick / NRPC_CAND;
+  prog.rpc_choice = pick % NRPC_CAND;
+}
+
+template <typename T>
 void run_program(const Program& prog, const SysTable& t, const int64_t* out_len, const int64_t* work_len,
                  cudaStream_t s, pnoeom_pno* timing_owner) {
   for (int k = 0; k < t.nsys; ++k) {
@@ -51,14 +96,12 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     PN_CUDA(cudaEventRecord(e1, s));
     P->events.push_back({cls, {e0, e1}});
   };
-  const int g = prog.group_choice, rpc = RPC_CAND[prog.rpc_choice];
   auto small = [&](const SmallSet* sets) {
     int n = 0;
     for (int k = 0; k < 3; ++k) {
       const SmallSet& S = sets[k];
       if (!S.nprob) continue;
-      run_sandwich_small<T>(S.probs.get(), S.starts[g].get(), S.ngroups[g], t, S.dims[0], S.dims[1], S.dims[2], S.dims[3],
-                            rpc, s);
+      run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
       ++n;
     }
     return n;
@@ -116,29 +159,13 @@ void autotune(pnoeom_pno* P, cudaStream_t s) {
   const int nv = std::max(1, P->nroots_sa);
   DBuf<float> r((size_t)nv * P->L), o((size_t)nv * P->L);
   r.zero(s);
-  cudaEvent_t e0, e1;
-  PN_CUDA(cudaEventCreate(&e0));
-  PN_CUDA(cudaEventCreate(&e1));
-  double best = 1e300;
-  int pick = 0, pick_r = 0;
-  for (int c = 0; c < NGROUP_CAND; ++c)
-    for (int rr = 0; rr < NRPC_CAND; ++rr) {
-      P->prog.group_choice = c;
-      P->prog.rpc_choice = rr;
-      apply_sigma<float>(P, nv, r.get(), o.get(), s);   // warm-up
-      PN_CUDA(cudaEventRecord(e0, s));
-      for (int k = 0; k < 3; ++k) apply_sigma<float>(P, nv, r.get(), o.get(), s);
-      PN_CUDA(cudaEventRecord(e1, s));
-      PN_CUDA(cudaEventSynchronize(e1));
-      float ms = 0;
-      PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      P->tune_ms[c * NRPC_CAND + rr] = ms / 3;
-      if (ms < best) { best = ms; pick = c; pick_r = rr; }
-    }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  P->prog.group_choice = pick;
-  P->prog.rpc_choice = pick_r;
+  DBuf<float>& work = work_of<float>(P);
+  if (work.n < (size_t)nv * P->work_len) work.alloc((size_t)nv * P->work_len, &P->footprint);
+  SysTable t;
+  t.nsys = 1;
+  t.max_nvec = nv;
+  t.s[0] = sysbuf(P, nv, r.get(), o.get(), work.get(), true);
+  tune_sets<float>(P->prog, t, s, P->tune_ms);
 }
 
 // ---------------------------------------------------------------------------
@@ -669,41 +696,28 @@ void batch_merge(pnoeom_batch* B, cudaStream_t s, bool tune) {
   B->w32.resize(n);
   G.group_choice = B->members[0]->prog.group_choice;
   G.rpc_choice = B->members[0]->prog.rpc_choice;
-  if (!tune) return;
-  // autotune the merged program: FP32 sigma of nroots_sa vectors per member
-  std::vector<DBuf<float>> r(n), o(n);
-  std::vector<const void*> rp(n);
-  std::vector<void*> op(n);
-  std::vector<int> nv(n);
-  for (int k = 0; k < n; ++k) {
-    nv[k] = std::max(1, B->members[k]->nroots_sa);
-    r[k].alloc((size_t)nv[k] * B->members[k]->L);
-    o[k].alloc((size_t)nv[k] * B->members[k]->L);
-    r[k].zero(s);
-    rp[k] = r[k].get(); op[k] = o[k].get();
-  }
-  cudaEvent_t e0, e1;
-  PN_CUDA(cudaEventCreate(&e0));
-  PN_CUDA(cudaEventCreate(&e1));
-  double best = 1e300;
-  int pick = 0, pick_r = 0;
-  for (int c = 0; c < NGROUP_CAND; ++c)
-    for (int rr = 0; rr < NRPC_CAND; ++rr) {
-      G.group_choice = c; G.rpc_choice = rr;
-      batch_sigma(B, nv.data(), rp.data(), op.data(), PNOEOM_FP32, s);
-      PN_CUDA(cudaEventRecord(e0, s));
-      for (int q = 0; q < 2; ++q) batch_sigma(B, nv.data(), rp.data(), op.data(), PNOEOM_FP32, s);
-      PN_CUDA(cudaEventRecord(e1, s));
-      PN_CUDA(cudaEventSynchronize(e1));
-      float ms = 0;
-      PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      B->tune_ms[c * NRPC_CAND + rr] = ms / 2;
-      if (ms < best) { best = ms; pick = c; pick_r = rr; }
+  for (int phase = 0; phase < 2; ++phase)   // untuned merge: each set takes the first member's choice
+    for (int b = 0; b < 3; ++b) {
+      SmallSet& D = phase == 0 ? G.small1[b] : G.small2[b];
+      const SmallSet& S0 = phase == 0 ? B->members[0]->prog.small1[b] : B->members[0]->prog.small2[b];
+      D.gchoice = S0.gchoice; D.rchoice = S0.rchoice;
     }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  G.group_choice = pick;
-  G.rpc_choice = pick_r;
+  if (!tune) return;
+  // autotune the merged program's small sets: FP32, nroots_sa vectors per member
+  std::vector<DBuf<float>> r(n), o(n);
+  SysTable t{};
+  t.nsys = n;
+  for (int k = 0; k < n; ++k) {
+    pnoeom_pno* P = B->members[k];
+    const int nv = std::max(1, P->nroots_sa);
+    r[k].alloc((size_t)nv * P->L);
+    o[k].alloc((size_t)nv * P->L);
+    r[k].zero(s);
+    if (B->w32[k].n < (size_t)nv * P->work_len) B->w32[k].alloc((size_t)nv * P->work_len);
+    t.max_nvec = std::max(t.max_nvec, nv);
+    t.s[k] = sysbuf(P, nv, r[k].get(), o[k].get(), B->w32[k].get(), true);
+  }
+  tune_sets<float>(G, t, s, B->tune_ms);
 }
 
 // Capture `body` (stream operations on s) as a CUDA graph and launch it, reusing
