@@ -5,9 +5,12 @@ Calls only oracle/ and the seeded generator.  For a workload it stores:
   * the Davidson excitation energies (the oracle's FP64 solve, Sec. 2);
   * sigma of one seeded canonical trial vector, projected (Sec. 2), for the
     singles and a sample of pair blocks, in the canonical basis (so the
-    comparison does not depend on PNO phases).
+    comparison does not depend on PNO phases).  For v > 32 each sampled pair
+    block keeps SIGMA_SAMPLES entries at seeded positions instead of all v^2.
 
-Usage: python tests/golden/make_golden.py medium   (about an hour on 8 cores)
+Usage: python tests/golden/make_golden.py medium   (about two hours on 8 cores)
+       python tests/golden/make_golden.py medium --sigma-only
+           (recomputes only the sigma fields of an existing fixture, ~2 minutes)
 """
 from __future__ import annotations
 
@@ -29,6 +32,22 @@ WORKLOADS = {
     "medium": dict(o=20, v=200, naux=600, nroots=6, t_pno=1e-7, seed=2, gs="mp1"),
 }
 SAMPLE_PAIRS = {"small": [(0, 0), (0, 4), (2, 3), (4, 4)], "medium": [(0, 19), (5, 5), (7, 12), (18, 19), (19, 19)]}
+SIGMA_SAMPLES = 256
+
+
+def sigma_fields(s1, s2, pairs, v):
+    """Sigma of the trial vector: singles whole, pair blocks whole (v <= 32) or sampled."""
+    out = {"sigma_trial_seed": 123, "sigma_s1": s1.tolist()}
+    if v <= 32:
+        out["sigma_pairs"] = {f"{i},{j}": s2[i, j].tolist() for (i, j) in pairs}
+    else:
+        rng = np.random.default_rng(7)
+        smp = {}
+        for (i, j) in pairs:
+            pos = rng.integers(0, v, size=(SIGMA_SAMPLES, 2))
+            smp[f"{i},{j}"] = [[int(a), int(b), float(s2[i, j, a, b])] for a, b in pos]
+        out["sigma_pair_samples"] = smp
+    return out
 
 
 def trial_vector(o, v, seed=123):
@@ -39,7 +58,7 @@ def trial_vector(o, v, seed=123):
     return r1, 0.5 * (r2 + r2.transpose(1, 0, 3, 2))
 
 
-def main(name):
+def main(name, sigma_only=False):
     w = WORKLOADS[name]
     o, v = w["o"], w["v"]
     t0 = time.time()
@@ -58,16 +77,24 @@ def main(name):
     s1, s2 = sp.unpack(ps(sp.pack(r1, r2)))
     out = {"workload": name, **{k: w[k] for k in ("o", "v", "naux", "nroots", "t_pno", "seed", "gs")},
            "n_ij": sp.n_ij.tolist(), "n_i": sp.n_i.tolist(), "vec_len": int(sp.length),
-           "sigma_trial_seed": 123, "sigma_s1": s1.tolist(),
-           "sigma_pairs": {f"{i},{j}": s2[i, j].tolist() for (i, j) in SAMPLE_PAIRS[name]}}
+           **sigma_fields(s1, s2, SAMPLE_PAIRS[name], v)}
     print(f"sigma done {time.time() - t0:.0f} s", flush=True)
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    if sigma_only:   # keep the stored solve, replace the sigma fields
+        old = json.load(open(path))
+        for k in ("sigma_pairs", "sigma_pair_samples"):
+            old.pop(k, None)
+        old.update(out)
+        json.dump(old, open(path, "w"))
+        print(f"updated sigma fields of {path}", flush=True)
+        return
     e, X, rn, it, conv = davidson.solve(ps, sp, w["nroots"])
     out.update({"energies": e.tolist(), "residual_norms": rn.tolist(), "iterations": int(it), "converged": bool(conv),
                 "cis_energies": sp.cis_omega.tolist(), "seconds": time.time() - t0})
-    path = os.path.join(HERE, f"oracle_{name}.json")
     json.dump(out, open(path, "w"))
     print(f"wrote {path}: energies {e}, converged {conv}, {time.time() - t0:.0f} s", flush=True)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "small")
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    main(args[0] if args else "small", sigma_only="--sigma-only" in sys.argv)
