@@ -133,7 +133,8 @@ int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, v
  * the device-wide synchronisation cudaMalloc/cudaFree imply, or an
  * application that has handed all device memory to its own pool allocator.
  * It computes exactly what sigma() computes, but its scratch memory (the
- * R-dependent intermediates, nvec * (v*v + o*o) elements) lives in a
+ * R-dependent intermediates, nvec * (v*v + o*o + 2*v*sum_ij n_ij) elements:
+ * FvR, FoR and the two E3 factors Y and Z) lives in a
  * file-scope device array of PNOEOM_NOALLOC_SCRATCH_BYTES bytes that every
  * GPU which loads the library keeps until the process exits.  Calls needing
  * more scratch than that return PNOEOM_ERR_UNSUPPORTED without launching
@@ -144,7 +145,7 @@ int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, v
  * overlap on the GPU race on it, so issue them on one stream or otherwise
  * serialise them.  No cudaMalloc, cudaFree or allocating library routine is
  * called.  Arguments, layouts and errors are those of sigma(). */
-#define PNOEOM_NOALLOC_SCRATCH_BYTES (8u << 20)
+#define PNOEOM_NOALLOC_SCRATCH_BYTES (64u << 20)
 int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
                   int precision, void* cuda_stream);
 

@@ -55,8 +55,9 @@ def test_noalloc_matches_sigma_twice(built, precision, dtype, tol):
 
 def test_noalloc_rejects_oversized_request(built):
     pkg, ctx, gp = built
-    per_vec = (gp.v * gp.v + gp.o * gp.o) * 8
-    nvec = 8 * 1024 * 1024 // per_vec + 1
+    # FP64 scratch per vector: FvR (v^2), FoR (o^2), Y and Z (v * sum n_ij each)
+    per_vec = (gp.v * gp.v + gp.o * gp.o + 2 * gp.v * int(np.sum(gp.n_ij))) * 8
+    nvec = (64 << 20) // per_vec + 1
     r = torch.zeros((1, gp.length), dtype=torch.float64, device="cuda:0")
     rc = pkg.lib().sigma_noalloc(ctx.h, gp.h, nvec, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(r.data_ptr()),
                                  0, None)
