@@ -231,6 +231,23 @@ int pno_get_cis_vectors(const pnoeom_pno* pno, double* b);
 
 int pno_get_cis(const pnoeom_pno* pno, double* omega);
 
+/* Dense FP32 product on the tensor cores: C (M x N) += alpha * A (M x K) * B (K x N),
+ * row-major device buffers (leading dimensions K, N, N).  It runs the tile kernel the
+ * sigma program uses for its dense GEMM tiles (FvR = -U_cat Y and Z = FvR^T U_cat of the
+ * E3 term, Sec. 2): tcgen05 kind::tf32 MMAs with each operand split into a tf32 high
+ * part and a tf32 remainder, hi*hi + hi*lo + lo*hi accumulated in FP32 in tensor memory,
+ * which keeps about 21 bits of every product.  Exported so that kernel can be tested on
+ * its own.  Blocks until done on cuda_stream.  Returns PNOEOM_ERR_INVALID_ARG for
+ * negative sizes or NULL buffers with nonzero sizes. */
+int pnoeom_gemm_tf32x3(pnoeom_ctx* ctx, const float* A, const float* B, float* C, int M, int N, int K, float alpha,
+                       void* cuda_stream);
+
+/* Status word of the tensor-core kernels on the context's device: 0 when every bounded
+ * wait of those kernels completed; bit 0 set when an mbarrier wait ran past its clock
+ * budget (about one second), in which case that tile's contribution was skipped and its
+ * result is invalid.  clear != 0 resets the word.  Synchronises the device. */
+int pnoeom_device_status(pnoeom_ctx* ctx, int clear, int* status);
+
 /* Eigenpairs of a small dense non-symmetric matrix on the host (the Davidson
  * subspace step, Sec. 2).  A: row-major n x n; wr, wi: real and imaginary
  * parts of the eigenvalues (unsorted); VR[i*n + k]: component i of the right

@@ -56,7 +56,7 @@ EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", 
            "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info",
            "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve",
            "pnoeom_server_create", "pnoeom_server_destroy", "pnoeom_server_submit", "pnoeom_server_poll",
-           "pnoeom_server_wait", "pnoeom_server_stats"]
+           "pnoeom_server_wait", "pnoeom_server_stats", "pnoeom_gemm_tf32x3", "pnoeom_device_status"]
 
 
 def lib():
@@ -94,6 +94,8 @@ def lib():
         L.pno_get_occupations.argtypes = [vp, dp]
         L.pno_get_cis_vectors.argtypes = [vp, dp]
         L.pnoeom_small_eig.argtypes = [i, dp, dp, dp, dp]
+        L.pnoeom_gemm_tf32x3.argtypes = [vp, vp, vp, vp, i, i, i, ctypes.c_float, vp]
+        L.pnoeom_device_status.argtypes = [vp, i, ip]
         L.pno_build_seconds.argtypes = [vp]; L.pno_build_seconds.restype = d
         L.pno_set_timing.argtypes = [vp, i]
         L.pno_sigma_timing.argtypes = [vp, i, i, i, ctypes.POINTER(ctypes.c_char_p), ip, dp, dp, dp]
@@ -135,6 +137,19 @@ class Context:
         if self.h:
             lib().pnoeom_destroy(self.h)
             self.h = None
+
+    def gemm_tf32x3(self, A, B, C, alpha=1.0, stream=None):
+        """C += alpha * A @ B for row-major FP32 CUDA tensors (pnoeom_gemm_tf32x3)."""
+        M, K = A.shape
+        N = B.shape[1]
+        _check(lib().pnoeom_gemm_tf32x3(self.h, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                                        ctypes.c_void_p(C.data_ptr()), M, N, K, alpha, _stream_ptr(stream)))
+
+    def device_status(self, clear=True):
+        """Status word of the tensor-core kernels (0: every bounded wait completed)."""
+        v = ctypes.c_int()
+        _check(lib().pnoeom_device_status(self.h, 1 if clear else 0, ctypes.byref(v)))
+        return v.value
 
     def __del__(self):
         try:

@@ -719,8 +719,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
                        int Nn, int abuf, int64_t aoff, int lda, int ta, int K, int bbuf, int64_t boff, int ldb, int tb,
                        double al) {
     if (M <= 0 || Nn <= 0 || K <= 0 || al == 0.0) return;
-    for (int m0 = 0; m0 < M; m0 += tile)
-      for (int n0 = 0; n0 < Nn; n0 += tile)
+    const int tm = tile, tn = tile == DENSE_TILE_TC ? 64 : tile;   // tile rows, tile columns
+    for (int m0 = 0; m0 < M; m0 += tm)
+      for (int n0 = 0; n0 < Nn; n0 += tn)
         for (int k0 = 0; k0 < K; k0 += kchunk) {
           DProb q{};
           q.a_off = aoff; q.b_off = boff; q.c_off = coff;
@@ -729,6 +730,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
           q.lda = lda; q.ldb = ldb; q.ldc = ldc;
           q.ta = ta; q.tb = tb; q.tc = tc;
           q.m0 = m0; q.n0 = n0; q.k0 = k0; q.klen = std::min(kchunk, K - k0); q.alpha = al;
+          q.tile_m = tm; q.tile_n = tn;
           L_.push_back(q);
         }
   };
@@ -750,10 +752,10 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? 0 : nn, B_WORK,
              P->work_for + lj_j, o, 0, -1.0);
   }
-  add_dense(G.dp1, 64, 256, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, off_Ucat, (int)nsum, 0, (int)nsum, B_WORK, P->work_y, v,
+  add_dense(G.dp1, DENSE_TILE_TC, 256, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, off_Ucat, (int)nsum, 0, (int)nsum, B_WORK, P->work_y, v,
             0, -1.0);
   // Phase 2 prologue: Z = FvR^T U_cat (v x sum n_p), read by the E3 products below
-  add_dense(G.dp2, 64, 1 << 30, B_WORK, P->work_z, (int)nsum, 0, v, (int)nsum, B_WORK, P->work_fvr, v, 1, v, B_POOL, off_Ucat,
+  add_dense(G.dp2, DENSE_TILE_TC, 1 << 30, B_WORK, P->work_z, (int)nsum, 0, v, (int)nsum, B_WORK, P->work_fvr, v, 1, v, B_POOL, off_Ucat,
             (int)nsum, 0, 1.0);
   // Phase 2
   for (int p = 0; p < npairs; ++p) {
@@ -887,7 +889,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
           if (q.b_buf == B_POOL) pool_blocks.insert({q.b_off, bsz});
           else vec_blocks.insert({q.b_off + ((int64_t)q.b_buf << 40), bsz});
           vec_blocks.insert({q.c_off + ((int64_t)q.c_buf << 40), (int64_t)q.M * q.N});
-          fl += 2.0 * std::min(64, q.M - q.m0) * std::min(64, q.N - q.n0) * q.klen;
+          fl += 2.0 * q.klen * std::min(q.tile_m, q.M - q.m0) * std::min(q.tile_n, q.N - q.n0);
         }
       double pe = 0, ve = 0;
       for (auto& b : pool_blocks) pe += b.second;

@@ -316,6 +316,24 @@ int pno_get_cis(const pnoeom_pno* pno, double* omega) {
   });
 }
 
+int pnoeom_gemm_tf32x3(pnoeom_ctx* ctx, const float* A, const float* B, float* C, int M, int N, int K, float alpha,
+                       void* cuda_stream) {
+  return guard([&] {
+    PN_CHECK(ctx, PNOEOM_ERR_INVALID_ARG, "NULL context");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::gemm_tf32x3(A, B, C, M, N, K, alpha, st(cuda_stream));
+  });
+}
+
+int pnoeom_device_status(pnoeom_ctx* ctx, int clear, int* status) {
+  return guard([&] {
+    PN_CHECK(ctx && status, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CUDA(cudaSetDevice(ctx->device));
+    PN_CUDA(cudaDeviceSynchronize());
+    *status = pnoeom::device_status(clear != 0);
+  });
+}
+
 int pnoeom_small_eig(int n, const double* A, double* wr, double* wi, double* VR) {
   return guard([&] {
     PN_CHECK(n >= 1 && A && wr && wi && VR, PNOEOM_ERR_INVALID_ARG, "bad arguments");

@@ -2,6 +2,7 @@
 #include <map>
 #include <mutex>
 #include "sigma_prog.cuh"
+#include "tc.cuh"
 
 namespace pnoeom {
 namespace {
@@ -338,9 +339,10 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
 }
 
 // Dense product tile: C[m0.., n0..] += alpha opA(A) opB(B) over K in [k0, k0 + klen).
-// BT x BT output tile, (BT/4)^2 threads with 4 x 4 register tiles, K staged in
-// chunks of 16 (A^T and B in shared memory, zero-filled outside the operands).
-template <typename T, int BT>
+// The tile is TM rows x BT columns, computed in passes of BT x BT with (BT/4)^2 threads
+// and 4 x 4 register tiles, K staged in chunks of 16 (A^T and B in shared memory,
+// zero-filled outside the operands).
+template <typename T, int BT, int TM>
 __global__ void __launch_bounds__((BT / 4) * (BT / 4)) k_dense(const DProb* __restrict__ probs,
                                                               const __grid_constant__ SysTable tab) {
   constexpr int NT = (BT / 4) * (BT / 4), KC = 16, LD = BT + 4;
@@ -351,55 +353,180 @@ __global__ void __launch_bounds__((BT / 4) * (BT / 4)) k_dense(const DProb* __re
   if (r >= tab.s[P.sys].nvec) return;
   const T* A = cbuf<T>(tab, P.sys, P.a_buf, r) + P.a_off;
   const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, r) + P.b_off;
-  const int Mt = min(BT, P.M - P.m0), Nt = min(BT, P.N - P.n0);
-  const int tx = threadIdx.x % (BT / 4), ty = threadIdx.x / (BT / 4);
-  T acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
-  for (int kk = 0; kk < P.klen; kk += KC) {
-    const int kn = min(KC, P.klen - kk), kb = P.k0 + kk;
-    __syncthreads();
-    for (int e = threadIdx.x; e < KC * BT; e += NT) {
-      int k, m;
-      if (P.ta) { k = e / BT; m = e % BT; } else { m = e / KC; k = e % KC; }
-      T v = T(0);
-      if (k < kn && m < Mt)
-        v = P.ta ? A[(int64_t)(kb + k) * P.lda + P.m0 + m] : A[(int64_t)(P.m0 + m) * P.lda + kb + k];
-      As[k * LD + m] = v;
-    }
-    for (int e = threadIdx.x; e < KC * BT; e += NT) {
-      int k, n;
-      if (P.tb) { n = e / KC; k = e % KC; } else { k = e / BT; n = e % BT; }
-      T v = T(0);
-      if (k < kn && n < Nt)
-        v = P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n];
-      Bs[k * LD + n] = v;
-    }
-    __syncthreads();
-    for (int k = 0; k < kn; ++k) {
-      T av[4], bv[4];
-      ld4(As + k * LD + ty * 4, av);
-      ld4(Bs + k * LD + tx * 4, bv);
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
-    }
-  }
   T* C = mbuf<T>(tab, P.sys, P.c_buf, r) + P.c_off;
   const T alpha = (T)P.alpha;
+  const int Nt = min(BT, P.N - P.n0);
+  const int tx = threadIdx.x % (BT / 4), ty = threadIdx.x / (BT / 4);
+  for (int mh = 0; mh < TM; mh += BT) {
+    const int m0 = P.m0 + mh;
+    const int Mt = min(BT, P.M - m0);
+    if (Mt <= 0) break;
+    T acc[4][4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int m = ty * 4 + a, n = tx * 4 + b;
-      if (m < Mt && n < Nt) {
-        const int64_t gm = P.m0 + m, gn = P.n0 + n;
-        atomicAdd(P.tc ? C + gn * P.ldc + gm : C + gm * P.ldc + gn, alpha * acc[a][b]);
+      for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int kk = 0; kk < P.klen; kk += KC) {
+      const int kn = min(KC, P.klen - kk), kb = P.k0 + kk;
+      __syncthreads();
+      for (int e = threadIdx.x; e < KC * BT; e += NT) {
+        int k, m;
+        if (P.ta) { k = e / BT; m = e % BT; } else { m = e / KC; k = e % KC; }
+        T v = T(0);
+        if (k < kn && m < Mt)
+          v = P.ta ? A[(int64_t)(kb + k) * P.lda + m0 + m] : A[(int64_t)(m0 + m) * P.lda + kb + k];
+        As[k * LD + m] = v;
+      }
+      for (int e = threadIdx.x; e < KC * BT; e += NT) {
+        int k, n;
+        if (P.tb) { n = e / KC; k = e % KC; } else { k = e / BT; n = e % BT; }
+        T v = T(0);
+        if (k < kn && n < Nt)
+          v = P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n];
+        Bs[k * LD + n] = v;
+      }
+      __syncthreads();
+      for (int k = 0; k < kn; ++k) {
+        T av[4], bv[4];
+        ld4(As + k * LD + ty * 4, av);
+        ld4(Bs + k * LD + tx * 4, bv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
       }
     }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int m = ty * 4 + a, n = tx * 4 + b;
+        if (m < Mt && n < Nt) {
+          const int64_t gm = m0 + m, gn = P.n0 + n;
+          atomicAdd(P.tc ? C + gn * P.ldc + gm : C + gm * P.ldc + gn, alpha * acc[a][b]);
+        }
+      }
+  }
+}
+
+// Device status word shared by the tensor-core kernels: bit 0 is set when an mbarrier
+// wait ran out of its clock budget (the kernel then skips the rest of its tile, frees its
+// TMEM and returns).  Read and cleared by pnoeom_device_status.
+__device__ int g_tc_status = 0;
+
+constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32;
+constexpr long long TC_WAIT_BUDGET = 2000000000LL;   // clock cycles (about one second)
+
+// Dense product tile on the tensor cores (FP32 data, 3xTF32): C[m0.., n0..] += alpha
+// opA(A) opB(B) over K in [k0, k0 + klen), a 128 x 64 tile per CTA of 128 threads.
+// Per K chunk of 32 the threads stage A (128 x 32) and B^T (64 x 32) as hi and lo tf32
+// parts in the K-major no-swizzle layout, with core matrices adjacent along M/N
+// (SBO = 128 B, LBO = rows / 8 * 128 B); one thread issues hi*hi + hi*lo + lo*hi for the
+// four K = 8 steps into the FP32 accumulator in TMEM (64 columns) and commits to an
+// mbarrier that every thread waits on before the chunk's buffers are reused.  The
+// epilogue reads TMEM (warp w: lanes 32w..32w+31 = tile rows) and adds alpha * D to C.
+__global__ void __launch_bounds__(128) k_dense_tc(const DProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* sAh = reinterpret_cast<float*>(smem_raw);
+  float* sAl = sAh + TC_BM * TC_BK;
+  float* sBh = sAl + TC_BM * TC_BK;
+  float* sBl = sBh + TC_BN * TC_BK;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBl + TC_BN * TC_BK);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const DProb P = probs[blockIdx.x];
+  const int r = blockIdx.y;
+  if (r >= tab.s[P.sys].nvec) return;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) tc::tmem_alloc(tslot, TC_BN);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  const float* A = cbuf<float>(tab, P.sys, P.a_buf, r) + P.a_off;
+  const float* Bm = cbuf<float>(tab, P.sys, P.b_buf, r) + P.b_off;
+  const int Mt = min(TC_BM, P.M - P.m0), Nt = min(TC_BN, P.N - P.n0);
+  constexpr uint32_t LBO_A = TC_BM / 8 * 128, LBO_B = TC_BN / 8 * 128, SBO = 128;
+  constexpr uint32_t IDESC = tc::idesc_tf32(TC_BM, TC_BN);
+  uint32_t parity = 0;
+  bool ok = true;
+  for (int kk = 0; kk < P.klen && ok; kk += TC_BK) {
+    const int kn = min(TC_BK, P.klen - kk), kb = P.k0 + kk;
+    // A chunk: thread -> (row m, 4 consecutive k), rows fastest
+    for (int c = tid; c < TC_BM * (TC_BK / 4); c += 128) {
+      const int m = c % TC_BM, k4 = c / TC_BM;
+      float h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k4 * 4 + j;
+        float x = 0.f;
+        if (m < Mt && k < kn)
+          x = P.ta ? A[(int64_t)(kb + k) * P.lda + P.m0 + m] : A[(int64_t)(P.m0 + m) * P.lda + kb + k];
+        tc::split_tf32(x, h[j], l[j]);
+      }
+      const uint32_t off = tc::kmajor_off(m, k4 * 4, LBO_A, SBO) / 4;
+      st4(sAh + off, h);
+      st4(sAl + off, l);
+    }
+    // B^T chunk: thread -> (column n, 4 consecutive k)
+    for (int c = tid; c < TC_BN * (TC_BK / 4); c += 128) {
+      const int n = c % TC_BN, k4 = c / TC_BN;
+      float h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k4 * 4 + j;
+        float x = 0.f;
+        if (n < Nt && k < kn)
+          x = P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n];
+        tc::split_tf32(x, h[j], l[j]);
+      }
+      const uint32_t off = tc::kmajor_off(n, k4 * 4, LBO_B, SBO) / 4;
+      st4(sBh + off, h);
+      st4(sBl + off, l);
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+#pragma unroll
+      for (int ks = 0; ks < TC_BK / 8; ++ks) {
+        const uint32_t da = ks * 2 * LBO_A, db = ks * 2 * LBO_B;
+        const uint32_t acc = (kk > 0 || ks > 0) ? 1u : 0u;
+        tc::mma_tf32(tmem, tc::sdesc(ah + da, LBO_A, SBO), tc::sdesc(bh + db, LBO_B, SBO), IDESC, acc);
+        tc::mma_tf32(tmem, tc::sdesc(ah + da, LBO_A, SBO), tc::sdesc(bl + db, LBO_B, SBO), IDESC, 1u);
+        tc::mma_tf32(tmem, tc::sdesc(al + da, LBO_A, SBO), tc::sdesc(bh + db, LBO_B, SBO), IDESC, 1u);
+      }
+      tc::mma_commit(mbar);
+    }
+    ok = tc::mbar_wait_bounded(mbar, parity, TC_WAIT_BUDGET);
+    parity ^= 1u;
+  }
+  if (!ok) atomicOr(&g_tc_status, 1);
+  tc::fence_after_sync();
+  if (ok) {
+    float* C = mbuf<float>(tab, P.sys, P.c_buf, r) + P.c_off;
+    const float alpha = (float)P.alpha;
+    const int m = warp * 32 + lane;
+#pragma unroll
+    for (int c16 = 0; c16 < TC_BN / 16; ++c16) {
+      float v[16];
+      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c16 * 16), v);
+      if (m < Mt) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int n = c16 * 16 + j;
+          if (n < Nt) {
+            const int64_t gm = P.m0 + m, gn = P.n0 + n;
+            atomicAdd(P.tc ? C + gn * P.ldc + gm : C + gm * P.ldc + gn, alpha * v[j]);
+          }
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, TC_BN);
 }
 
 constexpr int VR = 8;   // roots per pass inside a GEMV CTA
@@ -529,11 +656,28 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
 template <typename T>
 void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cudaStream_t s) {
   if (nprob <= 0 || t.max_nvec <= 0) return;
-  if (tile == 64)
-    k_dense<T, 64><<<dim3(nprob, t.max_nvec), 256, 0, s>>>(d_probs, t);
-  else
-    k_dense<T, 32><<<dim3(nprob, t.max_nvec), 64, 0, s>>>(d_probs, t);
+  if (tile == DENSE_TILE_TC) {   // 128 x 64 tiles: tensor cores in FP32, two 64 x 64 halves in FP64
+    if (sizeof(T) == 4) {
+      const size_t smem = (size_t)(2 * TC_BM * TC_BK + 2 * TC_BN * TC_BK) * sizeof(float) + 16;
+      ensure_dynamic_smem((const void*)k_dense_tc, smem);
+      k_dense_tc<<<dim3(nprob, t.max_nvec), 128, smem, s>>>(d_probs, t);
+    } else {
+      k_dense<T, 64, 128><<<dim3(nprob, t.max_nvec), 256, 0, s>>>(d_probs, t);
+    }
+  } else {
+    k_dense<T, 32, 32><<<dim3(nprob, t.max_nvec), 64, 0, s>>>(d_probs, t);
+  }
   PN_CUDA(cudaGetLastError());
+}
+
+int device_status(bool clear) {
+  int v = 0;
+  PN_CUDA(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)));
+  if (clear) {
+    const int z = 0;
+    PN_CUDA(cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)));
+  }
+  return v;
 }
 
 template void run_sandwich<double>(const SProb*, int, const SysTable&, int, cudaStream_t);
@@ -545,4 +689,36 @@ template void run_sandwich_small<float>(const SProb*, const int*, int, const Sys
 template void run_dense<double>(const DProb*, int, const SysTable&, int, cudaStream_t);
 template void run_dense<float>(const DProb*, int, const SysTable&, int, cudaStream_t);
 
+}  // namespace pnoeom
+
+namespace pnoeom {
+// C (M x N, row-major, ldc = N) += alpha A (M x K, row-major) B (K x N, row-major), FP32
+// device buffers, through the tensor-core dense tile kernel of the sigma program.
+void gemm_tf32x3(const float* A, const float* B, float* C, int M, int N, int K, float alpha, cudaStream_t s) {
+  PN_CHECK(M >= 0 && N >= 0 && K >= 0 && (M == 0 || N == 0 || K == 0 || (A && B && C)), PNOEOM_ERR_INVALID_ARG,
+           "bad GEMM arguments");
+  if (M == 0 || N == 0 || K == 0) return;
+  std::vector<DProb> h;
+  for (int m0 = 0; m0 < M; m0 += TC_BM)
+    for (int n0 = 0; n0 < N; n0 += TC_BN) {
+      DProb q{};
+      q.a_buf = B_POOL; q.b_buf = B_RIN; q.c_buf = B_SOUT;
+      q.M = M; q.N = N; q.K = K;
+      q.lda = K; q.ldb = N; q.ldc = N;
+      q.m0 = m0; q.n0 = n0; q.k0 = 0; q.klen = K;
+      q.tile_m = TC_BM; q.tile_n = TC_BN; q.alpha = alpha;
+      h.push_back(q);
+    }
+  DBuf<DProb> d(h.size());
+  d.upload(h.data(), h.size(), s);
+  SysTable t{};
+  t.nsys = 1;
+  t.max_nvec = 1;
+  t.s[0].pool = A;
+  t.s[0].rin = B;
+  t.s[0].sout = C;
+  t.s[0].nvec = 1;
+  run_dense<float>(d.get(), (int)h.size(), t, DENSE_TILE_TC, s);
+  PN_CUDA(cudaStreamSynchronize(s));
+}
 }  // namespace pnoeom

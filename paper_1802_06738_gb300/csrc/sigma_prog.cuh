@@ -34,6 +34,7 @@ struct DProb {
   int lda, ldb, ldc;
   int ta, tb, tc;
   int m0, n0, k0, klen;
+  int tile_m, tile_n;                 // tile extents of the list (accounting)
   double alpha;
 };
 
@@ -86,8 +87,14 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
                         int dk2, int dn, int roots_per_cta, cudaStream_t s);
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
-// tile = 64 (256 threads) or 32 (64 threads): the edge of the output tiles of the list.
+// Output tiles of a dense list: DENSE_TILE_TC = 128 rows x 64 columns (tensor cores in
+// FP32, SIMT in FP64), else tile x tile (SIMT).
+constexpr int DENSE_TILE_TC = 128;
 template <typename T>
 void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cudaStream_t s);
+// Reads (and with clear, resets) the tensor-core kernels' device status word: 0 when
+// every bounded wait completed.
+int device_status(bool clear);
+void gemm_tf32x3(const float* A, const float* B, float* C, int M, int N, int K, float alpha, cudaStream_t s);
 
 }  // namespace pnoeom

@@ -113,10 +113,10 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     n0 = small(prog.small1);
     run_sandwich<T>(prog.gen1.get(), prog.n_gen1, t, prog.smem_elems, s);
   });
-  timed(4, [&] { run_dense<T>(prog.d1.get(), prog.n_d1, t, 64, s); });
+  timed(4, [&] { run_dense<T>(prog.d1.get(), prog.n_d1, t, DENSE_TILE_TC, s); });
   timed(1, [&] { run_gemv<T>(prog.v1.get(), prog.n_v1, t, s); });
   timed(5, [&] {
-    run_dense<T>(prog.d2.get(), prog.n_d2, t, 64, s);
+    run_dense<T>(prog.d2.get(), prog.n_d2, t, DENSE_TILE_TC, s);
     run_dense<T>(prog.d3.get(), prog.n_d3, t, 32, s);
   });
   timed(2, [&] {
