@@ -128,7 +128,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Product 2: C[m][(vector, n)] += As^T Ts, 4 x 4 register tiles that each thread
 // keeps for the whole group (MAXT tiles per thread).
 template <typename T, int NT, int MAXT>
-__global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 4 : 2) : 1) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
                                                        const __grid_constant__ SysTable tab, int rpc, int dm, int dk1,
                                                        int dk2, int dn) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -150,11 +150,17 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
   const int nct = ((Mt + 3) >> 2) * nr * nt4;
   // padding is read (never stored) by the 4-wide tiles: keep it finite
   for (int e = tid; e < total; e += NT) S0[e] = T(0);
+  // Product 2 register tiles: when there are fewer C tiles than threads, s2 lanes (a
+  // power of two <= 8, adjacent lanes of one warp) share a tile, each summing every s2-th
+  // k; their partial tiles are reduced once, after the group.
+  int s2 = 1;
+  while (s2 < 8 && nct * s2 * 2 <= NT) s2 *= 2;
+  const int sl2 = tid & (s2 - 1);
   int cm4[MAXT], cr[MAXT], cn4[MAXT];
   T acc[MAXT][4][4];
 #pragma unroll
   for (int j = 0; j < MAXT; ++j) {
-    const int t = tid + j * NT;
+    const int t = (tid + j * NT) / s2;
     cn4[j] = t % nt4;
     cr[j] = (t / nt4) % nr;
     cm4[j] = t / (nt4 * nr);
@@ -163,7 +169,9 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[j][a][b] = T(0);
   }
-  // issue the copies of problem P into stage buffer `buf`
+  // Row-wise staging: each work item copies one contiguous source row with incrementing
+  // pointers.  A, B and (when xb == 0) X go through cp.async; X with xb != 0 is merged in
+  // registers by stage_xeff.
   auto issue = [&](const SProb& P, int buf) {
     T* As = S0 + buf * stage;
     T* Bs = As + asz;
@@ -174,49 +182,71 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
     const int xr0 = hasA ? 0 : P.m0, xc0 = hasB ? 0 : P.n0;
     if (hasA) {
       const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
-      if (P.ta) {   // stored K1 x M: element (m, k) at A[k lda + m]
-        const float rd = 1.0f / (float)Mt;
-        for (int e = tid; e < Mt * K1; e += NT) {
-          const int k = fdiv(e, rd), m = e - k * Mt;
-          cp_async_el(As + k * Mp + m, A + (int64_t)k * P.lda + P.m0 + m);
+      if (P.ta) {   // stored K1 x M: row k of the store -> row k of As
+        for (int k = tid; k < K1; k += NT) {
+          const T* src = A + (int64_t)k * P.lda + P.m0;
+          T* dst = As + k * Mp;
+          for (int m = 0; m < Mt; ++m) cp_async_el(dst + m, src + m);
         }
-      } else {
-        const float rd = 1.0f / (float)K1;
-        for (int e = tid; e < Mt * K1; e += NT) {
-          const int m = fdiv(e, rd), k = e - m * K1;
-          cp_async_el(As + k * Mp + m, A + (int64_t)(P.m0 + m) * P.lda + k);
+      } else {      // row m of A -> column m of As
+        for (int m = tid; m < Mt; m += NT) {
+          const T* src = A + (int64_t)(P.m0 + m) * P.lda;
+          T* dst = As + m;
+          for (int k = 0; k < K1; ++k) cp_async_el(dst + k * Mp, src + k);
         }
       }
     }
     if (hasB) {
       const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, 0) + P.b_off;
       const int K2 = P.K2;
-      if (P.tb) {   // stored N x K2
-        const float rd = 1.0f / (float)K2;
-        for (int e = tid; e < K2 * Nt; e += NT) {
-          const int n = fdiv(e, rd), k = e - n * K2;
-          cp_async_el(Bs + k * Np + n, Bm + (int64_t)(P.n0 + n) * P.ldb + k);
+      if (P.tb) {   // stored N x K2: row n -> column n of Bs
+        for (int n = tid; n < Nt; n += NT) {
+          const T* src = Bm + (int64_t)(P.n0 + n) * P.ldb;
+          T* dst = Bs + n;
+          for (int k = 0; k < K2; ++k) cp_async_el(dst + k * Np, src + k);
         }
-      } else {
-        const float rd = 1.0f / (float)Nt;
-        for (int e = tid; e < K2 * Nt; e += NT) {
-          const int k = fdiv(e, rd), n = e - k * Nt;
-          cp_async_el(Bs + k * Np + n, Bm + (int64_t)k * P.ldb + P.n0 + n);
+      } else {      // row k -> row k of Bs
+        for (int k = tid; k < K2; k += NT) {
+          const T* src = Bm + (int64_t)k * P.ldb + P.n0;
+          T* dst = Bs + k * Np;
+          for (int n = 0; n < Nt; ++n) cp_async_el(dst + n, src + n);
         }
       }
     }
-    {   // opX(X)[xr0 + a][xc0 + b] -> Xs[b][r K1p + a]
-      const int per = kr * kc;
-      const float rd_per = 1.0f / (float)per, rd_kr = 1.0f / (float)kr;
-      for (int e = tid; e < nr * per; e += NT) {
-        const int r = fdiv(e, rd_per), rem = e - r * per;
-        const int b = fdiv(rem, rd_kr), a = rem - b * kr;
-        const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
-        const int xa = xr0 + a, xbb = xc0 + b;
-        cp_async_el(Xs + b * xld + r * K1p + a, P.tx ? X + (int64_t)xbb * P.ldx + xa : X + (int64_t)xa * P.ldx + xbb);
+    if (P.xb == 0.0) {   // opX(X)[xr0 + a][xc0 + b] -> Xs[b][r K1p + a]
+      if (P.tx) {   // opX(X)[a][b] = X[b][a]: row xc0 + b of X -> row b of Xs
+        for (int it = tid; it < nr * kc; it += NT) {
+          const int r = it / kc, b = it - r * kc;
+          const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)(xc0 + b) * P.ldx + xr0;
+          T* dst = Xs + b * xld + r * K1p;
+          for (int a = 0; a < kr; ++a) cp_async_el(dst + a, src + a);
+        }
+      } else {      // opX(X)[a][b] = X[a][b]: row xr0 + a of X -> column a of Xs
+        for (int it = tid; it < nr * kr; it += NT) {
+          const int r = it / kr, a = it - r * kr;
+          const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)(xr0 + a) * P.ldx + xc0;
+          T* dst = Xs + r * K1p + a;
+          for (int b = 0; b < kc; ++b) cp_async_el(dst + b * xld, src + b);
+        }
       }
     }
     cp_async_commit();
+  };
+  // X_eff = opX(X) + xb opX(X)^T of a square block (xr0 = xc0 = 0, kr = kc), merged in
+  // registers: item (vector, b) writes row b of Xs from row b and column b of X.
+  auto stage_xeff = [&](const SProb& P, T* Xs, int K) {
+    const T xb = (T)P.xb;
+    for (int it = tid; it < nr * K; it += NT) {
+      const int r = it / K, b = it - r * K;
+      const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
+      const T* row = X + (int64_t)b * P.ldx;   // X[b][a], a = 0..K-1
+      const T* col = X + b;                    // X[a][b] at col + a * ldx
+      T* dst = Xs + b * xld + r * K1p;
+      if (P.tx)   // opX(X)[a][b] = X[b][a]
+        for (int a = 0; a < K; ++a) dst[a] = row[a] + xb * col[(int64_t)a * P.ldx];
+      else        // opX(X)[a][b] = X[a][b]
+        for (int a = 0; a < K; ++a) dst[a] = col[(int64_t)a * P.ldx] + xb * row[a];
+    }
   };
   __syncthreads();   // zero fill done before the first copies land
   issue(P0, 0);
@@ -233,31 +263,24 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
     const int K1 = P.K1;
     const int kr = hasA ? K1 : Mt, kc = hasB ? P.K2 : Nt;
     const T alpha = (T)P.alpha, xb = (T)P.xb;
-    if (xb != T(0)) {   // X_eff = opX(X) + xb opX(X)^T, in place on pairs (a <= b) of the square block
-      const int per = kr * kr;
-      const float rd_per = 1.0f / (float)per, rd_kr = 1.0f / (float)kr;
-      for (int e = tid; e < nr * per; e += NT) {
-        const int r = fdiv(e, rd_per), rem = e - r * per;
-        const int b = fdiv(rem, rd_kr), a = rem - b * kr;
-        if (a > b) continue;
-        T* xab = Xs + b * xld + r * K1p + a;   // opX(X)[a][b]
-        T* xba = Xs + a * xld + r * K1p + b;   // opX(X)[b][a]
-        const T u = *xab, w = *xba;
-        if (a == b) {
-          *xab = u + xb * u;
-        } else {
-          *xab = u + xb * w;
-          *xba = w + xb * u;
-        }
-      }
+    if (xb != T(0)) {   // X_eff staged now, from registers
+      stage_xeff(P, Xs, kr);
       __syncthreads();
     }
-    {   // product 1
+    {   // product 1: tiles (vector, a4, n4); s1 lanes share a tile over k when tiles are few
       const int ka4 = (kr + 3) >> 2;
       const int n1 = nr * ka4 * nt4;
-      for (int t = tid; t < n1; t += NT) {
-        const int n4 = t % nt4, rest = t / nt4;
-        const int a4 = rest % ka4, r = rest / ka4;
+      int s1 = 1;
+      if (hasB)
+        while (s1 < 8 && n1 * s1 * 2 <= NT) s1 *= 2;
+      const int total1 = n1 * s1;
+      const float rd_nt4 = 1.0f / (float)nt4, rd_ka4 = 1.0f / (float)ka4;
+      for (int base = 0; base < total1; base += NT) {
+        const int tt = base + tid;
+        const bool valid = tt < total1;
+        const int t = valid ? tt / s1 : 0, sl = tt & (s1 - 1);
+        const int rest = fdiv(t, rd_nt4), n4 = t - rest * nt4;
+        const int r = fdiv(rest, rd_ka4), a4 = rest - r * ka4;
         T c[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -266,16 +289,22 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
         const T* xp = Xs + r * K1p + a4 * 4;
         if (hasB) {
           const T* bp = Bs + n4 * 4;
-          for (int b = 0; b < kc; ++b) {
-            T xv[4], bv[4];
-            ld4(xp + b * xld, xv);
-            ld4(bp + b * Np, bv);
+          if (valid)
+            for (int b = sl; b < kc; b += s1) {
+              T xv[4], bv[4];
+              ld4(xp + b * xld, xv);
+              ld4(bp + b * Np, bv);
+#pragma unroll
+              for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) c[a][q] += xv[a] * bv[q];
+            }
+          for (int off = 1; off < s1; off <<= 1)   // every lane of the warp takes part
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-              for (int q = 0; q < 4; ++q) c[a][q] += xv[a] * bv[q];
-          }
-        } else {   // T = X_eff on the tile's columns
+              for (int q = 0; q < 4; ++q) c[a][q] += __shfl_xor_sync(0xffffffffu, c[a][q], off);
+        } else if (valid) {   // T = X_eff on the tile's columns
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             if (n4 * 4 + q < kc) {
@@ -285,22 +314,24 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
               for (int a = 0; a < 4; ++a) c[a][q] = xv[a];
             }
         }
-        T* tp = Ts + (a4 * 4) * tld + r * Np + n4 * 4;
+        if (valid && sl == 0) {
+          T* tp = Ts + (a4 * 4) * tld + r * Np + n4 * 4;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          T o[4] = {alpha * c[a][0], alpha * c[a][1], alpha * c[a][2], alpha * c[a][3]};
-          st4(tp + a * tld, o);
+          for (int a = 0; a < 4; ++a) {
+            T o[4] = {alpha * c[a][0], alpha * c[a][1], alpha * c[a][2], alpha * c[a][3]};
+            st4(tp + a * tld, o);
+          }
         }
       }
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < MAXT; ++j) {   // product 2, into the register tiles
-      if (tid + j * NT >= nct) continue;
+      if (tid + j * NT >= nct * s2) continue;
       const T* tp = Ts + cr[j] * Np + cn4[j] * 4;
       if (hasA) {
         const T* ap = As + cm4[j] * 4;
-        for (int k = 0; k < K1; ++k) {
+        for (int k = sl2; k < K1; k += s2) {
           T av[4], tv[4];
           ld4(ap + k * Mp, av);
           ld4(tp + k * tld, tv);
@@ -309,7 +340,7 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[j][a][q] += av[a] * tv[q];
         }
-      } else {
+      } else if (sl2 == 0) {
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
           T tv[4];
@@ -320,10 +351,16 @@ __global__ void __launch_bounds__(NT) k_sandwich_small(const SProb* __restrict__
       }
     }
   }
+  if (s2 > 1)   // one tile per thread here (nct * s2 <= NT): reduce the s2 partial tiles
+    for (int off = 1; off < s2; off <<= 1)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[0][a][q] += __shfl_xor_sync(0xffffffffu, acc[0][a][q], off);
   // one atomic add per element of the group's C tile (other groups may share it)
 #pragma unroll
   for (int j = 0; j < MAXT; ++j) {
-    if (tid + j * NT >= nct) continue;
+    if (tid + j * NT >= nct * s2 || sl2 != 0) continue;
     T* C = mbuf<T>(tab, P0.sys, P0.c_buf, rbase + cr[j]) + P0.c_off;
 #pragma unroll
     for (int a = 0; a < 4; ++a)
