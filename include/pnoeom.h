@@ -181,10 +181,12 @@ int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, co
 int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* opts, void* cuda_stream,
                        double* energies, double* res_norms, int* iters, int* converged);
 
-/* Serving (continuous batching of excited-state solves).  A server owns two
- * threads: a builder that admits queued requests in arrival order when their
- * estimated setup footprint fits the HBM budget (0 = no budget) and runs
- * pno_build on its own stream, and a solver that keeps every built request's
+/* Serving (continuous batching of excited-state solves).  A server owns
+ * builder threads (3 by default; the environment variable
+ * PNOEOM_SERVER_BUILDERS, read at creation, sets 1..16) that admit queued
+ * requests in arrival order when their estimated setup footprint fits the
+ * HBM budget (0 = no budget) and run pno_build concurrently, each on its own
+ * stream and cuSOLVER handle, and a solver thread that keeps every built request's
  * PNOs, operator blocks and Davidson subspace resident and runs lockstep
  * Davidson rounds over all of them through one merged sigma program (a CUDA
  * graph).  Requests that finish building join at the next round boundary;
@@ -195,7 +197,7 @@ typedef struct pnoeom_server pnoeom_server;
 enum { PNOEOM_REQ_QUEUED = 0, PNOEOM_REQ_BUILDING = 1, PNOEOM_REQ_RUNNING = 2, PNOEOM_REQ_DONE = 3,
        PNOEOM_REQ_FAILED = 4 };
 int pnoeom_server_create(pnoeom_ctx* ctx, size_t hbm_budget_bytes, int max_active, pnoeom_server** out);
-/* Stops both threads (queued requests are not run) and frees all state. */
+/* Stops the server's threads (queued requests are not run) and frees all state. */
 void pnoeom_server_destroy(pnoeom_server* srv);
 /* Queue one solve.  Inputs must be host memory; they are copied.  A request
  * whose estimated footprint exceeds the budget fails at once with

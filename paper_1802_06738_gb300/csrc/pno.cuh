@@ -125,7 +125,8 @@ struct pnoeom_server {
   int64_t next_id = 1;
   bool stop = false;
   int64_t rounds = 0, merges = 0, total_sigma_evals = 0;
-  std::thread builder, solver;
+  std::vector<std::thread> builders;   // concurrent pno_build workers, one stream and solver handle each
+  std::thread solver;
   std::string fatal;
 };
 

@@ -1022,7 +1022,9 @@ static void server_solver(pnoeom_server* S) {
 
 void server_start(pnoeom_server* S) {
   S->t0 = wall_s();
-  S->builder = std::thread(server_builder, S);
+  int nb = 3;   // builder threads; PNOEOM_SERVER_BUILDERS overrides (1..16)
+  if (const char* e = std::getenv("PNOEOM_SERVER_BUILDERS")) nb = std::max(1, std::min(16, std::atoi(e)));
+  for (int k = 0; k < nb; ++k) S->builders.emplace_back(server_builder, S);
   S->solver = std::thread(server_solver, S);
 }
 
@@ -1032,7 +1034,8 @@ void server_stop(pnoeom_server* S) {
     S->stop = true;
   }
   S->cv.notify_all();
-  if (S->builder.joinable()) S->builder.join();
+  for (auto& b : S->builders)
+    if (b.joinable()) b.join();
   if (S->solver.joinable()) S->solver.join();
 }
 
