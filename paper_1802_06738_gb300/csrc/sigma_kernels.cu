@@ -117,17 +117,19 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Grouped small sandwich (see run_sandwich_small).  Shared memory, with the set's
 // bounds dm, dk1 (rows of the staged X block), dk2 (its columns), dn padded to 4,
-// and two copies (problem g and g + 1) of the staged operands:
+// and NB copies (NB = 2: problem g and g + 1; NB = 1: one) of the staged operands:
 //   As [dk1][Mp]        A^T (tile rows)
 //   Bs [dk2][Np]        B (tile columns)
 //   Xs [dk2][R * K1p]   opX(X)^T of the R vectors side by side (X_eff after the merge pass)
 // and one copy of
 //   Ts [K1p][R * Np]    alpha X_eff B of the R vectors side by side.
-// The operands of problem g + 1 are copied with cp.async while problem g computes.
+// With NB = 2 the operands of problem g + 1 are copied with cp.async while problem g
+// computes; NB = 1 copies them at the start of each problem and needs half the staging
+// memory (more CTAs per SM where the stacked X blocks are large).
 // Product 1: Ts = alpha Xs^T Bs, rows (vector, a) x columns n, 4 x 4 register tiles.
 // Product 2: C[m][(vector, n)] += As^T Ts, 4 x 4 register tiles that each thread
 // keeps for the whole group (MAXT tiles per thread).
-template <typename T, int NT, int MAXT>
+template <typename T, int NT, int MAXT, int NB>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 4 : 2) : 1) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
                                                        const __grid_constant__ SysTable tab, int rpc, int dm, int dk1,
                                                        int dk2, int dn) {
@@ -137,8 +139,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 4 : 2) : 1) 
   const int asz = dk1 * Mp, bsz = dk2 * Np, xsz = dk2 * xld;
   const int stage = asz + bsz + xsz;   // one copy of the staged operands (a multiple of 4)
   T* S0 = reinterpret_cast<T*>(smem_raw);
-  T* Ts = S0 + 2 * stage;
-  const int total = 2 * stage + K1p * tld;
+  T* Ts = S0 + NB * stage;
+  const int total = NB * stage + K1p * tld;
   const int tid = threadIdx.x;
   const int g0 = gstart[blockIdx.x], g1 = gstart[blockIdx.x + 1];
   const SProb P0 = probs[g0];
@@ -248,13 +250,23 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 4 : 2) : 1) 
         for (int a = 0; a < K; ++a) dst[a] = col[(int64_t)a * P.ldx] + xb * row[a];
     }
   };
-  __syncthreads();   // zero fill done before the first copies land
-  issue(P0, 0);
+  if (NB == 2) {
+    __syncthreads();   // zero fill done before the first copies land
+    issue(P0, 0);
+  }
   for (int g = g0; g < g1; ++g) {
-    const int buf = (g - g0) & 1;
-    cp_async_wait_all();
-    __syncthreads();   // problem g staged; every thread is done with problem g - 1
-    if (g + 1 < g1) issue(probs[g + 1], buf ^ 1);
+    int buf = 0;
+    if (NB == 2) {   // problem g was copied while g - 1 computed; start copying g + 1
+      buf = (g - g0) & 1;
+      cp_async_wait_all();
+      __syncthreads();   // problem g staged; every thread is done with problem g - 1
+      if (g + 1 < g1) issue(probs[g + 1], buf ^ 1);
+    } else {         // one stage buffer: copy problem g now
+      __syncthreads();   // every thread is done with problem g - 1 (and the zero fill)
+      issue(probs[g], 0);
+      cp_async_wait_all();
+      __syncthreads();
+    }
     const SProb P = probs[g];
     T* As = S0 + buf * stage;
     T* Bs = As + asz;
@@ -444,6 +456,84 @@ __global__ void __launch_bounds__((BT / 4) * (BT / 4)) k_dense(const DProb* __re
         }
       }
   }
+}
+
+// Dense product with a small output tile (at most 32 x 32) and a long K: one tile per
+// CTA of 256 threads.  The 4 x 4 register tiles are fewer than the threads, so s lanes
+// (a power of two, adjacent lanes of one warp) share a tile, each taking every s-th k of
+// a shared-memory chunk; their partial tiles are reduced with shuffles at the end.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dense_skinny(const DProb* __restrict__ probs,
+                                                     const __grid_constant__ SysTable tab) {
+  constexpr int NT = 256, KC = 64, LD = 36;
+  __shared__ __align__(16) T As[KC * LD];   // A^T chunk: [k][m]
+  __shared__ __align__(16) T Bs[KC * LD];   // B chunk:   [k][n]
+  const DProb P = probs[blockIdx.x];
+  const int r = blockIdx.y;
+  if (r >= tab.s[P.sys].nvec) return;
+  const T* A = cbuf<T>(tab, P.sys, P.a_buf, r) + P.a_off;
+  const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, r) + P.b_off;
+  const int Mt = min(32, P.M - P.m0), Nt = min(32, P.N - P.n0);
+  const int mt4 = (Mt + 3) >> 2, nt4 = (Nt + 3) >> 2, tiles = mt4 * nt4;
+  int sp = 1;
+  while (sp < 32 && tiles * sp * 2 <= NT) sp *= 2;
+  const int tid = threadIdx.x, t = tid / sp, sl = tid & (sp - 1);
+  const bool valid = t < tiles;
+  const int m4 = valid ? t / nt4 : 0, n4 = valid ? t - m4 * nt4 : 0;
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  for (int kk = 0; kk < P.klen; kk += KC) {
+    const int kn = min(KC, P.klen - kk), kb = P.k0 + kk;
+    __syncthreads();
+    for (int e = tid; e < KC * 32; e += NT) {
+      int k, m;
+      if (P.ta) { k = e >> 5; m = e & 31; } else { m = e / KC; k = e % KC; }
+      T v = T(0);
+      if (k < kn && m < Mt)
+        v = P.ta ? A[(int64_t)(kb + k) * P.lda + P.m0 + m] : A[(int64_t)(P.m0 + m) * P.lda + kb + k];
+      As[k * LD + m] = v;
+    }
+    for (int e = tid; e < KC * 32; e += NT) {
+      int k, n;
+      if (P.tb) { n = e / KC; k = e % KC; } else { k = e >> 5; n = e & 31; }
+      T v = T(0);
+      if (k < kn && n < Nt)
+        v = P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n];
+      Bs[k * LD + n] = v;
+    }
+    __syncthreads();
+    if (valid)
+      for (int k = sl; k < kn; k += sp) {
+        T av[4], bv[4];
+        ld4(As + k * LD + m4 * 4, av);
+        ld4(Bs + k * LD + n4 * 4, bv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] += av[a] * bv[b];
+      }
+  }
+  for (int off = 1; off < sp; off <<= 1)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += __shfl_xor_sync(0xffffffffu, acc[a][b], off);
+  if (!valid || sl != 0) return;
+  T* C = mbuf<T>(tab, P.sys, P.c_buf, r) + P.c_off;
+  const T alpha = (T)P.alpha;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int m = m4 * 4 + a, n = n4 * 4 + b;
+      if (m < Mt && n < Nt) {
+        const int64_t gm = P.m0 + m, gn = P.n0 + n;
+        atomicAdd(P.tc ? C + gn * P.ldc + gm : C + gm * P.ldc + gn, alpha * acc[a][b]);
+      }
+    }
 }
 
 // Device status word shared by the tensor-core kernels: bit 0 is set when an mbarrier
@@ -657,6 +747,16 @@ void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s
   PN_CUDA(cudaGetLastError());
 }
 
+template <typename T, int NT, int MAXT, int NB>
+static void launch_small_nb(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm,
+                            int dk1, int dk2, int dn, int rpc, size_t smem, cudaStream_t s) {
+  ensure_dynamic_smem((const void*)k_sandwich_small<T, NT, MAXT, NB>, smem);
+  const int ychunks = (t.max_nvec + rpc - 1) / rpc;
+  k_sandwich_small<T, NT, MAXT, NB>
+      <<<dim3(ngroups, ychunks), NT, smem, s>>>(d_probs, d_group_start, t, rpc, dm, dk1, dk2, dn);
+  PN_CUDA(cudaGetLastError());
+}
+
 template <typename T, int NT, int MAXT>
 static void launch_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
                          int dk2, int dn, int rpc, cudaStream_t s) {
@@ -664,16 +764,19 @@ static void launch_small(const SProb* d_probs, const int* d_group_start, int ngr
   // C register tiles per vector: rows/4 x cols/4; at most NT * MAXT per CTA
   const int tiles = (Mp / 4) * (Np / 4);
   rpc = std::max(1, std::min(rpc, std::min(t.max_nvec, NT * MAXT / tiles)));
-  auto smem_of = [&](int r) { return (size_t)(2 * (dk1 * Mp + dk2 * Np + dk2 * r * K1p) + K1p * r * Np) * sizeof(T); };
-  const size_t limit = 200 * 1024;
-  while (rpc > 1 && smem_of(rpc) > limit) --rpc;
-  PN_CHECK(smem_of(rpc) <= limit && tiles <= NT * MAXT, PNOEOM_ERR_UNSUPPORTED,
+  auto smem_of = [&](int r, int nb) {
+    return (size_t)(nb * (dk1 * Mp + dk2 * Np + dk2 * r * K1p) + K1p * r * Np) * sizeof(T);
+  };
+  const size_t limit = 200 * 1024, two_per_sm = 113 * 1024;
+  // double buffering unless only single buffering leaves room for two CTAs per SM
+  const int nb = (smem_of(rpc, 2) > two_per_sm && smem_of(rpc, 1) <= two_per_sm) ? 1 : 2;
+  while (rpc > 1 && smem_of(rpc, nb) > limit) --rpc;
+  PN_CHECK(smem_of(rpc, nb) <= limit && tiles <= NT * MAXT, PNOEOM_ERR_UNSUPPORTED,
            "PNO blocks too large for the grouped sandwich kernel");
-  const size_t smem = smem_of(rpc);
-  ensure_dynamic_smem((const void*)k_sandwich_small<T, NT, MAXT>, smem);
-  const int ychunks = (t.max_nvec + rpc - 1) / rpc;
-  k_sandwich_small<T, NT, MAXT><<<dim3(ngroups, ychunks), NT, smem, s>>>(d_probs, d_group_start, t, rpc, dm, dk1, dk2, dn);
-  PN_CUDA(cudaGetLastError());
+  if (nb == 2)
+    launch_small_nb<T, NT, MAXT, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, rpc, smem_of(rpc, 2), s);
+  else
+    launch_small_nb<T, NT, MAXT, 1>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, rpc, smem_of(rpc, 1), s);
 }
 
 template <typename T>
@@ -701,8 +804,8 @@ void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cud
     } else {
       k_dense<T, 64, 128><<<dim3(nprob, t.max_nvec), 256, 0, s>>>(d_probs, t);
     }
-  } else {
-    k_dense<T, 32, 32><<<dim3(nprob, t.max_nvec), 64, 0, s>>>(d_probs, t);
+  } else {   // tiles of at most 32 x 32: one per CTA, K split over the spare lanes
+    k_dense_skinny<T><<<dim3(nprob, t.max_nvec), 256, 0, s>>>(d_probs, t);
   }
   PN_CUDA(cudaGetLastError());
 }

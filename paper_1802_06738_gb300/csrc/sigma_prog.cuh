@@ -88,7 +88,7 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
 // Output tiles of a dense list: DENSE_TILE_TC = 128 rows x 64 columns (tensor cores in
-// FP32, SIMT in FP64), else tile x tile (SIMT).
+// FP32, SIMT in FP64); 32: tiles of at most 32 x 32, one per CTA with K split over lanes.
 constexpr int DENSE_TILE_TC = 128;
 template <typename T>
 void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cudaStream_t s);
