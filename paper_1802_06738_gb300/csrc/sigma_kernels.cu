@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(256) k_dense_skinny(const DProb* __restrict__ 
 __device__ int g_tc_status = 0;
 
 constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32;
+constexpr int TC_STAGE = 2 * TC_BM * TC_BK + 2 * TC_BN * TC_BK;   // floats per pipeline stage
 constexpr long long TC_WAIT_BUDGET = 2000000000LL;   // clock cycles (about one second)
 
 // Dense product tile on the tensor cores (FP32 data, 3xTF32): C[m0.., n0..] += alpha
@@ -549,23 +550,28 @@ constexpr long long TC_WAIT_BUDGET = 2000000000LL;   // clock cycles (about one 
 // Per K chunk of 32 the threads stage A (128 x 32) and B^T (64 x 32) as hi and lo tf32
 // parts in the K-major no-swizzle layout, with core matrices adjacent along M/N
 // (SBO = 128 B, LBO = rows / 8 * 128 B); one thread issues hi*hi + hi*lo + lo*hi for the
-// four K = 8 steps into the FP32 accumulator in TMEM (64 columns) and commits to an
-// mbarrier that every thread waits on before the chunk's buffers are reused.  The
-// epilogue reads TMEM (warp w: lanes 32w..32w+31 = tile rows) and adds alpha * D to C.
+// four K = 8 steps into the FP32 accumulator in TMEM (64 columns) and commits to the
+// stage's mbarrier.  Two stages: the next chunk's global loads go to registers while the
+// MMAs run.  The epilogue reads TMEM (warp w: lanes 32w..32w+31 = tile rows) and adds
+// alpha * D to C.
 __global__ void __launch_bounds__(128) k_dense_tc(const DProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // per stage: A hi, A lo (128 x 32 each), B hi, B lo (64 x 32 each); stage b at b * TC_STAGE
   float* sAh = reinterpret_cast<float*>(smem_raw);
   float* sAl = sAh + TC_BM * TC_BK;
   float* sBh = sAl + TC_BM * TC_BK;
   float* sBl = sBh + TC_BN * TC_BK;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(sBl + TC_BN * TC_BK);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(reinterpret_cast<float*>(smem_raw) + 2 * TC_STAGE);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
   const DProb P = probs[blockIdx.x];
   const int r = blockIdx.y;
   if (r >= tab.s[P.sys].nvec) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tc::tmem_alloc(tslot, TC_BN);
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    tc::mbar_init(mbar + 1, 1);
+  }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -575,59 +581,93 @@ __global__ void __launch_bounds__(128) k_dense_tc(const DProb* __restrict__ prob
   const int Mt = min(TC_BM, P.M - P.m0), Nt = min(TC_BN, P.N - P.n0);
   constexpr uint32_t LBO_A = TC_BM / 8 * 128, LBO_B = TC_BN / 8 * 128, SBO = 128;
   constexpr uint32_t IDESC = tc::idesc_tf32(TC_BM, TC_BN);
-  uint32_t parity = 0;
-  bool ok = true;
-  for (int kk = 0; kk < P.klen && ok; kk += TC_BK) {
-    const int kn = min(TC_BK, P.klen - kk), kb = P.k0 + kk;
-    // A chunk: thread -> (row m, 4 consecutive k), rows fastest
-    for (int c = tid; c < TC_BM * (TC_BK / 4); c += 128) {
-      const int m = c % TC_BM, k4 = c / TC_BM;
-      float h[4], l[4];
+  // Software pipeline over K chunks of 32: the global loads of chunk c + 1 are issued into
+  // registers while the MMAs of chunk c run; two shared-memory stages, one mbarrier each
+  // (the stage of chunk c is reused by chunk c + 2 once its MMAs have completed).
+  const int nchunk = (P.klen + TC_BK - 1) / TC_BK;
+  float ra[TC_BM * TC_BK / 4 / 128][4], rb[TC_BN * TC_BK / 4 / 128][4];
+  auto load = [&](int c) {
+    const int kb = P.k0 + c * TC_BK, kn = min(TC_BK, P.klen - c * TC_BK);
+#pragma unroll
+    for (int q = 0; q < TC_BM * TC_BK / 4 / 128; ++q) {
+      const int e = tid + q * 128, m = e % TC_BM, k4 = e / TC_BM;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int k = k4 * 4 + j;
-        float x = 0.f;
-        if (m < Mt && k < kn)
-          x = P.ta ? A[(int64_t)(kb + k) * P.lda + P.m0 + m] : A[(int64_t)(P.m0 + m) * P.lda + kb + k];
-        tc::split_tf32(x, h[j], l[j]);
+        ra[q][j] = (m < Mt && k < kn)
+                       ? (P.ta ? A[(int64_t)(kb + k) * P.lda + P.m0 + m] : A[(int64_t)(P.m0 + m) * P.lda + kb + k])
+                       : 0.f;
       }
-      const uint32_t off = tc::kmajor_off(m, k4 * 4, LBO_A, SBO) / 4;
-      st4(sAh + off, h);
-      st4(sAl + off, l);
     }
-    // B^T chunk: thread -> (column n, 4 consecutive k)
-    for (int c = tid; c < TC_BN * (TC_BK / 4); c += 128) {
-      const int n = c % TC_BN, k4 = c / TC_BN;
-      float h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < TC_BN * TC_BK / 4 / 128; ++q) {
+      const int e = tid + q * 128, n = e % TC_BN, k4 = e / TC_BN;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int k = k4 * 4 + j;
-        float x = 0.f;
-        if (n < Nt && k < kn)
-          x = P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n];
-        tc::split_tf32(x, h[j], l[j]);
+        rb[q][j] = (n < Nt && k < kn)
+                       ? (P.tb ? Bm[(int64_t)(P.n0 + n) * P.ldb + kb + k] : Bm[(int64_t)(kb + k) * P.ldb + P.n0 + n])
+                       : 0.f;
       }
+    }
+  };
+  uint32_t parity[2] = {0u, 0u};
+  bool ok = true;
+  if (nchunk > 0) load(0);
+  for (int c = 0; c < nchunk && ok; ++c) {
+    const int b = c & 1;
+    if (c >= 2) {   // the MMAs of chunk c - 2 read stage b
+      ok = tc::mbar_wait_bounded(mbar + b, parity[b], TC_WAIT_BUDGET);
+      parity[b] ^= 1u;
+      if (!ok) break;
+    }
+    float* Ah = sAh + b * TC_STAGE;
+    float* Al = sAl + b * TC_STAGE;
+    float* Bh = sBh + b * TC_STAGE;
+    float* Bl = sBl + b * TC_STAGE;
+#pragma unroll
+    for (int q = 0; q < TC_BM * TC_BK / 4 / 128; ++q) {
+      const int e = tid + q * 128, m = e % TC_BM, k4 = e / TC_BM;
+      float h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tc::split_tf32(ra[q][j], h[j], l[j]);
+      const uint32_t off = tc::kmajor_off(m, k4 * 4, LBO_A, SBO) / 4;
+      st4(Ah + off, h);
+      st4(Al + off, l);
+    }
+#pragma unroll
+    for (int q = 0; q < TC_BN * TC_BK / 4 / 128; ++q) {
+      const int e = tid + q * 128, n = e % TC_BN, k4 = e / TC_BN;
+      float h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) tc::split_tf32(rb[q][j], h[j], l[j]);
       const uint32_t off = tc::kmajor_off(n, k4 * 4, LBO_B, SBO) / 4;
-      st4(sBh + off, h);
-      st4(sBl + off, l);
+      st4(Bh + off, h);
+      st4(Bl + off, l);
     }
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc::fence_after_sync();
-      const uint32_t ah = tc::smem_u32(sAh), al = tc::smem_u32(sAl), bh = tc::smem_u32(sBh), bl = tc::smem_u32(sBl);
+      const uint32_t ah = tc::smem_u32(Ah), al = tc::smem_u32(Al), bh = tc::smem_u32(Bh), bl = tc::smem_u32(Bl);
 #pragma unroll
       for (int ks = 0; ks < TC_BK / 8; ++ks) {
         const uint32_t da = ks * 2 * LBO_A, db = ks * 2 * LBO_B;
-        const uint32_t acc = (kk > 0 || ks > 0) ? 1u : 0u;
+        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
         tc::mma_tf32(tmem, tc::sdesc(ah + da, LBO_A, SBO), tc::sdesc(bh + db, LBO_B, SBO), IDESC, acc);
         tc::mma_tf32(tmem, tc::sdesc(ah + da, LBO_A, SBO), tc::sdesc(bl + db, LBO_B, SBO), IDESC, 1u);
         tc::mma_tf32(tmem, tc::sdesc(al + da, LBO_A, SBO), tc::sdesc(bh + db, LBO_B, SBO), IDESC, 1u);
       }
-      tc::mma_commit(mbar);
+      tc::mma_commit(mbar + b);
     }
-    ok = tc::mbar_wait_bounded(mbar, parity, TC_WAIT_BUDGET);
-    parity ^= 1u;
+    if (c + 1 < nchunk) load(c + 1);
+  }
+  // the last one or two chunks' MMAs (MMAs complete in issue order: waiting for the last
+  // commit covers the earlier ones, but each barrier's phase is consumed to keep them paired)
+  for (int c = max(0, nchunk - 2); c < nchunk && ok; ++c) {
+    const int b = c & 1;
+    ok = tc::mbar_wait_bounded(mbar + b, parity[b], TC_WAIT_BUDGET);
+    parity[b] ^= 1u;
   }
   if (!ok) atomicOr(&g_tc_status, 1);
   tc::fence_after_sync();
@@ -798,7 +838,7 @@ void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cud
   if (nprob <= 0 || t.max_nvec <= 0) return;
   if (tile == DENSE_TILE_TC) {   // 128 x 64 tiles: tensor cores in FP32, two 64 x 64 halves in FP64
     if (sizeof(T) == 4) {
-      const size_t smem = (size_t)(2 * TC_BM * TC_BK + 2 * TC_BN * TC_BK) * sizeof(float) + 16;
+      const size_t smem = (size_t)(2 * TC_STAGE) * sizeof(float) + 32;
       ensure_dynamic_smem((const void*)k_dense_tc, smem);
       k_dense_tc<<<dim3(nprob, t.max_nvec), 128, smem, s>>>(d_probs, t);
     } else {
