@@ -130,7 +130,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // Product 2: C[m][(vector, n)] += As^T Ts, 4 x 4 register tiles that each thread
 // keeps for the whole group (MAXT tiles per thread).
 template <typename T, int NT, int MAXT, int NB>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 4 : 2) : 1) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 6 : (MAXT == 2 ? 3 : 2)) : 1) k_sandwich_small(const SProb* __restrict__ probs, const int* __restrict__ gstart,
                                                        const __grid_constant__ SysTable tab, int rpc, int dm, int dk1,
                                                        int dk2, int dn) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
