@@ -588,9 +588,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       // accumulate into A_DS_p: (i,j) as is, (j,i) with rows transposed; for i == j both
       if (ord == 0) G.add_block(Y, L1, Yc.get(), L1, nn * nn, (int)L1, 1.0, 0);
       if (ord == 1 || i == j) G.add_block(Y, L1, Yc.get(), L1, nn * nn, (int)L1, 1.0, nn);
-      G.sync();
     }
-    G.sync();
+    // no synchronisation per pair: temporaries return to this thread's cache and are
+    // reused in stream order, so the host plans the next pair while this one runs
   }
 
   tm.mark("  pair loop (D, A_DS)");
@@ -667,7 +667,6 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
           else { G.kron(out, L, Sq, lds, w, nn, ni, 3, 2.0); G.kron(out, L, Sq, lds, w, nn, ni, 2, -1.0); }
         }
       }
-      G.sync();
     }
   }
   G.sync();
