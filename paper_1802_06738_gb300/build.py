@@ -44,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and out:
             print(out.decode())
     if force or procs or lib_mtime < newest:
-        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB_PATH] + objs + ["-lcusolver", "-lcudart"]
+        cmd = [nvcc] + ARCH + ["-shared", "-o", LIB_PATH] + objs + ["-lcusolver", "-lcublas", "-lcudart"]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout.decode())

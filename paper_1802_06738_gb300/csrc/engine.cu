@@ -1,5 +1,7 @@
 // Dense tensor engine: grouped GEMM, N-d permute, einsum planner.
 #include "engine.cuh"
+#include <cublas_v2.h>
+#include <tuple>
 #include <algorithm>
 #include <numeric>
 #include <map>
@@ -286,9 +288,84 @@ inline unsigned grid_for(size_t n) {
 }
 }  // namespace
 
+namespace {
+// One cuBLAS handle per host thread (created on first use, destroyed at thread exit).
+struct ThreadBlas {
+  cublasHandle_t h = nullptr;
+  ~ThreadBlas() {
+    if (h) {
+      std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+      cublasDestroy(h);
+    }
+  }
+  cublasHandle_t get(cudaStream_t s) {
+    if (!h) {
+      std::lock_guard<std::recursive_mutex> lk(capture_mutex());
+      PN_CHECK(cublasCreate(&h) == CUBLAS_STATUS_SUCCESS, PNOEOM_ERR_CUDA, "cublasCreate failed");
+    }
+    PN_CHECK(cublasSetStream(h, s) == CUBLAS_STATUS_SUCCESS, PNOEOM_ERR_CUDA, "cublasSetStream failed");
+    return h;
+  }
+};
+thread_local ThreadBlas t_blas;
+
+// FP64 problems with at least this many multiply-adds go to cuBLAS (the FP64 tensor-core
+// GEMMs of the library), grouped by shape into batched calls; smaller ones stay on the
+// grouped SIMT kernel, where one launch covers many of them.
+constexpr double BLAS_MIN_MACS = 32768.0;
+
+// C = alpha op(A) op(B) + beta C in row-major storage is, read column-major,
+// C^T = alpha op(B)^T op(A)^T + beta C^T: cuBLAS gets B first, m = N, n = M.
+void blas_dgemm_groups(const std::vector<GemmProb<double>>& big, cudaStream_t s) {
+  if (big.empty()) return;
+  using Key = std::tuple<int, int, int, int, int, int, int, int, double, double>;
+  std::map<Key, std::vector<const GemmProb<double>*>> groups;
+  for (const auto& P : big) groups[Key{P.M, P.N, P.K, P.lda, P.ldb, P.ldc, P.ta, P.tb, P.alpha, P.beta}].push_back(&P);
+  cublasHandle_t h = t_blas.get(s);
+  for (auto& g : groups) {
+    const GemmProb<double>& P = *g.second.front();
+    const cublasOperation_t opb = P.tb ? CUBLAS_OP_T : CUBLAS_OP_N, opa = P.ta ? CUBLAS_OP_T : CUBLAS_OP_N;
+    const double al = P.alpha, be = P.beta;
+    cublasStatus_t st;
+    if (g.second.size() == 1) {
+      st = cublasDgemm(h, opb, opa, P.N, P.M, P.K, &al, P.b, P.ldb, P.a, P.lda, &be, P.c, P.ldc);
+    } else {
+      const size_t n = g.second.size();
+      std::vector<const double*> hp(3 * n);
+      for (size_t k = 0; k < n; ++k) {
+        hp[k] = g.second[k]->b;
+        hp[n + k] = g.second[k]->a;
+        hp[2 * n + k] = g.second[k]->c;
+      }
+      DBuf<const double*> dp(3 * n);
+      dp.upload(hp.data(), 3 * n, s);
+      st = cublasDgemmBatched(h, opb, opa, P.N, P.M, P.K, &al, dp.get(), P.ldb, dp.get() + n, P.lda, &be,
+                              const_cast<double* const*>(dp.get() + 2 * n), P.ldc, (int)n);
+    }
+    PN_CHECK(st == CUBLAS_STATUS_SUCCESS, PNOEOM_ERR_CUDA, "cuBLAS DGEMM failed");
+  }
+}
+}  // namespace
+
 template <typename T>
-void grouped_gemm(const std::vector<GemmProb<T>>& probs, cudaStream_t s) {
-  if (probs.empty()) return;
+void grouped_gemm(const std::vector<GemmProb<T>>& probs_in, cudaStream_t s) {
+  if (probs_in.empty()) return;
+  std::vector<GemmProb<T>> rest;
+  const std::vector<GemmProb<T>>* pp = &probs_in;
+  if (sizeof(T) == 8) {
+    std::vector<GemmProb<double>> big;
+    for (const auto& P : probs_in) {
+      if (P.M <= 0 || P.N <= 0) continue;
+      if ((double)P.M * P.N * std::max(P.K, 1) >= BLAS_MIN_MACS && P.K > 0)
+        big.push_back(reinterpret_cast<const GemmProb<double>&>(P));
+      else
+        rest.push_back(P);
+    }
+    blas_dgemm_groups(big, s);
+    pp = &rest;
+    if (rest.empty()) return;
+  }
+  const std::vector<GemmProb<T>>& probs = *pp;
   // by-value path: up to NPV problems per launch
   size_t i0 = 0;
   bool small = true;
