@@ -966,6 +966,10 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       }
       auto ranges = order_by_output(b[k]);
       S.nprob = (int)b[k].size();
+      bool all_ab = !b[k].empty();
+      for (const SProb& q : b[k]) all_ab = all_ab && q.a_buf != B_NONE && q.b_buf != B_NONE;
+      S.ab = all_ab;
+      S.pb = 1;
       S.h_probs = b[k];
       for (int c = 0; c < NGROUP_CAND; ++c) {
         std::vector<int>& st = S.h_starts[c];

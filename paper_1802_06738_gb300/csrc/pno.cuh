@@ -27,6 +27,8 @@ struct SmallSet {
   int dims[4] = {1, 1, 1, 1};   // max M, K1, K2, N
   int nprob = 0;
   int gchoice = 2, rchoice = NRPC_CAND - 1;       // tuned (group size, vectors per CTA) of this set
+  bool ab = false;                                 // every problem has A and B (batched variant possible)
+  int pb = 1;                                      // problems staged together (tuned; 1 unless ab)
   double tune_ms[NTUNE] = {0};
   std::vector<SProb> h_probs;                      // host copies (batch merging)
   std::vector<int> h_starts[NGROUP_CAND];

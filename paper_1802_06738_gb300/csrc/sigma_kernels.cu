@@ -387,6 +387,230 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 6 : (MAXT ==
   }
 }
 
+// Batched grouped sandwich, for sets whose problems all have A and B: a CTA stages
+// pb consecutive problems of its group at once (single stage buffer), forms T for all of
+// them in one pass of product 1, and runs product 2 once over the concatenation of their
+// K ranges: C[m][(vector, n)] += sum over the batch of A_p T_p = [A_1 .. A_pb][T_1; ..; T_pb].
+// Shared memory (floats), K1p = pad4(dk1), with compact K offsets koff_p = sum of pad4(K1):
+//   Xs [pb][dk2][R * K1p]   X_eff^T per problem
+//   Bs [pb][dk2][Np]        B per problem
+//   As [pb * K1p][Mp]       A^T of the batch, rows koff_p .. (pad rows zero)
+//   Ts [pb * K1p][R * Np]   alpha_p X_eff B_p of the batch, rows koff_p ..
+// Barriers per batch: two (after staging, after product 1), instead of two or three per
+// problem.  Register tiles, split-K and staging are those of k_sandwich_small.
+constexpr int PB_MAX = 4;
+template <typename T, int NT, int MAXT>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 6 : (MAXT == 2 ? 3 : 2)) : 1)
+    k_sandwich_batch(const SProb* __restrict__ probs, const int* __restrict__ gstart, const __grid_constant__ SysTable tab,
+                     int rpc, int pb, int dm, int dk1, int dk2, int dn) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Mp = pad4(dm), K1p = pad4(dk1), Np = pad4(dn);
+  const int xld = rpc * K1p, tld = rpc * Np;
+  const int xsz = dk2 * xld, bsz = dk2 * Np;
+  T* Xs0 = reinterpret_cast<T*>(smem_raw);
+  T* Bs0 = Xs0 + pb * xsz;
+  T* As = Bs0 + pb * bsz;
+  T* Ts = As + pb * K1p * Mp;
+  const int total = pb * (xsz + bsz + K1p * Mp + K1p * tld);
+  const int tid = threadIdx.x;
+  const int g0 = gstart[blockIdx.x], g1 = gstart[blockIdx.x + 1];
+  const SProb P0 = probs[g0];
+  const int rbase = blockIdx.y * rpc;
+  const int nr = min(rpc, tab.s[P0.sys].nvec - rbase);
+  if (nr <= 0) return;
+  const int Mt = min(64, P0.M - P0.m0), Nt = min(64, P0.N - P0.n0);
+  const int nt4 = (Nt + 3) >> 2;
+  const int nct = ((Mt + 3) >> 2) * nr * nt4;
+  for (int e = tid; e < total; e += NT) Xs0[e] = T(0);
+  int s2 = 1;
+  while (s2 < 8 && nct * s2 * 2 <= NT) s2 *= 2;
+  const int sl2 = tid & (s2 - 1);
+  int cm4[MAXT], cr[MAXT], cn4[MAXT];
+  T acc[MAXT][4][4];
+#pragma unroll
+  for (int j = 0; j < MAXT; ++j) {
+    const int t = (tid + j * NT) / s2;
+    cn4[j] = t % nt4;
+    cr[j] = (t / nt4) % nr;
+    cm4[j] = t / (nt4 * nr);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[j][a][b] = T(0);
+  }
+  for (int gb = g0; gb < g1; gb += pb) {
+    const int nb = min(pb, g1 - gb);
+    int koff[PB_MAX + 1], t1off[PB_MAX + 1];
+    koff[0] = 0;
+    t1off[0] = 0;
+#pragma unroll
+    for (int q = 0; q < PB_MAX; ++q) {
+      const int K1 = q < nb ? probs[gb + q].K1 : 0;
+      koff[q + 1] = koff[q] + pad4(K1);
+      t1off[q + 1] = t1off[q] + nr * ((K1 + 3) >> 2) * nt4;
+    }
+    __syncthreads();   // every thread is done with the previous batch
+    for (int q = 0; q < nb; ++q) {   // staging
+      const SProb& P = probs[gb + q];
+      const int K1 = P.K1, K2 = P.K2;
+      T* Xs = Xs0 + q * xsz;
+      T* Bs = Bs0 + q * bsz;
+      T* Aq = As + koff[q] * Mp;
+      {
+        const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
+        if (P.ta) {
+          for (int k = tid; k < K1; k += NT) {
+            const T* src = A + (int64_t)k * P.lda + P.m0;
+            for (int m = 0; m < Mt; ++m) cp_async_el(Aq + k * Mp + m, src + m);
+          }
+        } else {
+          for (int m = tid; m < Mt; m += NT) {
+            const T* src = A + (int64_t)(P.m0 + m) * P.lda;
+            for (int k = 0; k < K1; ++k) cp_async_el(Aq + k * Mp + m, src + k);
+          }
+        }
+        for (int e = tid; e < (pad4(K1) - K1) * Mp; e += NT) Aq[K1 * Mp + e] = T(0);   // K padding rows
+      }
+      {
+        const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, 0) + P.b_off;
+        if (P.tb) {
+          for (int n = tid; n < Nt; n += NT) {
+            const T* src = Bm + (int64_t)(P.n0 + n) * P.ldb;
+            for (int k = 0; k < K2; ++k) cp_async_el(Bs + k * Np + n, src + k);
+          }
+        } else {
+          for (int k = tid; k < K2; k += NT) {
+            const T* src = Bm + (int64_t)k * P.ldb + P.n0;
+            for (int n = 0; n < Nt; ++n) cp_async_el(Bs + k * Np + n, src + n);
+          }
+        }
+      }
+      if (P.xb == 0.0) {
+        if (P.tx) {
+          for (int it = tid; it < nr * K2; it += NT) {
+            const int r = it / K2, b = it - r * K2;
+            const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)b * P.ldx;
+            T* dst = Xs + b * xld + r * K1p;
+            for (int a = 0; a < K1; ++a) cp_async_el(dst + a, src + a);
+          }
+        } else {
+          for (int it = tid; it < nr * K1; it += NT) {
+            const int r = it / K1, a = it - r * K1;
+            const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)a * P.ldx;
+            T* dst = Xs + r * K1p + a;
+            for (int b = 0; b < K2; ++b) cp_async_el(dst + b * xld, src + b);
+          }
+        }
+      } else {   // square X: X_eff = opX(X) + xb opX(X)^T, merged in registers
+        const T xb = (T)P.xb;
+        for (int it = tid; it < nr * K1; it += NT) {
+          const int r = it / K1, b = it - r * K1;
+          const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
+          const T* row = X + (int64_t)b * P.ldx;
+          const T* col = X + b;
+          T* dst = Xs + b * xld + r * K1p;
+          if (P.tx)
+            for (int a = 0; a < K1; ++a) dst[a] = row[a] + xb * col[(int64_t)a * P.ldx];
+          else
+            for (int a = 0; a < K1; ++a) dst[a] = col[(int64_t)a * P.ldx] + xb * row[a];
+        }
+      }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    {   // product 1 over the batch: tiles (problem, vector, a4, n4)
+      const int n1 = t1off[nb];
+      int s1 = 1;
+      while (s1 < 8 && n1 * s1 * 2 <= NT) s1 *= 2;
+      const int total1 = n1 * s1;
+      const float rd_nt4 = 1.0f / (float)nt4;
+      for (int base = 0; base < total1; base += NT) {
+        const int tt = base + tid;
+        const bool valid = tt < total1;
+        const int t = valid ? tt / s1 : 0, sl = tt & (s1 - 1);
+        int q = 0;
+#pragma unroll
+        for (int z = 1; z < PB_MAX; ++z) q += (z < nb && t >= t1off[z]) ? 1 : 0;
+        const SProb& P = probs[gb + q];
+        const int ka4 = (P.K1 + 3) >> 2;
+        const int tl = t - t1off[q];
+        const int rest = fdiv(tl, rd_nt4), n4 = tl - rest * nt4;
+        const int r = rest / ka4, a4 = rest - r * ka4;
+        T c[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) c[a][b] = T(0);
+        const T* xp = Xs0 + q * xsz + r * K1p + a4 * 4;
+        const T* bp = Bs0 + q * bsz + n4 * 4;
+        if (valid)
+          for (int b = sl; b < P.K2; b += s1) {
+            T xv[4], bv[4];
+            ld4(xp + b * xld, xv);
+            ld4(bp + b * Np, bv);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+              for (int w = 0; w < 4; ++w) c[a][w] += xv[a] * bv[w];
+          }
+        for (int off = 1; off < s1; off <<= 1)
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) c[a][w] += __shfl_xor_sync(0xffffffffu, c[a][w], off);
+        if (valid && sl == 0) {
+          const T alpha = (T)P.alpha;
+          T* tp = Ts + (koff[q] + a4 * 4) * tld + r * Np + n4 * 4;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            T o[4] = {alpha * c[a][0], alpha * c[a][1], alpha * c[a][2], alpha * c[a][3]};
+            st4(tp + a * tld, o);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const int Ktot = koff[nb];
+#pragma unroll
+    for (int j = 0; j < MAXT; ++j) {   // product 2 over the concatenated K of the batch
+      if (tid + j * NT >= nct * s2) continue;
+      const T* tp = Ts + cr[j] * Np + cn4[j] * 4;
+      const T* ap = As + cm4[j] * 4;
+      for (int k = sl2; k < Ktot; k += s2) {
+        T av[4], tv[4];
+        ld4(ap + k * Mp, av);
+        ld4(tp + k * tld, tv);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int w = 0; w < 4; ++w) acc[j][a][w] += av[a] * tv[w];
+      }
+    }
+  }
+  if (s2 > 1)
+    for (int off = 1; off < s2; off <<= 1)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[0][a][w] += __shfl_xor_sync(0xffffffffu, acc[0][a][w], off);
+#pragma unroll
+  for (int j = 0; j < MAXT; ++j) {
+    if (tid + j * NT >= nct * s2 || sl2 != 0) continue;
+    T* C = mbuf<T>(tab, P0.sys, P0.c_buf, rbase + cr[j]) + P0.c_off;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const int m = cm4[j] * 4 + a, n = cn4[j] * 4 + w;
+        if (m < Mt && n < Nt) {
+          const int64_t gm = P0.m0 + m, gn = P0.n0 + n;
+          atomicAdd(P0.tc ? C + gn * P0.ldc + gm : C + gm * P0.ldc + gn, acc[j][a][w]);
+        }
+      }
+  }
+}
+
 // Dense product tile: C[m0.., n0..] += alpha opA(A) opB(B) over K in [k0, k0 + klen).
 // The tile is TM rows x BT columns, computed in passes of BT x BT with (BT/4)^2 threads
 // and 4 x 4 register tiles, K staged in chunks of 16 (A^T and B in shared memory,
@@ -819,12 +1043,45 @@ static void launch_small(const SProb* d_probs, const int* d_group_start, int ngr
     launch_small_nb<T, NT, MAXT, 1>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, rpc, smem_of(rpc, 1), s);
 }
 
+template <typename T, int NT, int MAXT>
+static bool launch_batch(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
+                         int dk2, int dn, int rpc, int pb, cudaStream_t s) {
+  const int Mp = pad4(dm), K1p = pad4(dk1), Np = pad4(dn);
+  const int tiles = (Mp / 4) * (Np / 4);
+  rpc = std::max(1, std::min(rpc, std::min(t.max_nvec, NT * MAXT / tiles)));
+  auto smem_of = [&](int r, int b) {
+    return (size_t)b * (size_t)(dk2 * r * K1p + dk2 * Np + K1p * Mp + K1p * r * Np) * sizeof(T);
+  };
+  const size_t limit = 200 * 1024;
+  while (pb > 1 && smem_of(rpc, pb) > limit) --pb;
+  while (rpc > 1 && smem_of(rpc, pb) > limit) --rpc;
+  if (pb < 2 || smem_of(rpc, pb) > limit || tiles > NT * MAXT) return false;
+  const size_t smem = smem_of(rpc, pb);
+  ensure_dynamic_smem((const void*)k_sandwich_batch<T, NT, MAXT>, smem);
+  const int ychunks = (t.max_nvec + rpc - 1) / rpc;
+  k_sandwich_batch<T, NT, MAXT>
+      <<<dim3(ngroups, ychunks), NT, smem, s>>>(d_probs, d_group_start, t, rpc, pb, dm, dk1, dk2, dn);
+  PN_CUDA(cudaGetLastError());
+  return true;
+}
+
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
-                        int dk2, int dn, int roots_per_cta, cudaStream_t s) {
+                        int dk2, int dn, int roots_per_cta, int pb, cudaStream_t s) {
   if (ngroups <= 0 || t.max_nvec <= 0) return;
   const int big = std::max(std::max(dm, dn), std::max(dk1, dk2));
   PN_CHECK(big <= SMALL_DIM, PNOEOM_ERR_UNSUPPORTED, "block too large for the grouped sandwich kernel");
+  pb = std::min(pb, PB_MAX);
+  if (pb > 1) {   // every problem has A and B: batched variant
+    bool done;
+    if (big <= 16)
+      done = launch_batch<T, 128, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, pb, s);
+    else if (big <= 32 || sizeof(T) == 8)
+      done = launch_batch<T, 256, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, pb, s);
+    else
+      done = launch_batch<T, 256, 4>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, pb, s);
+    if (done) return;
+  }
   if (big <= 16)
     launch_small<T, 128, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
   else if (big <= 32 || sizeof(T) == 8)
@@ -864,8 +1121,10 @@ template void run_sandwich<double>(const SProb*, int, const SysTable&, int, cuda
 template void run_sandwich<float>(const SProb*, int, const SysTable&, int, cudaStream_t);
 template void run_gemv<double>(const VProb*, int, const SysTable&, cudaStream_t);
 template void run_gemv<float>(const VProb*, int, const SysTable&, cudaStream_t);
-template void run_sandwich_small<double>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, cudaStream_t);
-template void run_sandwich_small<float>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, cudaStream_t);
+template void run_sandwich_small<double>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, int,
+                                        cudaStream_t);
+template void run_sandwich_small<float>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, int,
+                                       cudaStream_t);
 template void run_dense<double>(const DProb*, int, const SysTable&, int, cudaStream_t);
 template void run_dense<float>(const DProb*, int, const SysTable&, int, cudaStream_t);
 

@@ -82,9 +82,11 @@ void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_e
 // register-tiled GEMM each, keeps the C tile of every vector in registers over the
 // group and adds it to C once.  dm, dk1, dk2, dn bound the tile rows, the rows and
 // columns of the staged X block, and the tile columns of every problem of the set.
+// pb > 1 (every problem of the set has A and B): pb consecutive problems of a group are
+// staged together and product 2 runs once over their concatenated K ranges.
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
-                        int dk2, int dn, int roots_per_cta, cudaStream_t s);
+                        int dk2, int dn, int roots_per_cta, int pb, cudaStream_t s);
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
 // Output tiles of a dense list: DENSE_TILE_TC = 128 rows x 64 columns (tensor cores in
