@@ -422,6 +422,24 @@ struct Dav {
     if (nrm > 0) { scale<double>(t, 1.0 / nrm, L, s); }
     return nrm;
   }
+  // orth() of t against rows 0..m-1 of V, applying the same combinations to st (sigma of t)
+  // with the rows of S (sigma is linear, so st stays sigma of the orthonormalised t)
+  double orth_pair(double* V, double* S, int m, double* t, double* st) {
+    for (int pass = 0; pass < 2; ++pass) {
+      if (!m) break;
+      std::vector<double> c = gram(t, 1, V, m);
+      for (double& x : c) x = -x;
+      combine(t, V, c, m, 1, 1.0);
+      combine(st, S, c, m, 1, 1.0);
+    }
+    std::vector<double> nn = gram(t, 1, t, 1);
+    double nrm = std::sqrt(std::max(0.0, nn[0]));
+    if (nrm > 0) {
+      scale<double>(t, 1.0 / nrm, L, s);
+      scale<double>(st, 1.0 / nrm, L, s);
+    }
+    return nrm;
+  }
 };
 }  // namespace
 
@@ -518,16 +536,27 @@ struct DavState {
     std::vector<int> add;
     for (int q = 0; q < nr; ++q) if (rn[q] >= tol_now()) add.push_back(q);
     int first_new = m;
-    if (m + (int)add.size() > maxsub) {      // collapse onto the Ritz vectors
-      PN_CUDA(cudaMemcpyAsync(V.get(), X.get(), (size_t)nr * L * 8, cudaMemcpyDeviceToDevice, s));
+    if (m + (int)add.size() > maxsub) {
+      // thick restart: keep the Ritz vectors of the lowest nkeep subspace eigenvalues (at
+      // least 2N, half the subspace), with their sigma formed from the stored sigma vectors
+      // by the same combinations (no new sigma evaluations)
+      const int nkeep = std::max(nr, std::min(m, std::min(std::max(2 * nr, maxsub / 2), maxsub - (int)add.size())));
+      std::vector<double> Ck((size_t)nkeep * m);
+      for (int q = 0; q < nkeep; ++q)
+        for (int a = 0; a < m; ++a) Ck[(size_t)q * m + a] = VR[(size_t)a * m + ord[q]];
+      DBuf<double> Xk((size_t)nkeep * L), Sk((size_t)nkeep * L);
+      D.combine(Xk.get(), V.get(), Ck, m, nkeep, 0.0);
+      D.combine(Sk.get(), S.get(), Ck, m, nkeep, 0.0);
       int mm = 0;
-      for (int q = 0; q < nr; ++q) {
+      for (int q = 0; q < nkeep; ++q) {
         double* t = V.get() + (int64_t)mm * L;
-        if (mm != q) PN_CUDA(cudaMemcpyAsync(t, V.get() + (int64_t)q * L, L * 8, cudaMemcpyDeviceToDevice, s));
-        if (D.orth(V.get(), mm, t) > 1e-10) ++mm;
+        double* st = S.get() + (int64_t)mm * L;
+        PN_CUDA(cudaMemcpyAsync(t, Xk.get() + (int64_t)q * L, L * 8, cudaMemcpyDeviceToDevice, s));
+        PN_CUDA(cudaMemcpyAsync(st, Sk.get() + (int64_t)q * L, L * 8, cudaMemcpyDeviceToDevice, s));
+        if (D.orth_pair(V.get(), S.get(), mm, t, st) > 1e-10) ++mm;
       }
       m = mm;
-      first_new = 0;                          // the collapsed vectors need sigma again
+      first_new = m;
     }
     int m0 = m;
     for (int q : add) {
