@@ -153,7 +153,9 @@ int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* 
  * semicanonical preconditioner omega + f_ii (+ f_jj) - fbar_a (- fbar_b),
  * FP64 orthogonalisation and subspace diagonalisation.  energies and
  * res_norms: host arrays of nroots_solve doubles; iters: host int.  Blocking.
- * Returns PNOEOM_ERR_NOT_CONVERGED with the best values after max_iter. */
+ * Returns PNOEOM_ERR_NOT_CONVERGED with the best values after max_iter, and
+ * PNOEOM_ERR_TIMEOUT when a tensor-core kernel's bounded wait ran out during the
+ * solve (see pnoeom_device_status; the results are then invalid). */
 int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, void* cuda_stream,
                    double* energies, double* res_norms, int* iters);
 
@@ -177,7 +179,9 @@ int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, co
 /* Davidson solves of all members in lockstep (each member its own subspace;
  * every round evaluates all members' pending vectors in one sigma launch).
  * Host outputs: energies and res_norms n x nroots_solve, iters and converged n.
- * Returns PNOEOM_ERR_NOT_CONVERGED if any member did not converge. */
+ * Returns PNOEOM_ERR_NOT_CONVERGED if any member did not converge, and
+ * PNOEOM_ERR_TIMEOUT when a tensor-core kernel's bounded wait ran out (see
+ * pnoeom_device_status; the results are then invalid). */
 int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* opts, void* cuda_stream,
                        double* energies, double* res_norms, int* iters, int* converged);
 

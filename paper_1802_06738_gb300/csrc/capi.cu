@@ -195,6 +195,8 @@ int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, vo
     PN_CHECK(ctx && pno && opts && energies && res_norms && iters, PNOEOM_ERR_INVALID_ARG, "NULL argument");
     PN_CUDA(cudaSetDevice(ctx->device));
     pnoeom::run_davidson(ctx, pno, opts, st(cuda_stream), energies, res_norms, iters, &conv);
+    PN_CHECK(pnoeom::device_status(true, st(cuda_stream)) == 0, PNOEOM_ERR_TIMEOUT,
+             "a tensor-core kernel's bounded wait ran out during the solve: results are invalid");
   });
   if (rc == PNOEOM_OK && !conv) {
     g_last_error = "Davidson did not converge within max_iter";
@@ -240,6 +242,8 @@ int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* 
     PN_CHECK(ctx && batch && opts && energies && res_norms && iters && converged, PNOEOM_ERR_INVALID_ARG, "NULL argument");
     PN_CUDA(cudaSetDevice(ctx->device));
     pnoeom::batch_solve(batch, opts, st(cuda_stream), energies, res_norms, iters, converged);
+    PN_CHECK(pnoeom::device_status(true, st(cuda_stream)) == 0, PNOEOM_ERR_TIMEOUT,
+             "a tensor-core kernel's bounded wait ran out during the solve: results are invalid");
     for (size_t k = 0; k < batch->members.size(); ++k) all = all && converged[k];
   });
   if (rc == PNOEOM_OK && !all) {
@@ -330,7 +334,7 @@ int pnoeom_device_status(pnoeom_ctx* ctx, int clear, int* status) {
     PN_CHECK(ctx && status, PNOEOM_ERR_INVALID_ARG, "NULL argument");
     PN_CUDA(cudaSetDevice(ctx->device));
     PN_CUDA(cudaDeviceSynchronize());
-    *status = pnoeom::device_status(clear != 0);
+    *status = pnoeom::device_status(clear != 0, nullptr);
   });
 }
 

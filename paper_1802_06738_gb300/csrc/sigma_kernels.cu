@@ -1107,12 +1107,14 @@ void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cud
   PN_CUDA(cudaGetLastError());
 }
 
-int device_status(bool clear) {
+int device_status(bool clear, cudaStream_t s) {
   int v = 0;
-  PN_CUDA(cudaMemcpyFromSymbol(&v, g_tc_status, sizeof(int)));
-  if (clear) {
+  PN_CUDA(cudaMemcpyFromSymbolAsync(&v, g_tc_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+  PN_CUDA(cudaStreamSynchronize(s));
+  if (clear && v) {
     const int z = 0;
-    PN_CUDA(cudaMemcpyToSymbol(g_tc_status, &z, sizeof(int)));
+    PN_CUDA(cudaMemcpyToSymbolAsync(g_tc_status, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    PN_CUDA(cudaStreamSynchronize(s));
   }
   return v;
 }

@@ -94,9 +94,9 @@ void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s
 constexpr int DENSE_TILE_TC = 128;
 template <typename T>
 void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cudaStream_t s);
-// Reads (and with clear, resets) the tensor-core kernels' device status word: 0 when
-// every bounded wait completed.
-int device_status(bool clear);
+// Reads (and with clear, resets) the tensor-core kernels' device status word, ordered on
+// stream s: 0 when every bounded wait completed.
+int device_status(bool clear, cudaStream_t s);
 void gemm_tf32x3(const float* A, const float* B, float* C, int M, int N, int K, float alpha, cudaStream_t s);
 
 }  // namespace pnoeom

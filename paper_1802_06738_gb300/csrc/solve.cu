@@ -578,9 +578,18 @@ struct DavState {
   }
 
   void finish_or_refine() {
-    if (prec == PNOEOM_FP32 && refine) {   // FP64 refinement: sigma of the whole subspace again in FP64
+    if (prec == PNOEOM_FP32 && refine) {
+      // FP64 refinement, started from the current Ritz vectors: the subspace collapses onto
+      // them (orthonormalised) and only their sigma is evaluated again, in FP64
       prec = PNOEOM_FP64;
       w_old.clear();
+      int mm = 0;
+      for (int q = 0; q < nr; ++q) {
+        double* t = V.get() + (int64_t)mm * L;
+        PN_CUDA(cudaMemcpyAsync(t, X.get() + (int64_t)q * L, L * 8, cudaMemcpyDeviceToDevice, s));
+        if (D.orth(V.get(), mm, t) > 1e-10) ++mm;
+      }
+      m = mm;
       p0 = 0; p1 = m;
       return;
     }
