@@ -29,6 +29,7 @@ struct SmallSet {
   int gchoice = 2, rchoice = NRPC_CAND - 1;       // tuned (group size, vectors per CTA) of this set
   bool ab = false;                                 // every problem has A and B (batched variant possible)
   int pb = 1;                                      // problems staged together (tuned; 1 unless ab)
+  int nb = 0;                                      // stage buffers of the unbatched kernel (tuned; 0 = by occupancy)
   double tune_ms[NTUNE] = {0};
   std::vector<SProb> h_probs;                      // host copies (batch merging)
   std::vector<int> h_starts[NGROUP_CAND];

@@ -1023,7 +1023,7 @@ static void launch_small_nb(const SProb* d_probs, const int* d_group_start, int 
 
 template <typename T, int NT, int MAXT>
 static void launch_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
-                         int dk2, int dn, int rpc, cudaStream_t s) {
+                         int dk2, int dn, int rpc, int nbsel, cudaStream_t s) {
   const int Mp = pad4(dm), K1p = pad4(dk1), Np = pad4(dn);
   // C register tiles per vector: rows/4 x cols/4; at most NT * MAXT per CTA
   const int tiles = (Mp / 4) * (Np / 4);
@@ -1032,8 +1032,10 @@ static void launch_small(const SProb* d_probs, const int* d_group_start, int ngr
     return (size_t)(nb * (dk1 * Mp + dk2 * Np + dk2 * r * K1p) + K1p * r * Np) * sizeof(T);
   };
   const size_t limit = 200 * 1024, two_per_sm = 113 * 1024;
-  // double buffering unless only single buffering leaves room for two CTAs per SM
-  const int nb = (smem_of(rpc, 2) > two_per_sm && smem_of(rpc, 1) <= two_per_sm) ? 1 : 2;
+  // stage buffers: the tuned choice (nbsel 1 or 2) if given, else double buffering unless
+  // only single buffering leaves room for two CTAs per SM
+  int nb = (smem_of(rpc, 2) > two_per_sm && smem_of(rpc, 1) <= two_per_sm) ? 1 : 2;
+  if (nbsel == 1 || nbsel == 2) nb = nbsel;
   while (rpc > 1 && smem_of(rpc, nb) > limit) --rpc;
   PN_CHECK(smem_of(rpc, nb) <= limit && tiles <= NT * MAXT, PNOEOM_ERR_UNSUPPORTED,
            "PNO blocks too large for the grouped sandwich kernel");
@@ -1067,7 +1069,7 @@ static bool launch_batch(const SProb* d_probs, const int* d_group_start, int ngr
 
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
-                        int dk2, int dn, int roots_per_cta, int pb, cudaStream_t s) {
+                        int dk2, int dn, int roots_per_cta, int pb, int nbsel, cudaStream_t s) {
   if (ngroups <= 0 || t.max_nvec <= 0) return;
   const int big = std::max(std::max(dm, dn), std::max(dk1, dk2));
   PN_CHECK(big <= SMALL_DIM, PNOEOM_ERR_UNSUPPORTED, "block too large for the grouped sandwich kernel");
@@ -1083,11 +1085,11 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
     if (done) return;
   }
   if (big <= 16)
-    launch_small<T, 128, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
+    launch_small<T, 128, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, nbsel, s);
   else if (big <= 32 || sizeof(T) == 8)
-    launch_small<T, 256, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
+    launch_small<T, 256, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, nbsel, s);
   else
-    launch_small<T, 256, 4>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, s);
+    launch_small<T, 256, 4>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, nbsel, s);
 }
 
 template <typename T>
@@ -1124,9 +1126,9 @@ template void run_sandwich<float>(const SProb*, int, const SysTable&, int, cudaS
 template void run_gemv<double>(const VProb*, int, const SysTable&, cudaStream_t);
 template void run_gemv<float>(const VProb*, int, const SysTable&, cudaStream_t);
 template void run_sandwich_small<double>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, int,
-                                        cudaStream_t);
+                                        int, cudaStream_t);
 template void run_sandwich_small<float>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, int,
-                                       cudaStream_t);
+                                       int, cudaStream_t);
 template void run_dense<double>(const DProb*, int, const SysTable&, int, cudaStream_t);
 template void run_dense<float>(const DProb*, int, const SysTable&, int, cudaStream_t);
 
