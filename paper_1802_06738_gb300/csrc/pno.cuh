@@ -30,6 +30,7 @@ struct SmallSet {
   bool ab = false;                                 // every problem has A and B (batched variant possible)
   int pb = 1;                                      // problems staged together (tuned; 1 unless ab)
   int nb = 0;                                      // stage buffers of the unbatched kernel (tuned; 0 = by occupancy)
+  int shape = 0;                                   // CTA shape of the unbatched kernel (tuned; 0 = by bucket)
   double tune_ms[NTUNE] = {0};
   std::vector<SProb> h_probs;                      // host copies (batch merging)
   std::vector<int> h_starts[NGROUP_CAND];

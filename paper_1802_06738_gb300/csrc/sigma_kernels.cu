@@ -1069,7 +1069,7 @@ static bool launch_batch(const SProb* d_probs, const int* d_group_start, int ngr
 
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
-                        int dk2, int dn, int roots_per_cta, int pb, int nbsel, cudaStream_t s) {
+                        int dk2, int dn, int roots_per_cta, int pb, int nbsel, int shape, cudaStream_t s) {
   if (ngroups <= 0 || t.max_nvec <= 0) return;
   const int big = std::max(std::max(dm, dn), std::max(dk1, dk2));
   PN_CHECK(big <= SMALL_DIM, PNOEOM_ERR_UNSUPPORTED, "block too large for the grouped sandwich kernel");
@@ -1084,9 +1084,16 @@ void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngro
       done = launch_batch<T, 256, 4>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, pb, s);
     if (done) return;
   }
-  if (big <= 16)
+  // CTA shape: 1 = 128 threads x 2 tiles, 2 = 256 x 2, 3 = 256 x 4 (FP32 only); 0 = by bucket
+  int sh = shape;
+  if (sh == 3 && sizeof(T) == 8) sh = 2;
+  if (sh < 1 || sh > 3) sh = big <= 16 ? 1 : (big <= 32 || sizeof(T) == 8) ? 2 : 3;
+  const int tiles = (pad4(dm) / 4) * (pad4(dn) / 4);
+  if (sh == 1 && tiles > 128 * 2) sh = 2;
+  if (sh == 2 && tiles > 256 * 2) sh = sizeof(T) == 8 ? 2 : 3;
+  if (sh == 1)
     launch_small<T, 128, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, nbsel, s);
-  else if (big <= 32 || sizeof(T) == 8)
+  else if (sh == 2)
     launch_small<T, 256, 2>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, nbsel, s);
   else
     launch_small<T, 256, 4>(d_probs, d_group_start, ngroups, t, dm, dk1, dk2, dn, roots_per_cta, nbsel, s);
@@ -1126,9 +1133,9 @@ template void run_sandwich<float>(const SProb*, int, const SysTable&, int, cudaS
 template void run_gemv<double>(const VProb*, int, const SysTable&, cudaStream_t);
 template void run_gemv<float>(const VProb*, int, const SysTable&, cudaStream_t);
 template void run_sandwich_small<double>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, int,
-                                        int, cudaStream_t);
+                                        int, int, cudaStream_t);
 template void run_sandwich_small<float>(const SProb*, const int*, int, const SysTable&, int, int, int, int, int, int,
-                                       int, cudaStream_t);
+                                       int, int, cudaStream_t);
 template void run_dense<double>(const DProb*, int, const SysTable&, int, cudaStream_t);
 template void run_dense<float>(const DProb*, int, const SysTable&, int, cudaStream_t);
 

@@ -85,9 +85,11 @@ void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_e
 // pb > 1 (every problem of the set has A and B): pb consecutive problems of a group are
 // staged together and product 2 runs once over their concatenated K ranges.
 // nbsel: stage buffers of the unbatched kernel (1 or 2; 0 = choose by occupancy).
+// shape: CTA shape of the unbatched kernel (1 = 128 threads x 2 C tiles each, 2 = 256 x 2,
+// 3 = 256 x 4; 0 = by bucket); shapes whose tiles cannot hold the C block are raised.
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
-                        int dk2, int dn, int roots_per_cta, int pb, int nbsel, cudaStream_t s);
+                        int dk2, int dn, int roots_per_cta, int pb, int nbsel, int shape, cudaStream_t s);
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
 // Output tiles of a dense list: DENSE_TILE_TC = 128 rows x 64 columns (tensor cores in

@@ -34,7 +34,7 @@ SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* wor
 template <typename T>
 static void run_small_set(const SmallSet& S, int c, int rr, const SysTable& t, cudaStream_t s) {
   run_sandwich_small<T>(S.probs.get(), S.starts[c].get(), S.ngroups[c], t, S.dims[0], S.dims[1], S.dims[2], S.dims[3],
-                        RPC_CAND[rr], S.pb, S.nb, s);
+                        RPC_CAND[rr], S.pb, S.nb, S.shape, s);
 }
 
 // Time every small-sandwich set of the program alone for every (group size, vectors
@@ -52,8 +52,9 @@ static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* 
       SmallSet& S = sets[k];
       if (!S.nprob) continue;
       double best = 1e300;
-      S.pb = 1;   // candidates are timed unbatched, with buffering by occupancy; the number
-      S.nb = 0;   // of stage buffers and the batch size are chosen afterwards
+      S.pb = 1;      // candidates are timed unbatched, with buffering by occupancy and the
+      S.nb = 0;      // bucket's CTA shape; the shape, the number of stage buffers and the
+      S.shape = 0;   // batch size are chosen afterwards
       for (int c = 0; c < NGROUP_CAND; ++c)
         for (int rr = 0; rr < NRPC_CAND; ++rr) {
           run_small_set<T>(S, c, rr, t, s);   // warm-up
@@ -69,6 +70,23 @@ static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* 
           if (ms < best) { best = ms; S.gchoice = c; S.rchoice = rr; }
         }
       // then the number of problems staged together, for the chosen (group, vectors per CTA)
+      auto time_set = [&]() {
+        run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
+        PN_CUDA(cudaEventRecord(e0, s));
+        for (int q = 0; q < 3; ++q) run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
+        PN_CUDA(cudaEventRecord(e1, s));
+        PN_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        return (double)ms;
+      };
+      int best_shape = 0;
+      for (int shc : {1, 2, 3}) {
+        S.shape = shc;
+        const double ms = time_set();
+        if (ms < best) { best = ms; best_shape = shc; }
+      }
+      S.shape = best_shape;
       int best_nb = 0;
       for (int nbc : {1, 2}) {
         S.nb = nbc;
@@ -761,6 +779,7 @@ void batch_merge(pnoeom_batch* B, cudaStream_t s, bool tune) {
           D.ab = base == 0 ? S.ab : (D.ab && S.ab);
           D.pb = base == 0 ? S.pb : std::min(D.pb, S.pb);
           D.nb = base == 0 ? S.nb : (D.nb == S.nb ? D.nb : 0);
+          D.shape = base == 0 ? S.shape : (D.shape == S.shape ? D.shape : 0);
         }
         if (!D.ab) D.pb = 1;
       }
