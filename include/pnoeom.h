@@ -80,7 +80,12 @@ typedef struct {
  * (<= nroots_sa).  precision: PNOEOM_FP64 or PNOEOM_FP32 sigma;
  * refine_fp64: after an FP32 solve, continue with FP64 sigma until the FP64
  * tolerances hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
- * change between iterations; max_subspace <= 0 means 8 * nroots_solve. */
+ * change between iterations; max_subspace <= 0 means 8 * nroots_solve.
+ * state_specific: 0 (the default, and the paper's method) builds state-averaged
+ * PNOs/OSVs; k in 1..nroots_sa builds them from the CIS(D) pair densities of CIS
+ * root k alone (1-based), the state-specific construction the paper compares
+ * against (Sec. 2: one PNO space per state); the Davidson solve is unchanged, so
+ * root k is energies[k - 1] with nroots_solve >= k. */
 typedef struct {
   double t_pno, t_osv;
   int nroots_sa, nroots_solve;
@@ -88,6 +93,7 @@ typedef struct {
   int refine_fp64;
   int max_iter, max_subspace;
   double res_tol, e_tol;
+  int state_specific;
 } pnoeom_opts;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no

@@ -116,10 +116,26 @@ def _truncate_semicanonical(Dm, thresh, fvv):
     return U, fbar, occ, n
 
 
+def ss_densities(eps, B, o, root, nroots, omegas=None, bs=None):
+    """State-specific densities (Methods: the PNOs of one state, the construction the
+    state average replaces): D[i,j] from the CIS(D) doubles of CIS root `root` alone
+    (0-based, among the lowest `nroots`), with weight 1."""
+    if omegas is None:
+        omegas, bs = cis(eps, B, o, nroots)
+    Bd = cisd_doubles(eps, B, o, omegas[root], bs[root])
+    D = {}
+    for i in range(o):
+        for j in range(i, o):
+            D[i, j] = pair_density(Bd[i, j], i, j)
+    return D, omegas, bs
+
+
 class PNOSpace:
     """PNO/OSV bases of one system and the packed-vector maps."""
 
-    def __init__(self, eps, B, o, nroots, t_pno, t_osv=None, D=None):
+    def __init__(self, eps, B, o, nroots, t_pno, t_osv=None, D=None, cis=None):
+        """D: pair densities (default: the state average of the lowest nroots); cis:
+        (omegas, vectors) of the CIS roots that seed the Davidson guesses when D is given."""
         self.o = o
         self.v = len(eps) - o
         self.eps = eps
@@ -127,6 +143,8 @@ class PNOSpace:
             t_osv = t_pno / 10.0
         if D is None:
             D, self.cis_omega, self.cis_b = sa_densities(eps, B, o, nroots)
+        elif cis is not None:
+            self.cis_omega, self.cis_b = cis
         self.D = D
         fvv = np.diag(eps[o:])
         self.U, self.fbar, self.occ, self.alleig = {}, {}, {}, {}

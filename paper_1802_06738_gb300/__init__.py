@@ -40,13 +40,15 @@ class Opts(ctypes.Structure):
                 ("nroots_sa", ctypes.c_int), ("nroots_solve", ctypes.c_int),
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("max_subspace", ctypes.c_int),
-                ("res_tol", ctypes.c_double), ("e_tol", ctypes.c_double)]
+                ("res_tol", ctypes.c_double), ("e_tol", ctypes.c_double),
+                ("state_specific", ctypes.c_int)]
 
 
 def make_opts(t_pno=1e-7, t_osv=-1.0, nroots=3, nroots_solve=None, precision=FP64, refine_fp64=0,
-              max_iter=100, max_subspace=0, res_tol=1e-7, e_tol=1e-10):
+              max_iter=100, max_subspace=0, res_tol=1e-7, e_tol=1e-10, state_specific=0):
+    """pnoeom_opts.  state_specific = k >= 1: PNOs from CIS root k's density alone (1-based)."""
     return Opts(t_pno, t_osv, nroots, nroots if nroots_solve is None else nroots_solve,
-                precision, refine_fp64, max_iter, max_subspace, res_tol, e_tol)
+                precision, refine_fp64, max_iter, max_subspace, res_tol, e_tol, state_specific)
 
 
 _lib = None

@@ -210,6 +210,8 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
   PN_CHECK(o >= 1 && v >= 1 && naux >= 1, PNOEOM_ERR_INVALID_ARG, "o, v and naux must be positive");
   PN_CHECK(sys->eps && sys->B, PNOEOM_ERR_INVALID_ARG, "eps and B are required");
   PN_CHECK(opts->nroots_sa >= 1 && opts->nroots_sa <= o * v, PNOEOM_ERR_INVALID_ARG, "nroots_sa out of range");
+  PN_CHECK(opts->state_specific >= 0 && opts->state_specific <= opts->nroots_sa, PNOEOM_ERR_INVALID_ARG,
+           "state_specific must be 0 (state-averaged) or a CIS root in 1..nroots_sa");
   PN_CHECK(opts->t_pno >= 0, PNOEOM_ERR_INVALID_ARG, "t_pno must be >= 0");
   P->o = o; P->v = v; P->naux = naux; P->nroots_sa = opts->nroots_sa;
   P->t_pno = opts->t_pno;
@@ -346,6 +348,8 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
 
   tm.mark("CIS");
   // ---- CIS(D) doubles and state-averaged pair densities ------------------------
+  // (state_specific = k: the density of CIS root k alone, weight 1)
+  const int ss = opts->state_specific;
   const int npairs = o * (o + 1) / 2;
   P->npairs = npairs;
   P->pidx.assign(o, std::vector<int>(o, -1));
@@ -356,6 +360,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
   {
     DV b(ov), Z((size_t)N * ov), K(t2.n), Bt(t2.n);
     for (int k = 0; k < nr; ++k) {
+      if (ss > 0 && k != ss - 1) continue;
       b.upload(&bcis[(size_t)k * ov], ov, s);
       bd.con("ic", b.get(), "Qac", Bvv.get(), "Qia", Z.get());
       bd.con("Qia", Z.get(), "Qbj", Bvo.get(), "ijab", K.get(), 1.0, 0.0);
@@ -372,7 +377,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
         std::vector<GemmProb<double>> pr;
         for (int p = 0; p < npairs; ++p) {
           int i = P->pair_i[p], j = P->pair_j[p];
-          double c = (2.0 / (1.0 + (i == j))) / nr;
+          double c = (2.0 / (1.0 + (i == j))) / (ss > 0 ? 1 : nr);
           const double* Bij = K.get() + ((int64_t)i * o + j) * V * V;
           const double* Tij = Bt.get() + ((int64_t)i * o + j) * V * V;
           double* Dp = Dens.get() + (int64_t)p * V * V;

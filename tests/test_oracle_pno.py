@@ -159,3 +159,21 @@ def test_truncation_counts_and_threshold_rule():
         n = sp.alleig[key]
         assert sp.n_ij[p] == int(np.sum(n >= 1e-7))
     assert sp.length == sp.n_i.sum() + (sp.n_ij ** 2).sum()
+
+
+def test_state_average_is_mean_of_state_specific_densities():
+    """Eq. eom:sa_density is the mean of the one-state densities: a wrong root index or
+    weight in the state-specific construction breaks the identity."""
+    eps, B, _ = _small(o=3, v=6, naux=18, seed=47)
+    o, nr = 3, 3
+    Dsa, om, bs = pno.sa_densities(eps, B, o, nr)
+    Dss = [pno.ss_densities(eps, B, o, k, nr, om, bs)[0] for k in range(nr)]
+    for key, D in Dsa.items():
+        mean = sum(Dk[key] for Dk in Dss) / nr
+        assert np.abs(mean - D).max() <= 1e-14 * max(1.0, np.abs(D).max())
+    # the states differ, so the one-state densities do too
+    assert max(np.abs(Dss[0][k] - Dss[1][k]).max() for k in Dsa) > 1e-6
+    # one-state densities keep the pair-density invariants (symmetric, PSD)
+    for key, D in Dss[1].items():
+        assert np.abs(D - D.T).max() < 1e-14 * max(1.0, np.abs(D).max())
+        assert np.linalg.eigvalsh(D).min() > -1e-12 * max(1.0, np.trace(D))
