@@ -11,7 +11,9 @@ Paper passages followed:
   - b^l_a (li|bj) - b^l_b (ai|lj) (G^{pq}_{rs} read as (rp|sq)).  A
   denominator of magnitude below 1e-4 Eh is replaced by +-1e-4 Eh.
 * pair density D^{ij}_(k) = 2/(1+delta_ij) (B B~^T + B^T B~), B~ = 2B - B^T,
-  and its state average D^{ij} = (1/N) sum_k D^{ij}_(k) (Eq. eom:sa_density).
+  and its state average D^{ij} = (1/N) sum_k D^{ij}_(k) (Eq. eom:sa_density);
+  the one-state density D^{ij}_(k) alone gives the state-specific PNOs that the
+  average replaces (Sec. 2).
 * PNOs: eigenvectors of D^{ij} with occupation >= T_CutPNO (all of them when
   T_CutPNO = 0); OSVs of occupied i: the same for D^{ii} at T_CutOSV =
   T_CutPNO / 10 (Sec. 3); both semicanonicalised by diagonalising the
