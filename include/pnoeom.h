@@ -85,7 +85,13 @@ typedef struct {
  * PNOs/OSVs; k in 1..nroots_sa builds them from the CIS(D) pair densities of CIS
  * root k alone (1-based), the state-specific construction the paper compares
  * against (Sec. 2: one PNO space per state); the Davidson solve is unchanged, so
- * root k is energies[k - 1] with nroots_solve >= k. */
+ * root k is energies[k - 1] with nroots_solve >= k.
+ * t_pno_gs: 0 (default) leaves the ground-state amplitudes as given; > 0 truncates
+ * them to ground-state PNOs: each T^{ij} is projected onto the eigenvectors of its
+ * pair density D_(0)^{ij} = 2/(1+delta_ij) (T T~^T + T^T T~), T~ = 2T - T^T, with
+ * occupation >= t_pno_gs (Methods, ground-state PNOs from the guess amplitudes).
+ * Only T2 is truncated (T1 and a PNO-CCSD re-solution in the truncated spaces are
+ * not), which is exact for the MP1 amplitudes used when t2 is NULL. */
 typedef struct {
   double t_pno, t_osv;
   int nroots_sa, nroots_solve;
@@ -94,6 +100,7 @@ typedef struct {
   int max_iter, max_subspace;
   double res_tol, e_tol;
   int state_specific;
+  double t_pno_gs;
 } pnoeom_opts;
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no

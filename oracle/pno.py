@@ -14,6 +14,8 @@ Paper passages followed:
   and its state average D^{ij} = (1/N) sum_k D^{ij}_(k) (Eq. eom:sa_density);
   the one-state density D^{ij}_(k) alone gives the state-specific PNOs that the
   average replaces (Sec. 2).
+* ground-state PNOs: the same density form built from the amplitudes T^{ij}
+  (Methods, D_(0)); truncation projects each T^{ij} onto the kept ones.
 * PNOs: eigenvectors of D^{ij} with occupation >= T_CutPNO (all of them when
   T_CutPNO = 0); OSVs of occupied i: the same for D^{ii} at T_CutOSV =
   T_CutPNO / 10 (Sec. 3); both semicanonicalised by diagonalising the
@@ -116,6 +118,24 @@ def _truncate_semicanonical(Dm, thresh, fvv):
         if U[m, c] < 0:
             U[:, c] = -U[:, c]
     return U, fbar, occ, n
+
+
+def gs_truncate_t2(t2, o, t_gs):
+    """Ground-state PNO truncation of T2 (Methods): for each pair i <= j the ground-state
+    pair density D_(0)^{ij} = 2/(1+delta_ij) (T T~^T + T^T T~), T~ = 2T - T^T, is
+    diagonalised; P^{ij} projects onto its eigenvectors with occupation >= t_gs (all of
+    them when t_gs = 0), and T^{ij} -> P T^{ij} P, T^{ji} -> P T^{ji} P."""
+    out = np.array(t2, copy=True)
+    for i in range(o):
+        for j in range(i, o):
+            D = pair_density(t2[i, j], i, j)
+            w, U = np.linalg.eigh(D)
+            Uk = U if t_gs == 0 else U[:, w >= t_gs]
+            P = Uk @ Uk.T
+            out[i, j] = P @ t2[i, j] @ P
+            if i != j:
+                out[j, i] = P @ t2[j, i] @ P
+    return out
 
 
 def ss_densities(eps, B, o, root, nroots, omegas=None, bs=None):

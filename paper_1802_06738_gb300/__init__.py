@@ -41,14 +41,15 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int), ("refine_fp64", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("max_subspace", ctypes.c_int),
                 ("res_tol", ctypes.c_double), ("e_tol", ctypes.c_double),
-                ("state_specific", ctypes.c_int)]
+                ("state_specific", ctypes.c_int), ("t_pno_gs", ctypes.c_double)]
 
 
 def make_opts(t_pno=1e-7, t_osv=-1.0, nroots=3, nroots_solve=None, precision=FP64, refine_fp64=0,
-              max_iter=100, max_subspace=0, res_tol=1e-7, e_tol=1e-10, state_specific=0):
-    """pnoeom_opts.  state_specific = k >= 1: PNOs from CIS root k's density alone (1-based)."""
+              max_iter=100, max_subspace=0, res_tol=1e-7, e_tol=1e-10, state_specific=0, t_pno_gs=0.0):
+    """pnoeom_opts.  state_specific = k >= 1: PNOs from CIS root k's density alone (1-based);
+    t_pno_gs > 0: T2 truncated to ground-state PNOs at that threshold."""
     return Opts(t_pno, t_osv, nroots, nroots if nroots_solve is None else nroots_solve,
-                precision, refine_fp64, max_iter, max_subspace, res_tol, e_tol, state_specific)
+                precision, refine_fp64, max_iter, max_subspace, res_tol, e_tol, state_specific, t_pno_gs)
 
 
 _lib = None

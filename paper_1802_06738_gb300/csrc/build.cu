@@ -210,6 +210,7 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
   PN_CHECK(o >= 1 && v >= 1 && naux >= 1, PNOEOM_ERR_INVALID_ARG, "o, v and naux must be positive");
   PN_CHECK(sys->eps && sys->B, PNOEOM_ERR_INVALID_ARG, "eps and B are required");
   PN_CHECK(opts->nroots_sa >= 1 && opts->nroots_sa <= o * v, PNOEOM_ERR_INVALID_ARG, "nroots_sa out of range");
+  PN_CHECK(opts->t_pno_gs >= 0.0, PNOEOM_ERR_INVALID_ARG, "t_pno_gs must be >= 0");
   PN_CHECK(opts->state_specific >= 0 && opts->state_specific <= opts->nroots_sa, PNOEOM_ERR_INVALID_ARG,
            "state_specific must be 0 (state-averaged) or a CIS root in 1..nroots_sa");
   PN_CHECK(opts->t_pno >= 0, PNOEOM_ERR_INVALID_ARG, "t_pno must be >= 0");
@@ -314,6 +315,64 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     bd.con("Qai", Bvo.get(), "Qbj", Bvo.get(), "ijab", t2.get());
     k_pair_div<<<gsz(t2.n), 256, 0, s>>>(t2.get(), deps.get(), o, v, 0.0, 0.0);
     PN_CUDA(cudaGetLastError());
+  }
+  if (opts->t_pno_gs > 0.0) {
+    // ground-state PNO truncation (Methods): per pair i <= j, D_(0) = 2/(1+d_ij)(T Tt^T + T^T Tt)
+    // with Tt = 2T - T^T, eigenvectors of occupation >= t_pno_gs span the pair's space, and
+    // T^{ij}, T^{ji} are replaced by P T P with P the projector onto it
+    const int npr = o * (o + 1) / 2;
+    std::vector<int> pi, pj;
+    std::vector<std::vector<int>> pid(o, std::vector<int>(o, 0));
+    for (int i = 0; i < o; ++i)
+      for (int j = i; j < o; ++j) { pid[i][j] = pid[j][i] = (int)pi.size(); pi.push_back(i); pj.push_back(j); }
+    DV D0((size_t)npr * V * V);
+    D0.zero(s);
+    {
+      DV Tt(t2.n);
+      bd.perm(t2.get(), Tt.get(), {O, O, V, V}, {0, 1, 3, 2}, -1.0, 0.0);
+      axpby<double>(Tt.get(), t2.get(), 2.0, 1.0, Tt.n, s);
+      for (int half = 0; half < 2; ++half) {   // two launches: one output tile per launch
+        std::vector<GemmProb<double>> pr;
+        for (int p = 0; p < npr; ++p) {
+          const int i = pi[p], j = pj[p];
+          const double c = 2.0 / (1.0 + (i == j));
+          const double* T = t2.get() + ((int64_t)i * o + j) * V * V;
+          const double* Tx = Tt.get() + ((int64_t)i * o + j) * V * V;
+          double* Dp = D0.get() + (int64_t)p * V * V;
+          if (half == 0) pr.push_back({T, Tx, Dp, v, v, v, v, v, v, 0, 1, c, 1.0});
+          else pr.push_back({T, Tx, Dp, v, v, v, v, v, v, 1, 0, c, 1.0});
+        }
+        grouped_gemm<double>(pr, s);
+      }
+    }
+    std::vector<double> w0((size_t)npr * v);
+    {
+      DV W0((size_t)npr * V);
+      eig_dense_sym(ctx->solver, s, D0.get(), W0.get(), v, npr);   // ascending; column-major vectors
+      W0.download(w0.data(), w0.size(), s);
+      bd.sync();
+    }
+    DV Pj((size_t)npr * V * V), tmp(t2.n);
+    Pj.zero(s);
+    std::vector<GemmProb<double>> pp, p1, p2;
+    for (int p = 0; p < npr; ++p) {
+      int n = 0;
+      for (int a = 0; a < v; ++a) n += w0[(size_t)p * v + a] >= opts->t_pno_gs;
+      if (!n) continue;   // empty space: P = 0
+      const double* Uk = D0.get() + (int64_t)p * V * V + (int64_t)(v - n) * v;   // kept eigenvectors (rows)
+      pp.push_back({Uk, Uk, Pj.get() + (int64_t)p * V * V, v, v, n, v, v, v, 1, 0, 1.0, 0.0});
+    }
+    grouped_gemm<double>(pp, s);
+    for (int i = 0; i < o; ++i)
+      for (int j = 0; j < o; ++j) {
+        const double* Pp = Pj.get() + (int64_t)pid[i][j] * V * V;
+        double* T = t2.get() + ((int64_t)i * o + j) * V * V;
+        double* X = tmp.get() + ((int64_t)i * o + j) * V * V;
+        p1.push_back({T, Pp, X, v, v, v, v, v, v, 0, 0, 1.0, 0.0});
+        p2.push_back({Pp, X, T, v, v, v, v, v, v, 0, 0, 1.0, 0.0});
+      }
+    grouped_gemm<double>(p1, s);
+    grouped_gemm<double>(p2, s);
   }
   DV u2(t2.n);   // u = 2 t - t^(ab swapped)
   bd.perm(t2.get(), u2.get(), {O, O, V, V}, {0, 1, 3, 2}, -1.0, 0.0);

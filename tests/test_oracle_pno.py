@@ -177,3 +177,26 @@ def test_state_average_is_mean_of_state_specific_densities():
     for key, D in Dss[1].items():
         assert np.abs(D - D.T).max() < 1e-14 * max(1.0, np.abs(D).max())
         assert np.linalg.eigvalsh(D).min() > -1e-12 * max(1.0, np.trace(D))
+
+
+def test_ground_state_pno_truncation_of_t2():
+    """T -> P T P with P from the ground-state pair density (Methods): threshold 0 is the
+    identity, the result lies in the kept spaces on both sides, T^{ji} = T^{ij T} holds,
+    and a tighter threshold keeps more (monotone discarded norm)."""
+    o, v, naux = 3, 8, 24
+    s = make_system(o, v, naux, 48)
+    t2 = ccsd.mp1_t2(s["eps"], s["B"], o)
+    assert np.abs(pno.gs_truncate_t2(t2, o, 0.0) - t2).max() < 1e-13 * np.abs(t2).max()
+    errs = []
+    for thr in (1e-3, 1e-5, 1e-7):
+        tt = pno.gs_truncate_t2(t2, o, thr)
+        for i in range(o):
+            for j in range(o):
+                assert np.abs(tt[j, i] - tt[i, j].T).max() < 1e-14
+        for i in range(o):
+            for j in range(i, o):
+                w, U = np.linalg.eigh(pno.pair_density(t2[i, j], i, j))
+                Q = U[:, w < thr]                       # discarded directions
+                assert np.abs(Q.T @ tt[i, j]).max() < 1e-12 and np.abs(tt[i, j] @ Q).max() < 1e-12
+        errs.append(np.linalg.norm(tt - t2))
+    assert errs[0] >= errs[1] >= errs[2] and errs[0] > 0
