@@ -37,6 +37,8 @@ static void run_small_set(const SmallSet& S, int c, int rr, const SysTable& t, c
                         RPC_CAND[rr], S.pb, S.nb, S.shape, s);
 }
 
+constexpr int TUNE_REPS = 5;   // separately timed launches per candidate, after one warm-up launch
+
 // Time every small-sandwich set of the program alone for every (group size, vectors
 // per CTA) candidate (CUDA events on s) and keep each set's fastest.  sum_ms[c] is the
 // summed time of all sets under candidate c; the program's reported choice is the
@@ -47,6 +49,22 @@ static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* 
   PN_CUDA(cudaEventCreate(&e0));
   PN_CUDA(cudaEventCreate(&e1));
   for (int c = 0; c < NTUNE; ++c) sum_ms[c] = 0;
+  // ms of the fastest of TUNE_REPS timed launches after one warm-up (interference only
+  // adds time, so the minimum is the steadiest estimate)
+  auto measure = [&](SmallSet& S, int c, int rr) {
+    run_small_set<T>(S, c, rr, t, s);
+    double best = 1e300;
+    for (int q = 0; q < TUNE_REPS; ++q) {
+      PN_CUDA(cudaEventRecord(e0, s));
+      run_small_set<T>(S, c, rr, t, s);
+      PN_CUDA(cudaEventRecord(e1, s));
+      PN_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      best = std::min(best, (double)ms);
+    }
+    return best;
+  };
   for (SmallSet* sets : {prog.small1, prog.small2})
     for (int k = 0; k < 3; ++k) {
       SmallSet& S = sets[k];
@@ -57,46 +75,23 @@ static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* 
       S.shape = 0;   // batch size are chosen afterwards
       for (int c = 0; c < NGROUP_CAND; ++c)
         for (int rr = 0; rr < NRPC_CAND; ++rr) {
-          run_small_set<T>(S, c, rr, t, s);   // warm-up
-          PN_CUDA(cudaEventRecord(e0, s));
-          for (int q = 0; q < 3; ++q) run_small_set<T>(S, c, rr, t, s);
-          PN_CUDA(cudaEventRecord(e1, s));
-          PN_CUDA(cudaEventSynchronize(e1));
-          float ms = 0;
-          PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          const double ms = measure(S, c, rr);
           const int idx = c * NRPC_CAND + rr;
-          S.tune_ms[idx] = ms / 3;
-          sum_ms[idx] += ms / 3;
+          S.tune_ms[idx] = ms;
+          sum_ms[idx] += ms;
           if (ms < best) { best = ms; S.gchoice = c; S.rchoice = rr; }
         }
-      // then the number of problems staged together, for the chosen (group, vectors per CTA)
-      auto time_set = [&]() {
-        run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
-        PN_CUDA(cudaEventRecord(e0, s));
-        for (int q = 0; q < 3; ++q) run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
-        PN_CUDA(cudaEventRecord(e1, s));
-        PN_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        return (double)ms;
-      };
       int best_shape = 0;
       for (int shc : {1, 2, 3}) {
         S.shape = shc;
-        const double ms = time_set();
+        const double ms = measure(S, S.gchoice, S.rchoice);
         if (ms < best) { best = ms; best_shape = shc; }
       }
       S.shape = best_shape;
       int best_nb = 0;
       for (int nbc : {1, 2}) {
         S.nb = nbc;
-        run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
-        PN_CUDA(cudaEventRecord(e0, s));
-        for (int q = 0; q < 3; ++q) run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
-        PN_CUDA(cudaEventRecord(e1, s));
-        PN_CUDA(cudaEventSynchronize(e1));
-        float ms = 0;
-        PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        const double ms = measure(S, S.gchoice, S.rchoice);
         if (ms < best) { best = ms; best_nb = nbc; }
       }
       S.nb = best_nb;
@@ -104,13 +99,7 @@ static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* 
       if (S.ab)
         for (int pbc : {2, 4}) {
           S.pb = pbc;
-          run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
-          PN_CUDA(cudaEventRecord(e0, s));
-          for (int q = 0; q < 3; ++q) run_small_set<T>(S, S.gchoice, S.rchoice, t, s);
-          PN_CUDA(cudaEventRecord(e1, s));
-          PN_CUDA(cudaEventSynchronize(e1));
-          float ms = 0;
-          PN_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          const double ms = measure(S, S.gchoice, S.rchoice);
           if (ms < best) { best = ms; best_pb = pbc; }
         }
       S.pb = best_pb;
