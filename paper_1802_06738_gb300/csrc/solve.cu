@@ -203,6 +203,21 @@ void autotune(pnoeom_pno* P, cudaStream_t s) {
   t.max_nvec = nv;
   t.s[0] = sysbuf(P, nv, r.get(), o.get(), work.get(), true);
   tune_sets<float>(P->prog, t, s, P->tune_ms);
+  // diagnostic overrides of the tuned small-kernel variants (tests force each variant):
+  // PNOEOM_SMALL_PB (2 or 4, sets whose problems all have A and B), PNOEOM_SMALL_SHAPE
+  // (1..3), PNOEOM_SMALL_NB (1 or 2)
+  auto env_int = [](const char* name) {
+    const char* e = std::getenv(name);
+    return e ? std::atoi(e) : -1;
+  };
+  const int fpb = env_int("PNOEOM_SMALL_PB"), fsh = env_int("PNOEOM_SMALL_SHAPE"), fnb = env_int("PNOEOM_SMALL_NB");
+  for (SmallSet* sets : {P->prog.small1, P->prog.small2})
+    for (int k = 0; k < 3; ++k) {
+      SmallSet& S = sets[k];
+      if (fpb >= 1 && fpb <= 4) S.pb = S.ab ? fpb : 1;
+      if (fsh >= 0 && fsh <= 3) S.shape = fsh;
+      if (fnb >= 0 && fnb <= 2) S.nb = fnb;
+    }
 }
 
 // ---------------------------------------------------------------------------
