@@ -40,7 +40,7 @@ METRIC = "PNO-EOM-CCSD sigma-evals/s (mixed FP32 sigma, FP64 setup/orthogonalisa
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="medium", choices=list(WORKLOADS))
@@ -85,26 +85,51 @@ def max_over_ranks(x, ws, device):
 
 
 class Clocks:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling (every 50 ms, each line time-stamped on
+    arrival by a reader thread).  Start it before the warm-up so the first samples exist
+    when the timed region begins; mark() the region, and summary() keeps the samples
+    inside it (or, for a region shorter than the sampling period, the nearest ones)."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.rows = []                 # (arrival time, csv fields)
+        self.window = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
 
+    def _read(self):
+        import time as _t
+        with open(self.path, "w") as f:
+            for line in self.proc.stdout:
+                f.write(line)
+                self.rows.append((_t.time(), [x.strip() for x in line.strip().split(",")]))
+
     def __enter__(self):
+        import threading
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
         except Exception:
             self.proc = None
         return self
+
+    def wait_first(self, limit_s=5.0):
+        """Block (at most limit_s) until the sampler has produced its first line."""
+        import time as _t
+        t_end = _t.time() + limit_s
+        while self.proc is not None and not self.rows and _t.time() < t_end:
+            _t.sleep(0.01)
+        return self
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -113,15 +138,24 @@ class Clocks:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-            self.f.close()
+            self.thread.join(timeout=5)
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
+        if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        rows = list(self.rows)
+        inside = rows
+        where = "timed region"
+        if self.window is not None:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if not inside and rows:   # region shorter than the sampling period: nearest samples
+                rows.sort(key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))
+                inside = rows[:2]
+                where = "nearest to the timed region"
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        for _, r in inside:
             try:
                 sm.append(float(r[1])); smax = float(r[2])
                 for nm, val in zip(names, r[5:9]):
@@ -131,7 +165,7 @@ class Clocks:
                 pass
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "window": where}
 
 
 def oracle_setup(w):
@@ -256,18 +290,20 @@ def run_batched(args, ws, rank, local):
     rng = np.random.default_rng(3)
     rs = [torch.tensor(rng.standard_normal((nr, p.length)), dtype=torch.float32, device=dev) for p in pnos]
     outs = [torch.empty_like(r) for r in rs]
-    with torch.cuda.stream(stream):
+    with torch.cuda.stream(stream), Clocks(local) as clk:
+        clk.wait_first()
         for _ in range(args.warmup):
             batch.sigma(rs, outs, precision=pkg.FP32, stream=h)
         stream.synchronize()
         barrier(ws)
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
-        with Clocks(local) as clk:
-            ev0.record(stream)
-            for _ in range(args.steps):
-                batch.sigma(rs, outs, precision=pkg.FP32, stream=h)
-            ev1.record(stream)
-            stream.synchronize()
+        tw0 = time.time()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            batch.sigma(rs, outs, precision=pkg.FP32, stream=h)
+        ev1.record(stream)
+        stream.synchronize()
+        clk.mark(tw0, time.time())
     t_sig = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
     # lockstep batched solve (mixed + FP64 refinement) vs the same systems one after another
     t0 = time.perf_counter()
@@ -312,6 +348,8 @@ def run_serving(args, ws, rank, local):
     srv = pkg.Server(ctx, hbm_budget_bytes=200 << 30, max_active=32)
     barrier(ws)
     with Clocks(local) as clk:
+        clk.wait_first()
+        tw0 = time.time()
         t0 = time.perf_counter()
         ids = []
         for k, r in enumerate(reqs):
@@ -323,6 +361,7 @@ def run_serving(args, ws, rank, local):
         for rid in ids:
             srv.wait(rid, 3600.0)
         wall = time.perf_counter() - t0
+        clk.mark(tw0, time.time())
     res = [srv.poll(rid) for rid in ids]
     st = srv.stats()
     srv.close()
@@ -400,19 +439,22 @@ def main():
     R32 = R64.float()
     S32 = torch.empty_like(R32)
     S64 = torch.empty_like(R64)
-    for _ in range(args.warmup):
-        gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
-    gp.set_timing(True)
-    barrier(ws)
-    torch.cuda.synchronize()
     with Clocks(local) as clk:
+        clk.wait_first()
+        for _ in range(args.warmup):
+            gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
+        gp.set_timing(True)
+        barrier(ws)
+        torch.cuda.synchronize()
         ev0 = torch.cuda.Event(enable_timing=True); ev1 = torch.cuda.Event(enable_timing=True)
         nvtx_push("sigma_timed")   # lets a profiler select exactly the timed launches
+        tw0 = time.time()
         ev0.record()
         for _ in range(args.steps):
             gp.sigma(R32, S32, precision=pkg.FP32, stream=stream)
         ev1.record()
         torch.cuda.synchronize()
+        clk.mark(tw0, time.time())
         nvtx_pop()
     barrier(ws)
     t_mixed = ev0.elapsed_time(ev1) / 1e3
