@@ -221,6 +221,20 @@ def roofline(dom, steps, peaks, clk):
     return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src, **common}
 
 
+def ncu_traffic(cls):
+    """DRAM bytes per sigma call of kernel class `cls` from the committed ncu summary
+    (a line "traffic per call (bytes): <class> = <bytes>"), or None."""
+    import re
+    f = os.path.join(ROOT, "profiles", "sandwich_sigma_traffic_medium.md")
+    if not os.path.exists(f):
+        return None
+    for line in open(f):
+        m = re.match(r"traffic per call \(bytes\): (\S+) = (\d+)", line.strip())
+        if m and m.group(1) == cls:
+            return float(m.group(2))
+    return None
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -506,11 +520,10 @@ def main():
     dom = max(prof, key=lambda d: d["ms"])
     clocks = clk.summary()
     roof = roofline(dom, args.steps, peaks, clocks)
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        traffic = json.load(open(tf)).get(dom["name"])
-    roof["traffic"] = traffic
+    roof["traffic"] = ncu_traffic(dom["name"]) if args.workload == "medium" else None
+    if roof["traffic"] is not None:
+        roof["traffic_per"] = f"call ({roof['launches_per_call']:.0f} launches), ncu dram__bytes_read.sum + dram__bytes_write.sum"
+        roof["traffic_over_algorithmic"] = roof["traffic"] / max(dom["bytes"], 1.0)
     cpu = None
     if not args.no_cpu_baseline and args.gpus == 1:
         t0 = time.time()
