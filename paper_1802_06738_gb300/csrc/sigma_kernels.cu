@@ -115,6 +115,71 @@ __device__ __forceinline__ void cp_async_el(T* dst, const T* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 
+// Element stride between the per-vector copies of a buffer (0 for the shared pool).
+__device__ __forceinline__ int64_t cvstride(const SysTable& t, int sys, int id) {
+  const SysBuf& b = t.s[sys];
+  switch (id) {
+    case B_POOL: return 0;
+    case B_RIN: return b.rin_stride;
+    case B_WORK: return b.work_stride;
+    default: return b.sout_stride;
+  }
+}
+
+// Staging of nv blocks of R x Cn elements into shared memory with cp.async: element
+// (v, r, c) is read at src[v * vs + r * rs + c * cs] and written to dst[v * dvs + r * dld + c].
+// Thread t keeps column c = t % Cn and walks rows t / Cn, t / Cn + NT / Cn, ... of the nv
+// blocks stacked, so the stores of a warp fall on consecutive words of shared memory (no
+// bank conflicts between rows) and, where cs == 1, its loads on consecutive words of the
+// source.  Needs 0 < Cn <= NT.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_block(T* dst, int dvs, int dld, const T* src, int64_t vs, int rs, int cs,
+                                            int nv, int R, int Cn, int tid) {
+  if (R <= 0 || Cn <= 0) return;
+  const int rstep = NT / Cn;
+  const int rr = tid / Cn;
+  if (rr >= rstep) return;   // the NT % Cn threads left over
+  const int c = tid - rr * Cn;
+  const int dv = rstep / R, dr = rstep - dv * R;
+  int v = rr / R, r = rr - v * R;
+  while (v < nv) {
+    cp_async_el(dst + v * dvs + r * dld + c, src + v * vs + (r * rs + c * cs));
+    r += dr;
+    v += dv;
+    if (r >= R) {
+      r -= R;
+      ++v;
+    }
+  }
+}
+
+// X_eff = opX(X) + xb opX(X)^T of nv square K x K blocks (element (a, b) of X_v at
+// src[v * vs + a * ldx + b]), merged in registers: dst[v * dvs + b * dld + a] =
+// opX(X_v)[a][b] + xb opX(X_v)[b][a], with opX(X)[a][b] = X[b][a] when tx.  Thread mapping
+// as in stage_block, a fastest.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_xeff_block(T* dst, int dvs, int dld, const T* src, int64_t vs, int ldx, bool tx,
+                                                 T xb, int nv, int K, int tid) {
+  if (K <= 0) return;
+  const int rstep = NT / K;
+  const int rr = tid / K;
+  if (rr >= rstep) return;
+  const int a = tid - rr * K;
+  const int dv = rstep / K, dr = rstep - dv * K;
+  int v = rr / K, b = rr - v * K;
+  while (v < nv) {
+    const T* X = src + v * vs;
+    const T xba = X[b * ldx + a], xab = X[a * ldx + b];   // X[b][a], X[a][b]
+    dst[v * dvs + b * dld + a] = tx ? xba + xb * xab : xab + xb * xba;
+    b += dr;
+    v += dv;
+    if (b >= K) {
+      b -= K;
+      ++v;
+    }
+  }
+}
+
 // Grouped small sandwich (see run_sandwich_small).  Shared memory, with the set's
 // bounds dm, dk1 (rows of the staged X block), dk2 (its columns), dn padded to 4,
 // and NB copies (NB = 2: problem g and g + 1; NB = 1: one) of the staged operands:
@@ -171,8 +236,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 6 : (MAXT ==
 #pragma unroll
       for (int b = 0; b < 4; ++b) acc[j][a][b] = T(0);
   }
-  // Row-wise staging: each work item copies one contiguous source row with incrementing
-  // pointers.  A, B and (when xb == 0) X go through cp.async; X with xb != 0 is merged in
+  // Staging (stage_block): A, B and (when xb == 0) X go through cp.async, every thread
+  // taking elements of consecutive destination columns; X with xb != 0 is merged in
   // registers by stage_xeff.
   auto issue = [&](const SProb& P, int buf) {
     T* As = S0 + buf * stage;
@@ -182,73 +247,34 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 6 : (MAXT ==
     const int K1 = P.K1;
     const int kr = hasA ? K1 : Mt, kc = hasB ? P.K2 : Nt;
     const int xr0 = hasA ? 0 : P.m0, xc0 = hasB ? 0 : P.n0;
-    if (hasA) {
+    if (hasA) {   // As[k][m] = opA(A)[m0 + m][k]; A stored K1 x M (ta) or M x K1
       const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
-      if (P.ta) {   // stored K1 x M: row k of the store -> row k of As
-        for (int k = tid; k < K1; k += NT) {
-          const T* src = A + (int64_t)k * P.lda + P.m0;
-          T* dst = As + k * Mp;
-          for (int m = 0; m < Mt; ++m) cp_async_el(dst + m, src + m);
-        }
-      } else {      // row m of A -> column m of As
-        for (int m = tid; m < Mt; m += NT) {
-          const T* src = A + (int64_t)(P.m0 + m) * P.lda;
-          T* dst = As + m;
-          for (int k = 0; k < K1; ++k) cp_async_el(dst + k * Mp, src + k);
-        }
-      }
+      if (P.ta)
+        stage_block<T, NT>(As, 0, Mp, A + P.m0, 0, P.lda, 1, 1, K1, Mt, tid);
+      else
+        stage_block<T, NT>(As, 0, Mp, A + (int64_t)P.m0 * P.lda, 0, 1, P.lda, 1, K1, Mt, tid);
     }
-    if (hasB) {
+    if (hasB) {   // Bs[k][n] = opB(B)[k][n0 + n]; B stored N x K2 (tb) or K2 x N
       const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, 0) + P.b_off;
-      const int K2 = P.K2;
-      if (P.tb) {   // stored N x K2: row n -> column n of Bs
-        for (int n = tid; n < Nt; n += NT) {
-          const T* src = Bm + (int64_t)(P.n0 + n) * P.ldb;
-          T* dst = Bs + n;
-          for (int k = 0; k < K2; ++k) cp_async_el(dst + k * Np, src + k);
-        }
-      } else {      // row k -> row k of Bs
-        for (int k = tid; k < K2; k += NT) {
-          const T* src = Bm + (int64_t)k * P.ldb + P.n0;
-          T* dst = Bs + k * Np;
-          for (int n = 0; n < Nt; ++n) cp_async_el(dst + n, src + n);
-        }
-      }
+      if (P.tb)
+        stage_block<T, NT>(Bs, 0, Np, Bm + (int64_t)P.n0 * P.ldb, 0, 1, P.ldb, 1, P.K2, Nt, tid);
+      else
+        stage_block<T, NT>(Bs, 0, Np, Bm + P.n0, 0, P.ldb, 1, 1, P.K2, Nt, tid);
     }
-    if (P.xb == 0.0) {   // opX(X)[xr0 + a][xc0 + b] -> Xs[b][r K1p + a]
-      if (P.tx) {   // opX(X)[a][b] = X[b][a]: row xc0 + b of X -> row b of Xs
-        for (int it = tid; it < nr * kc; it += NT) {
-          const int r = it / kc, b = it - r * kc;
-          const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)(xc0 + b) * P.ldx + xr0;
-          T* dst = Xs + b * xld + r * K1p;
-          for (int a = 0; a < kr; ++a) cp_async_el(dst + a, src + a);
-        }
-      } else {      // opX(X)[a][b] = X[a][b]: row xr0 + a of X -> column a of Xs
-        for (int it = tid; it < nr * kr; it += NT) {
-          const int r = it / kr, a = it - r * kr;
-          const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)(xr0 + a) * P.ldx + xc0;
-          T* dst = Xs + r * K1p + a;
-          for (int b = 0; b < kc; ++b) cp_async_el(dst + b * xld, src + b);
-        }
-      }
+    if (P.xb == 0.0) {   // Xs[b][r K1p + a] = opX(X_r)[xr0 + a][xc0 + b]
+      const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase) + P.x_off;
+      const int64_t vs = cvstride(tab, P.sys, P.x_buf);
+      if (P.tx)   // opX(X)[a][b] = X[b][a]
+        stage_block<T, NT>(Xs, K1p, xld, X + (int64_t)xc0 * P.ldx + xr0, vs, P.ldx, 1, nr, kc, kr, tid);
+      else        // opX(X)[a][b] = X[a][b]
+        stage_block<T, NT>(Xs, K1p, xld, X + (int64_t)xr0 * P.ldx + xc0, vs, 1, P.ldx, nr, kc, kr, tid);
     }
     cp_async_commit();
   };
-  // X_eff = opX(X) + xb opX(X)^T of a square block (xr0 = xc0 = 0, kr = kc), merged in
-  // registers: item (vector, b) writes row b of Xs from row b and column b of X.
+  // X_eff = opX(X) + xb opX(X)^T of a square block (xr0 = xc0 = 0, kr = kc).
   auto stage_xeff = [&](const SProb& P, T* Xs, int K) {
-    const T xb = (T)P.xb;
-    for (int it = tid; it < nr * K; it += NT) {
-      const int r = it / K, b = it - r * K;
-      const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
-      const T* row = X + (int64_t)b * P.ldx;   // X[b][a], a = 0..K-1
-      const T* col = X + b;                    // X[a][b] at col + a * ldx
-      T* dst = Xs + b * xld + r * K1p;
-      if (P.tx)   // opX(X)[a][b] = X[b][a]
-        for (int a = 0; a < K; ++a) dst[a] = row[a] + xb * col[(int64_t)a * P.ldx];
-      else        // opX(X)[a][b] = X[a][b]
-        for (int a = 0; a < K; ++a) dst[a] = col[(int64_t)a * P.ldx] + xb * row[a];
-    }
+    stage_xeff_block<T, NT>(Xs, K1p, xld, cbuf<T>(tab, P.sys, P.x_buf, rbase) + P.x_off, cvstride(tab, P.sys, P.x_buf),
+                            P.ldx, P.tx != 0, (T)P.xb, nr, K, tid);
   };
   if (NB == 2) {
     __syncthreads();   // zero fill done before the first copies land
@@ -456,64 +482,30 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (NT == 128 ? 6 : (MAXT ==
       T* Xs = Xs0 + q * xsz;
       T* Bs = Bs0 + q * bsz;
       T* Aq = As + koff[q] * Mp;
-      {
+      {   // Aq[k][m] = opA(A)[m0 + m][k]
         const T* A = cbuf<T>(tab, P.sys, P.a_buf, 0) + P.a_off;
-        if (P.ta) {
-          for (int k = tid; k < K1; k += NT) {
-            const T* src = A + (int64_t)k * P.lda + P.m0;
-            for (int m = 0; m < Mt; ++m) cp_async_el(Aq + k * Mp + m, src + m);
-          }
-        } else {
-          for (int m = tid; m < Mt; m += NT) {
-            const T* src = A + (int64_t)(P.m0 + m) * P.lda;
-            for (int k = 0; k < K1; ++k) cp_async_el(Aq + k * Mp + m, src + k);
-          }
-        }
+        if (P.ta)
+          stage_block<T, NT>(Aq, 0, Mp, A + P.m0, 0, P.lda, 1, 1, K1, Mt, tid);
+        else
+          stage_block<T, NT>(Aq, 0, Mp, A + (int64_t)P.m0 * P.lda, 0, 1, P.lda, 1, K1, Mt, tid);
         for (int e = tid; e < (pad4(K1) - K1) * Mp; e += NT) Aq[K1 * Mp + e] = T(0);   // K padding rows
       }
-      {
+      {   // Bs[k][n] = opB(B)[k][n0 + n]
         const T* Bm = cbuf<T>(tab, P.sys, P.b_buf, 0) + P.b_off;
-        if (P.tb) {
-          for (int n = tid; n < Nt; n += NT) {
-            const T* src = Bm + (int64_t)(P.n0 + n) * P.ldb;
-            for (int k = 0; k < K2; ++k) cp_async_el(Bs + k * Np + n, src + k);
-          }
-        } else {
-          for (int k = tid; k < K2; k += NT) {
-            const T* src = Bm + (int64_t)k * P.ldb + P.n0;
-            for (int n = 0; n < Nt; ++n) cp_async_el(Bs + k * Np + n, src + n);
-          }
-        }
+        if (P.tb)
+          stage_block<T, NT>(Bs, 0, Np, Bm + (int64_t)P.n0 * P.ldb, 0, 1, P.ldb, 1, K2, Nt, tid);
+        else
+          stage_block<T, NT>(Bs, 0, Np, Bm + P.n0, 0, P.ldb, 1, 1, K2, Nt, tid);
       }
-      if (P.xb == 0.0) {
-        if (P.tx) {
-          for (int it = tid; it < nr * K2; it += NT) {
-            const int r = it / K2, b = it - r * K2;
-            const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)b * P.ldx;
-            T* dst = Xs + b * xld + r * K1p;
-            for (int a = 0; a < K1; ++a) cp_async_el(dst + a, src + a);
-          }
-        } else {
-          for (int it = tid; it < nr * K1; it += NT) {
-            const int r = it / K1, a = it - r * K1;
-            const T* src = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off + (int64_t)a * P.ldx;
-            T* dst = Xs + r * K1p + a;
-            for (int b = 0; b < K2; ++b) cp_async_el(dst + b * xld, src + b);
-          }
-        }
+      const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase) + P.x_off;
+      const int64_t vs = cvstride(tab, P.sys, P.x_buf);
+      if (P.xb == 0.0) {   // Xs[b][r K1p + a] = opX(X_r)[a][b]
+        if (P.tx)
+          stage_block<T, NT>(Xs, K1p, xld, X, vs, P.ldx, 1, nr, K2, K1, tid);
+        else
+          stage_block<T, NT>(Xs, K1p, xld, X, vs, 1, P.ldx, nr, K2, K1, tid);
       } else {   // square X: X_eff = opX(X) + xb opX(X)^T, merged in registers
-        const T xb = (T)P.xb;
-        for (int it = tid; it < nr * K1; it += NT) {
-          const int r = it / K1, b = it - r * K1;
-          const T* X = cbuf<T>(tab, P.sys, P.x_buf, rbase + r) + P.x_off;
-          const T* row = X + (int64_t)b * P.ldx;
-          const T* col = X + b;
-          T* dst = Xs + b * xld + r * K1p;
-          if (P.tx)
-            for (int a = 0; a < K1; ++a) dst[a] = row[a] + xb * col[(int64_t)a * P.ldx];
-          else
-            for (int a = 0; a < K1; ++a) dst[a] = col[(int64_t)a * P.ldx] + xb * row[a];
-        }
+        stage_xeff_block<T, NT>(Xs, K1p, xld, X, vs, P.ldx, P.tx != 0, (T)P.xb, nr, K1, tid);
       }
     }
     cp_async_commit();
