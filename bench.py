@@ -222,13 +222,21 @@ def roofline(dom, steps, peaks, clk):
 
 
 def ncu_traffic(cls):
-    """DRAM bytes per sigma call of kernel class `cls` from the committed ncu summary
-    (a line "traffic per call (bytes): <class> = <bytes>"), or None."""
+    """DRAM bytes per sigma call of kernel class `cls` from the committed ncu summary (a
+    line "traffic per call (bytes): <class> = <bytes>"), or None.  The summary records the
+    sha256 of the kernel source it was captured with ("kernel source sha256: <hex>"); once
+    that source has changed the counters no longer describe the kernel and None is returned."""
+    import hashlib
     import re
     f = os.path.join(ROOT, "profiles", "sandwich_sigma_traffic_medium.md")
-    if not os.path.exists(f):
+    src = os.path.join(ROOT, "paper_1802_06738_gb300", "csrc", "sigma_kernels.cu")
+    if not os.path.exists(f) or not os.path.exists(src):
         return None
-    for line in open(f):
+    text = open(f).read()
+    h = re.search(r"kernel source sha256: ([0-9a-f]{64})", text)
+    if h is None or h.group(1) != hashlib.sha256(open(src, "rb").read()).hexdigest():
+        return None
+    for line in text.splitlines():
         m = re.match(r"traffic per call \(bytes\): (\S+) = (\d+)", line.strip())
         if m and m.group(1) == cls:
             return float(m.group(2))
