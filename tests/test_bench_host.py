@@ -1,0 +1,59 @@
+"""Host-side logic of bench.py that needs no GPU: the clock summary keeps only the
+nvidia-smi samples inside the timed region and reads the throttle reasons, and the DRAM
+traffic figure is reported only while the kernel source matches the hash recorded with
+the ncu capture."""
+import hashlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _row(mhz, power_cap="Not Active", thermal="Not Active"):
+    return ["0", str(mhz), "2070", "900.0", "0x0", "Not Active", "Not Active", thermal, power_cap]
+
+
+def _clocks(rows, window):
+    c = bench.Clocks(0)
+    c.proc = object()   # a sampler that ran
+    c.rows = rows
+    c.window = window
+    return c
+
+
+def test_clock_summary_keeps_samples_inside_the_timed_region():
+    rows = [(0.0, _row(1200)), (1.0, _row(2070)), (1.5, _row(2055, power_cap="Active")), (3.0, _row(900))]
+    s = _clocks(rows, (0.9, 2.0)).summary()
+    assert s["samples"] == 2 and s["window"] == "timed region"
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_short_region_takes_the_nearest_samples():
+    rows = [(0.0, _row(1000)), (1.00, _row(2070, thermal="Active")), (1.10, _row(2070)), (5.0, _row(500))]
+    s = _clocks(rows, (1.02, 1.04)).summary()
+    assert s["window"] == "nearest to the timed region" and s["samples"] == 2
+    assert s["sm_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_sampler():
+    assert bench.Clocks(0).summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_traffic_reported_only_for_the_captured_kernel_source(tmp_path, monkeypatch):
+    src = tmp_path / "paper_1802_06738_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    kernel = src / "sigma_kernels.cu"
+    kernel.write_text("// kernel v1\n")
+    digest = hashlib.sha256(kernel.read_bytes()).hexdigest()
+    (tmp_path / "profiles" / "sandwich_sigma_traffic_medium.md").write_text(
+        f"traffic per call (bytes): sandwich->sigma = 1234\n\nkernel source sha256: {digest}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.ncu_traffic("sandwich->sigma") == 1234.0
+    assert bench.ncu_traffic("dense->sigma") is None
+    kernel.write_text("// kernel v2\n")
+    assert bench.ncu_traffic("sandwich->sigma") is None
