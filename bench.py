@@ -446,14 +446,17 @@ def main():
     lat_mixed, lat_fp64 = [], []
     e_mixed = e_fp64 = None
     it_mixed = it_fp64 = None
+    ev_mixed = ev_fp64 = {"fp32": 0, "fp64": 0}
     opts_fp64 = pkg.make_opts(t_pno=w["t_pno"], nroots=nr, precision=pkg.FP64)
     for k in range(args.solves):
         torch.cuda.synchronize(); t0 = time.perf_counter()
         e_mixed, rn, it_mixed, conv_m = gp.davidson_solve(opts_mixed, stream=stream)
         torch.cuda.synchronize(); lat_mixed.append(time.perf_counter() - t0)
+        ev_mixed = gp.solve_stats()
         t0 = time.perf_counter()
         e_fp64, rn64, it_fp64, conv_64 = gp.davidson_solve(opts_fp64, stream=stream)
         torch.cuda.synchronize(); lat_fp64.append(time.perf_counter() - t0)
+        ev_fp64 = gp.solve_stats()
 
     # --- timed sigma steps, operators resident in HBM
     rng = np.random.default_rng(1 + rank)
@@ -552,6 +555,12 @@ def main():
                   "abs_err_mixed_refined": [abs(a - b) for a, b in zip(e_mixed, gold["energies"])],
                   "abs_err_fp64": [abs(a - b) for a, b in zip(e_fp64, gold["energies"])]}
     lat = lambda xs: {"p50_s": float(np.percentile(xs, 50)), "p99_s": float(np.percentile(xs, 99)), "n": len(xs)}
+
+    def in_solve(ev, xs):   # sigma-evals of one whole solve (setup excluded) and their rate
+        n = ev["fp32"] + ev["fp64"]
+        return {"sigma_evals_fp32": ev["fp32"], "sigma_evals_fp64": ev["fp64"],
+                "sigma_evals_per_s": n / float(np.percentile(xs, 50))}
+    gflop_call = sum(d["flops"] for d in prof) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "sigma-evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
@@ -564,9 +573,13 @@ def main():
         "fp64_path": {"value": ws * nr * k64 / t_fp64, "unit": "sigma-evals/s", "steps": k64,
                       "ms_per_step": 1e3 * t_fp64 / k64},
         "mixed_vs_fp64_sigma_max_rel_err": sig_rel_err,
-        "solve": {"mixed_refined": {**lat(lat_mixed), "iterations": it_mixed, "energies": list(map(float, e_mixed))},
-                  "fp64": {**lat(lat_fp64), "iterations": it_fp64, "energies": list(map(float, e_fp64))},
+        "solve": {"mixed_refined": {**lat(lat_mixed), "iterations": it_mixed, **in_solve(ev_mixed, lat_mixed),
+                                    "energies": list(map(float, e_mixed))},
+                  "fp64": {**lat(lat_fp64), "iterations": it_fp64, **in_solve(ev_fp64, lat_fp64),
+                           "energies": list(map(float, e_fp64))},
                   "pno_build_s": build_s},
+        "flop_weighted": {"gflop_per_call": gflop_call, "tflops": gflop_call / (t_mixed / args.steps) / 1e3,
+                          "note": "algorithmic FLOPs of all sigma kernel classes per 6-root call / CUDA-event time"},
         "energy_check": golden,
         "e2e": {"value": ws * nr * args.steps / t_e2e, "unit": "sigma-evals/s",
                 "h2d_bytes_per_step": int(Rh.numel() * 4), "d2h_bytes_per_step": int(Sh.numel() * 4)},

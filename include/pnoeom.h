@@ -238,6 +238,12 @@ int pnoeom_server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int
  * vectors on the host (nroots_solve * vec_len doubles). */
 int pno_get_eigenvectors(const pnoeom_pno* pno, double* X);
 
+/* Sigma evaluations (one vector of one root each) of the last davidson_solve on
+ * this handle, split by the precision they ran in: FP32 (the mixed phase) and
+ * FP64 (a plain FP64 solve, or the refinement that follows the FP32 phase).
+ * Both 0 before the first solve.  Host-only; either pointer may be NULL. */
+int pno_solve_stats(const pnoeom_pno* pno, int64_t* sigma_evals_fp32, int64_t* sigma_evals_fp64);
+
 /* All eigenvalues (ascending) of every state-averaged pair density D^{ij}
  * (Eq. eom:sa_density): npairs x v doubles on the host, pair-major.  The PNO
  * occupation numbers whose truncation at T_CutPNO defines n_ij. */

@@ -59,7 +59,8 @@ EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", 
            "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info",
            "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve",
            "pnoeom_server_create", "pnoeom_server_destroy", "pnoeom_server_submit", "pnoeom_server_poll",
-           "pnoeom_server_wait", "pnoeom_server_stats", "pnoeom_gemm_tf32x3", "pnoeom_device_status"]
+           "pnoeom_server_wait", "pnoeom_server_stats", "pnoeom_gemm_tf32x3", "pnoeom_device_status",
+           "pno_solve_stats"]
 
 
 def lib():
@@ -93,6 +94,7 @@ def lib():
         L.pnoeom_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ip, ip, i64p, i64p, i64p]
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
+        L.pno_solve_stats.argtypes = [vp, i64p, i64p]
         L.pno_get_cis.argtypes = [vp, dp]
         L.pno_get_occupations.argtypes = [vp, dp]
         L.pno_get_cis_vectors.argtypes = [vp, dp]
@@ -288,6 +290,12 @@ class PNO:
                                           ctypes.byref(by), ctypes.byref(fl)))
             out.append(dict(name=nm.value.decode(), launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value))
         return out
+
+    def solve_stats(self):
+        """dict(fp32, fp64): sigma evaluations of the last davidson_solve, by precision."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().pno_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return dict(fp32=a.value, fp64=b.value)
 
     def eigenvectors(self):
         import numpy as np

@@ -299,6 +299,14 @@ int pno_get_eigenvectors(const pnoeom_pno* pno, double* X) {
   });
 }
 
+int pno_solve_stats(const pnoeom_pno* pno, int64_t* sigma_evals_fp32, int64_t* sigma_evals_fp64) {
+  return guard([&] {
+    PN_CHECK(pno, PNOEOM_ERR_INVALID_ARG, "NULL handle");
+    if (sigma_evals_fp32) *sigma_evals_fp32 = pno->last_sigma_evals[0];
+    if (sigma_evals_fp64) *sigma_evals_fp64 = pno->last_sigma_evals[1];
+  });
+}
+
 int pno_get_occupations(const pnoeom_pno* pno, double* occ) {
   return guard([&] {
     PN_CHECK(pno && occ, PNOEOM_ERR_INVALID_ARG, "NULL argument");

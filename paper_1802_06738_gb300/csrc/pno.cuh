@@ -87,6 +87,7 @@ struct pnoeom_pno {
   std::vector<double> occupations;           // npairs x v eigenvalues of D^{ij}
   std::vector<double> last_X;
   int last_nroots = 0;
+  int64_t last_sigma_evals[2] = {0, 0};   // FP32 / FP64 sigma evaluations of the last solve
   // per-call scratch kept across calls
   pnoeom::DBuf<double> work64; pnoeom::DBuf<float> work32;
   // tracing: per kernel class, operator elements read once per launch,

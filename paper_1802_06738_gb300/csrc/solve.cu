@@ -496,6 +496,7 @@ struct DavState {
   DBuf<float> fin, fout;    // FP32 copies of the pending vectors and their sigma
   int m = 0, nr = 0, it = 0, p0 = 0, p1 = 0;
   int64_t sigma_evals = 0;
+  int64_t sigma_evals_prec[2] = {0, 0};   // FP32, FP64 sigma evaluations
   bool done = false, converged = false;
   bool trace = std::getenv("PNOEOM_LOG_DAVIDSON") != nullptr;
   std::vector<double> w, rn, w_old;
@@ -666,7 +667,11 @@ void drive(std::vector<DavState*>& st, int chunk, Eval&& eval) {
         }
       if (!need) continue;
       eval(st, nv, prec);
-      for (size_t k = 0; k < st.size(); ++k) { st[k]->p0 += nv[k]; st[k]->sigma_evals += nv[k]; }
+      for (size_t k = 0; k < st.size(); ++k) {
+        st[k]->p0 += nv[k];
+        st[k]->sigma_evals += nv[k];
+        st[k]->sigma_evals_prec[prec == PNOEOM_FP64] += nv[k];
+      }
     }
   }
 }
@@ -687,7 +692,11 @@ void drive_round(std::vector<DavState*>& st, int chunk, Eval&& eval) {
       }
     if (!need) continue;
     eval(st, nv, prec);
-    for (size_t k = 0; k < st.size(); ++k) { st[k]->p0 += nv[k]; st[k]->sigma_evals += nv[k]; }
+    for (size_t k = 0; k < st.size(); ++k) {
+      st[k]->p0 += nv[k];
+      st[k]->sigma_evals += nv[k];
+      st[k]->sigma_evals_prec[prec == PNOEOM_FP64] += nv[k];
+    }
   }
 }
 
@@ -737,6 +746,8 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
     eval_states(P->prog, ss, nv, prec, &w64, &w32, s, nullptr);
   });
   d.results(energies, res_norms, iters);
+  P->last_sigma_evals[0] = d.sigma_evals_prec[0];
+  P->last_sigma_evals[1] = d.sigma_evals_prec[1];
   *converged = d.converged ? 1 : 0;
 }
 

@@ -156,10 +156,13 @@ def test_sigma_fp32_error_bound(pkg, ctx, case):
 def test_davidson_fp64_matches_oracle(pkg, ctx, case):
     d = oracle_case(case)
     gp = _build(pkg, ctx, d)
+    assert gp.solve_stats() == dict(fp32=0, fp64=0)
     e, rn, it, conv = gp.davidson_solve()
     w, X, rno, ito, convo = davidson.solve(d["ps"], d["sp"], d["nr"])
     assert conv and convo
     assert np.abs(e - w).max() < 1e-8
+    ev = gp.solve_stats()   # the guesses, then at least one new sigma per iteration but the last; FP64 only
+    assert ev["fp32"] == 0 and ev["fp64"] >= it
 
 
 def test_davidson_mixed_with_refinement(pkg, ctx):
@@ -169,3 +172,5 @@ def test_davidson_mixed_with_refinement(pkg, ctx):
     w, X, rno, ito, convo = davidson.solve(d["ps"], d["sp"], d["nr"])
     assert conv
     assert np.abs(e - w).max() < 1e-6
+    ev = gp.solve_stats()   # the FP32 phase from the guesses, then the FP64 refinement
+    assert ev["fp32"] >= d["nr"] and ev["fp64"] >= 1
