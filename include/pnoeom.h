@@ -107,6 +107,7 @@ typedef struct {
  * budget; otherwise pno_build refuses (PNOEOM_ERR_NOMEM) a system whose
  * estimated footprint exceeds it. */
 int pnoeom_create(pnoeom_ctx** ctx, int device, size_t hbm_budget_bytes);
+/* Frees the context (NULL: no-op).  Handles built on it are destroyed first. */
 void pnoeom_destroy(pnoeom_ctx* ctx);
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -120,6 +121,8 @@ const char* pnoeom_last_error(void);
  * copied; *out owns all device state. */
 int pno_build(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts,
               void* cuda_stream, pnoeom_pno** out);
+/* Frees the handle and its device memory (NULL: no-op).  Work issued on it must
+ * have completed, and batches that reference it are destroyed first. */
 void pno_destroy(pnoeom_pno* pno);
 
 /* Sizes of the packed PNO vector.  Arrays stay valid until pno_destroy.
@@ -254,6 +257,9 @@ int pno_get_occupations(const pnoeom_pno* pno, double* occ);
  * (2 sum b^2 = 1), largest-magnitude entry positive. */
 int pno_get_cis_vectors(const pnoeom_pno* pno, double* b);
 
+/* The nroots_sa lowest singlet CIS excitation energies omega_k (Eh, ascending;
+ * Sec. 2, CIS(D) paragraph) whose doubles define the state average, as doubles on
+ * the host. */
 int pno_get_cis(const pnoeom_pno* pno, double* omega);
 
 /* Dense FP32 product on the tensor cores: C (M x N) += alpha * A (M x K) * B (K x N),
