@@ -78,8 +78,10 @@ typedef struct {
  * t_osv: T_CutOSV, < 0 means t_pno / 10 (Sec. 3).  nroots_sa: N of the state
  * average (Eq. eom:sa_density); nroots_solve: roots returned by the solver
  * (<= nroots_sa).  precision: PNOEOM_FP64 or PNOEOM_FP32 sigma;
- * refine_fp64: after an FP32 solve, continue with FP64 sigma until the FP64
- * tolerances hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
+ * refine_fp64: the FP32 phase aims at res_tol and hands over to FP64 sigma when
+ * that holds, when its largest residual (below 1e-4) stops halving within three
+ * iterations, or when no new direction survives; the FP64 phase then restarts
+ * from the N Ritz vectors and runs until the FP64 tolerances hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
  * change between iterations; max_subspace <= 0 means 8 * nroots_solve.
  * state_specific: 0 (the default, and the paper's method) builds state-averaged
  * PNOs/OSVs; k in 1..nroots_sa builds them from the CIS(D) pair densities of CIS

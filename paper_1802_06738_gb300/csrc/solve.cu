@@ -500,6 +500,9 @@ struct DavState {
   bool done = false, converged = false;
   bool trace = std::getenv("PNOEOM_LOG_DAVIDSON") != nullptr;
   std::vector<double> w, rn, w_old;
+  std::vector<double> rhist;   // largest residual norm of every FP32 iteration (mixed solves)
+  // Level below which a stalled FP32 phase hands over to the FP64 refinement.
+  static constexpr double SWITCH_RES = 1e-4;
 
   DavState(pnoeom_pno* P_, const pnoeom_opts* opts, cudaStream_t s_) : P(P_), s(s_), L(P_->L), D{P_, s_, P_->L} {
     nroots = opts->nroots_solve;
@@ -511,8 +514,10 @@ struct DavState {
     e_tol = opts->e_tol > 0 ? opts->e_tol : 1e-10;
     prec = opts->precision == PNOEOM_FP32 ? PNOEOM_FP32 : PNOEOM_FP64;
     refine = prec == PNOEOM_FP32 && opts->refine_fp64;
-    // in mixed precision, converge to a looser residual first, then refine in FP64
-    tol_mixed = refine ? std::max(res_tol, 1e-4) : res_tol;
+    // mixed precision: the FP32 phase aims at the final residual tolerance and hands over
+    // to the FP64 refinement when that holds or, below SWITCH_RES, when its largest residual
+    // stops halving within three iterations (the error floor of the FP32 sigma)
+    tol_mixed = res_tol;
     std::vector<int64_t> offs;
     std::vector<int> ns;
     for (int p = 0; p < P->npairs; ++p)
@@ -570,6 +575,13 @@ struct DavState {
     for (int q = 0; q < nr; ++q) conv = conv && rn[q] < tol_now();
     conv = conv && (prec == PNOEOM_FP32 && refine ? true : dw < e_tol);
     if (conv) { finish_or_refine(); return; }
+    if (prec == PNOEOM_FP32 && refine) {
+      double rmax = 0;
+      for (double x : rn) rmax = std::max(rmax, x);
+      rhist.push_back(rmax);
+      const size_t k = rhist.size();
+      if (rmax < SWITCH_RES && k >= 4 && rmax > 0.5 * rhist[k - 4]) { finish_or_refine(); return; }
+    }
     std::vector<int> add;
     for (int q = 0; q < nr; ++q) if (rn[q] >= tol_now()) add.push_back(q);
     int first_new = m;
@@ -607,7 +619,8 @@ struct DavState {
     if (m == m0 && first_new == m) {   // no new direction: converged if every residual is within tolerance
       bool allres = true;
       for (int q = 0; q < nr; ++q) allres = allres && rn[q] < tol_now();
-      if (allres) { finish_or_refine(); return; }
+      // an FP32 phase whose directions the FP32 sigma can no longer resolve hands over to FP64
+      if (allres || (prec == PNOEOM_FP32 && refine)) { finish_or_refine(); return; }
       done = true;
       return;
     }
