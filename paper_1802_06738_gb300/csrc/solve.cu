@@ -488,7 +488,7 @@ struct DavState {
   cudaStream_t s;
   int64_t L;
   int nroots, maxsub, max_iter;
-  double res_tol, e_tol, tol_mixed;
+  double res_tol, e_tol;
   bool refine;
   int prec;
   Dav D;
@@ -514,10 +514,9 @@ struct DavState {
     e_tol = opts->e_tol > 0 ? opts->e_tol : 1e-10;
     prec = opts->precision == PNOEOM_FP32 ? PNOEOM_FP32 : PNOEOM_FP64;
     refine = prec == PNOEOM_FP32 && opts->refine_fp64;
-    // mixed precision: the FP32 phase aims at the final residual tolerance and hands over
-    // to the FP64 refinement when that holds or, below SWITCH_RES, when its largest residual
-    // stops halving within three iterations (the error floor of the FP32 sigma)
-    tol_mixed = res_tol;
+    // mixed precision: the FP32 phase aims at the final residual tolerance too and hands
+    // over to the FP64 refinement when that holds or, below SWITCH_RES, when its largest
+    // residual stops halving within three iterations (the error floor of the FP32 sigma)
     std::vector<int64_t> offs;
     std::vector<int> ns;
     for (int p = 0; p < P->npairs; ++p)
@@ -536,8 +535,6 @@ struct DavState {
     nr = std::min(nroots, m);
     p0 = 0; p1 = m;
   }
-
-  double tol_now() const { return prec == PNOEOM_FP32 ? tol_mixed : res_tol; }
 
   // one Davidson iteration on the current subspace (all sigma available)
   void iterate() {
@@ -572,7 +569,7 @@ struct DavState {
                    prec == PNOEOM_FP32 ? "fp32" : "fp64", rmax, dw, w.empty() ? 0.0 : w[0]);
     }
     bool conv = true;
-    for (int q = 0; q < nr; ++q) conv = conv && rn[q] < tol_now();
+    for (int q = 0; q < nr; ++q) conv = conv && rn[q] < res_tol;
     conv = conv && (prec == PNOEOM_FP32 && refine ? true : dw < e_tol);
     if (conv) { finish_or_refine(); return; }
     if (prec == PNOEOM_FP32 && refine) {
@@ -583,7 +580,7 @@ struct DavState {
       if (rmax < SWITCH_RES && k >= 4 && rmax > 0.5 * rhist[k - 4]) { finish_or_refine(); return; }
     }
     std::vector<int> add;
-    for (int q = 0; q < nr; ++q) if (rn[q] >= tol_now()) add.push_back(q);
+    for (int q = 0; q < nr; ++q) if (rn[q] >= res_tol) add.push_back(q);
     int first_new = m;
     if (m + (int)add.size() > maxsub) {
       // thick restart: keep the Ritz vectors of the lowest nkeep subspace eigenvalues (at
@@ -618,7 +615,7 @@ struct DavState {
     }
     if (m == m0 && first_new == m) {   // no new direction: converged if every residual is within tolerance
       bool allres = true;
-      for (int q = 0; q < nr; ++q) allres = allres && rn[q] < tol_now();
+      for (int q = 0; q < nr; ++q) allres = allres && rn[q] < res_tol;
       // an FP32 phase whose directions the FP32 sigma can no longer resolve hands over to FP64
       if (allres || (prec == PNOEOM_FP32 && refine)) { finish_or_refine(); return; }
       done = true;
