@@ -232,7 +232,9 @@ int pnoeom_server_submit(pnoeom_server* srv, const pnoeom_system* sys, const pno
 int pnoeom_server_poll(pnoeom_server* srv, int64_t id, int* status, double* energies, double* res_norms,
                        int* iters, int64_t* sigma_evals, double* times);
 /* Block until request `id` is DONE or FAILED, or timeout_s elapses
- * (PNOEOM_ERR_TIMEOUT). */
+ * (PNOEOM_ERR_TIMEOUT).  PNOEOM_ERR_CUDA if the server stopped before the
+ * request finished (a worker thread could not get its stream or solver handle;
+ * submit then fails the same way). */
 int pnoeom_server_wait(pnoeom_server* srv, int64_t id, double timeout_s);
 /* Counters: device bytes held for admitted requests, queued / building-or-built
  * / running requests, lockstep rounds, program merges, sigma-evals done. */

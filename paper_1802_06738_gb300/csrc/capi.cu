@@ -34,6 +34,9 @@ int pnoeom::guard_call(const std::function<void()>& f) {
   } catch (const std::exception& e) {
     g_last_error = e.what();
     return PNOEOM_ERR_CUDA;
+  } catch (...) {   // nothing may cross the C boundary
+    g_last_error = "unknown exception";
+    return PNOEOM_ERR_CUDA;
   }
 }
 

@@ -969,18 +969,23 @@ size_t estimate_build_bytes(int o, int v, int naux) {
 namespace pnoeom {
 
 static void server_builder(pnoeom_server* S) {
-  cudaSetDevice(S->device);
-  pnoeom_ctx bctx;
-  bctx.device = S->device;
-  if (cusolverDnCreate(&bctx.solver) != CUSOLVER_STATUS_SUCCESS) {
+  auto fail = [&](const char* why) {   // the server cannot run: stop it and tell every waiter
     std::lock_guard<std::mutex> lk(S->mu);
-    S->fatal = "builder: cusolverDnCreate failed";
+    S->fatal = why;
     S->stop = true;
     S->cv.notify_all();
+  };
+  if (cudaSetDevice(S->device) != cudaSuccess) { fail("builder: cudaSetDevice failed"); return; }
+  pnoeom_ctx bctx;
+  bctx.device = S->device;
+  if (cusolverDnCreate(&bctx.solver) != CUSOLVER_STATUS_SUCCESS) { fail("builder: cusolverDnCreate failed"); return; }
+  cudaStream_t bs;
+  if (cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking) != cudaSuccess) {
+    cusolverDnDestroy(bctx.solver);
+    bctx.solver = nullptr;
+    fail("builder: cudaStreamCreateWithFlags failed");
     return;
   }
-  cudaStream_t bs;
-  cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
   for (;;) {
     std::shared_ptr<Request> r;
     {
@@ -1027,9 +1032,14 @@ static void server_builder(pnoeom_server* S) {
 }
 
 static void server_solver(pnoeom_server* S) {
-  cudaSetDevice(S->device);
   cudaStream_t ss;
-  cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+  if (cudaSetDevice(S->device) != cudaSuccess || cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->fatal = "solver: no stream on the server's device";
+    S->stop = true;
+    S->cv.notify_all();
+    return;
+  }
   std::vector<std::shared_ptr<Request>> active;
   pnoeom_batch B;
   bool dirty = true;
@@ -1218,6 +1228,8 @@ void server_wait(pnoeom_server* srv, int64_t id, double timeout_s) {
       return r->status == PNOEOM_REQ_DONE || r->status == PNOEOM_REQ_FAILED || !srv->fatal.empty();
     });
     PN_CHECK(ok, PNOEOM_ERR_TIMEOUT, "request " + std::to_string(id) + " not finished within the timeout");
+    PN_CHECK(r->status == PNOEOM_REQ_DONE || r->status == PNOEOM_REQ_FAILED, PNOEOM_ERR_CUDA,
+             "server stopped: " + srv->fatal);
   }
 
 void server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int* running, int64_t* rounds,
