@@ -141,7 +141,10 @@ int pno_get_basis(const pnoeom_pno* pno, int pair, double* U, double* fbar);
 /* sigma = Hbar R projected into the PNO/OSV spaces (Sec. 2) for nvec packed
  * vectors.  r_dev, s_dev: caller-owned device buffers of nvec * vec_len
  * elements of the chosen precision (double for FP64, float for FP32).
- * Asynchronous on cuda_stream. */
+ * Asynchronous on cuda_stream.  Calls on one handle share its scratch (the
+ * R-dependent intermediates, grown when a call needs more vectors than any
+ * before it): issue them on one stream, or synchronise between calls on
+ * different streams.  Calls on different handles may overlap. */
 int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
           int precision, void* cuda_stream);
 
