@@ -73,7 +73,7 @@ def lib():
         vp, ip, dp, i, d = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_double
         L.pnoeom_create.argtypes = [ctypes.POINTER(vp), i, ctypes.c_size_t]
         L.pnoeom_destroy.argtypes = [vp]; L.pnoeom_destroy.restype = None
-        L.pnoeom_last_error.restype = ctypes.c_char_p
+        L.pnoeom_last_error.argtypes = []; L.pnoeom_last_error.restype = ctypes.c_char_p
         L.pno_build.argtypes = [vp, ctypes.POINTER(System), ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
         L.pno_destroy.argtypes = [vp]; L.pno_destroy.restype = None
         L.pno_query.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]

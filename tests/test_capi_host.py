@@ -37,6 +37,13 @@ def test_every_declared_symbol_is_exported(pkg):
     assert set(names) <= set(pkg.EXPORTS) | {"pnoeom_create"}
 
 
+def test_binding_declares_argument_types_of_every_export(pkg):
+    # without argtypes ctypes passes Python ints as C int, truncating 64-bit handles
+    L = pkg.lib()
+    for n in set(pkg.EXPORTS) | {"pnoeom_create"}:
+        assert getattr(L, n).argtypes is not None, n
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 8, 24, 48])
 def test_small_eig_real_spectrum(pkg, n):
     rng = np.random.default_rng(n)
