@@ -309,9 +309,9 @@ struct ThreadBlas {
 };
 thread_local ThreadBlas t_blas;
 
-// FP64 problems with at least this many multiply-adds go to cuBLAS (the FP64 tensor-core
-// GEMMs of the library), grouped by shape into batched calls; smaller ones stay on the
-// grouped SIMT kernel, where one launch covers many of them.
+// FP64 problems with at least this many multiply-adds go to cuBLAS DGEMM, grouped by
+// shape into batched calls; smaller ones stay on the grouped SIMT kernel, where one launch
+// covers many of them.
 constexpr double BLAS_MIN_MACS = 32768.0;
 
 // C = alpha op(A) op(B) + beta C in row-major storage is, read column-major,
