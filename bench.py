@@ -95,7 +95,10 @@ class Clocks:
         self.proc = None
         self.rows = []                 # (arrival time, csv fields)
         self.window = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples (the JSON line carries their summary); PNOEOM_CLOCKS_DIR picks the folder
+        import tempfile
+        self.path = os.path.join(os.environ.get("PNOEOM_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"pnoeom_clocks_{os.getpid()}.csv")
 
     def _read(self):
         import time as _t
