@@ -480,9 +480,9 @@ struct Dav {
 }  // namespace
 
 // One system's Davidson solve as a state machine.  iterate() needs sigma of
-// every vector in the pending slot range [p0, p1) of V in S; the driver
-// evaluates those (for many systems at once in a batch) and calls iterate()
-// again.  Sec. 2, PNO-EOM-CCSD Davidson; readings in the header of pnoeom.h.
+// every vector in the pending slot range [p0, p1) of V in S; drive() or
+// drive_round() evaluates those (for many systems at once in a batch) and calls
+// iterate() again.  Sec. 2, PNO-EOM-CCSD Davidson; readings in the header of pnoeom.h.
 struct DavState {
   pnoeom_pno* P;
   cudaStream_t s;
