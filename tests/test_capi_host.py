@@ -37,6 +37,33 @@ def test_every_declared_symbol_is_exported(pkg):
     assert set(names) <= set(pkg.EXPORTS) | {"pnoeom_create"}
 
 
+def test_struct_layouts_match_the_header(pkg, tmp_path):
+    """The ctypes mirrors of pnoeom_system and pnoeom_opts have the C layout: size and
+    every field's offset, from a C program compiled against include/pnoeom.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"pnoeom_system": pkg.System, "pnoeom_opts": pkg.Opts}
+    lines = ['#include "pnoeom.h"', "#include <stddef.h>", "#include <stdio.h>", "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(ln.split()[:2]): int(ln.split()[2]) for ln in out if ln.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
 def test_binding_declares_argument_types_of_every_export(pkg):
     # without argtypes ctypes passes Python ints as C int, truncating 64-bit handles
     L = pkg.lib()
