@@ -144,7 +144,11 @@ int pno_get_basis(const pnoeom_pno* pno, int pair, double* U, double* fbar);
  * Asynchronous on cuda_stream.  Calls on one handle share its scratch (the
  * R-dependent intermediates, grown when a call needs more vectors than any
  * before it): issue them on one stream, or synchronise between calls on
- * different streams.  Calls on different handles may overlap. */
+ * different streams.  Calls on different handles may overlap.  In FP32 some terms run
+ * on the tensor cores, whose bounded waits do not raise an error here: the result is
+ * valid only if pnoeom_device_status reads 0 once the stream has been synchronised
+ * (davidson_solve checks this itself).  The call makes ctx's device current for its
+ * duration and restores the caller's current device before returning. */
 int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
           int precision, void* cuda_stream);
 
@@ -165,7 +169,8 @@ int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, v
  * call's contents (each call clears what it needs): calls whose executions
  * overlap on the GPU race on it, so issue them on one stream or otherwise
  * serialise them.  No cudaMalloc, cudaFree or allocating library routine is
- * called.  Arguments, layouts and errors are those of sigma(). */
+ * called.  Arguments, layouts and errors are those of sigma(), including the check of
+ * pnoeom_device_status that an FP32 result needs before it is trusted. */
 #define PNOEOM_NOALLOC_SCRATCH_BYTES (64u << 20)
 int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, void* s_dev,
                   int precision, void* cuda_stream);
@@ -285,6 +290,24 @@ int pnoeom_gemm_tf32x3(pnoeom_ctx* ctx, const float* A, const float* B, float* C
  * budget (about one second), in which case that tile's contribution was skipped and its
  * result is invalid.  clear != 0 resets the word.  Synchronises the device. */
 int pnoeom_device_status(pnoeom_ctx* ctx, int clear, int* status);
+
+/* Failure detection without a GPU fault.  pnoeom_selftest_bounded_wait launches one
+ * CTA that waits on an mbarrier nothing ever arrives at, for at most budget_cycles
+ * clock cycles (1 .. 2e9, about one second at most), and records the expiry exactly as
+ * a tensor-core kernel does: bit 0 of the status word (pnoeom_device_status), so the
+ * next davidson_solve or pnoeom_batch_solve returns PNOEOM_ERR_TIMEOUT and clears it.
+ * *timed_out receives 1 when the wait ran out (it always should).  Blocking. */
+int pnoeom_selftest_bounded_wait(pnoeom_ctx* ctx, long long budget_cycles, void* cuda_stream, int* timed_out);
+
+/* Host-side fault injection in the library's caching device allocator: after `after`
+ * further successful allocation requests (0: the very next one) one request fails as
+ * if the device were out of memory, so the call making it returns PNOEOM_ERR_NOMEM;
+ * a negative value disables the injection.  Process-wide.  pnoeom_alloc_live_bytes
+ * reports the bytes of allocator blocks currently held by live objects (handles,
+ * batches, scratch), which returns to its earlier value when a failed call has
+ * released everything it took. */
+int pnoeom_inject_alloc_failure(long long after);
+int pnoeom_alloc_live_bytes(long long* bytes);
 
 /* Eigenpairs of a small dense non-symmetric matrix on the host (the Davidson
  * subspace step, Sec. 2).  A: row-major n x n; wr, wi: real and imaginary

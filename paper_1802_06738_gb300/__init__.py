@@ -60,7 +60,8 @@ EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", 
            "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve",
            "pnoeom_server_create", "pnoeom_server_destroy", "pnoeom_server_submit", "pnoeom_server_poll",
            "pnoeom_server_wait", "pnoeom_server_stats", "pnoeom_gemm_tf32x3", "pnoeom_device_status",
-           "pno_solve_stats"]
+           "pno_solve_stats", "pnoeom_selftest_bounded_wait", "pnoeom_inject_alloc_failure",
+           "pnoeom_alloc_live_bytes"]
 
 
 def lib():
@@ -102,6 +103,9 @@ def lib():
         L.pnoeom_gemm_tf32x3.argtypes = [vp, vp, vp, vp, i, i, i, ctypes.c_float, vp]
         L.pnoeom_device_status.argtypes = [vp, i, ip]
         L.pno_build_seconds.argtypes = [vp]; L.pno_build_seconds.restype = d
+        L.pnoeom_selftest_bounded_wait.argtypes = [vp, ctypes.c_longlong, vp, ip]
+        L.pnoeom_inject_alloc_failure.argtypes = [ctypes.c_longlong]
+        L.pnoeom_alloc_live_bytes.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
         L.pno_set_timing.argtypes = [vp, i]
         L.pno_sigma_timing.argtypes = [vp, i, i, i, ctypes.POINTER(ctypes.c_char_p), ip, dp, dp, dp]
         _lib = L

@@ -54,7 +54,7 @@ int pnoeom_create(pnoeom_ctx** ctx, int device, size_t hbm_budget_bytes) {
     int ndev = 0;
     PN_CUDA(cudaGetDeviceCount(&ndev));
     PN_CHECK(device >= 0 && device < ndev, PNOEOM_ERR_INVALID_ARG, "no such CUDA device");
-    PN_CUDA(cudaSetDevice(device));
+    pnoeom::DeviceScope dev_scope(device);
     auto* c = new pnoeom_ctx();
     c->device = device;
     c->budget = hbm_budget_bytes;
@@ -75,7 +75,7 @@ void pnoeom_destroy(pnoeom_ctx* ctx) {
 int pno_build(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts, void* cuda_stream, pnoeom_pno** out) {
   return guard([&] {
     PN_CHECK(ctx && sys && opts && out, PNOEOM_ERR_INVALID_ARG, "NULL argument");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     auto* P = new pnoeom_pno();
     try {
       pnoeom::build_system(ctx, sys, opts, st(cuda_stream), P);
@@ -83,7 +83,11 @@ int pno_build(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts
         throw pnoeom::Error(PNOEOM_ERR_NOMEM, "device footprint " + std::to_string(P->footprint) +
                                                   " bytes exceeds the context budget");
     } catch (...) {
+      // free the partial handle, then return the setup's cached blocks to CUDA (the
+      // stream is drained first: blocks may still be in use by queued work)
       delete P;
+      cudaStreamSynchronize(st(cuda_stream));
+      pnoeom::pool_trim();
       throw;
     }
     *out = P;
@@ -180,7 +184,7 @@ int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, v
     PN_CHECK(nvec >= 0, PNOEOM_ERR_INVALID_ARG, "nvec < 0");
     if (nvec == 0) return;
     PN_CHECK(r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL vector");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     auto* P = const_cast<pnoeom_pno*>(pno);
     if (precision == PNOEOM_FP64)
       pnoeom::apply_sigma<double>(P, nvec, (const double*)r_dev, (double*)s_dev, st(cuda_stream));
@@ -196,7 +200,7 @@ int davidson_solve(pnoeom_ctx* ctx, pnoeom_pno* pno, const pnoeom_opts* opts, vo
   int conv = 0;
   int rc = guard([&] {
     PN_CHECK(ctx && pno && opts && energies && res_norms && iters, PNOEOM_ERR_INVALID_ARG, "NULL argument");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     pnoeom::run_davidson(ctx, pno, opts, st(cuda_stream), energies, res_norms, iters, &conv);
     PN_CHECK(pnoeom::device_status(true, st(cuda_stream)) == 0, PNOEOM_ERR_TIMEOUT,
              "a tensor-core kernel's bounded wait ran out during the solve: results are invalid");
@@ -212,7 +216,7 @@ int pnoeom_batch_create(pnoeom_ctx* ctx, pnoeom_pno* const* members, int n, void
   return guard([&] {
     PN_CHECK(ctx && members && out && n >= 1, PNOEOM_ERR_INVALID_ARG, "bad arguments");
     for (int k = 0; k < n; ++k) PN_CHECK(members[k], PNOEOM_ERR_INVALID_ARG, "NULL member");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     auto* B = new pnoeom_batch();
     B->device = ctx->device;
     B->members.assign(members, members + n);
@@ -233,7 +237,7 @@ int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, co
   return guard([&] {
     PN_CHECK(ctx && batch && nvec && r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL argument");
     PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32, PNOEOM_ERR_INVALID_ARG, "unknown precision");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     pnoeom::batch_sigma(batch, nvec, r_dev, s_dev, precision, st(cuda_stream));
   });
 }
@@ -243,7 +247,7 @@ int pnoeom_batch_solve(pnoeom_ctx* ctx, pnoeom_batch* batch, const pnoeom_opts* 
   int all = 1;
   int rc = guard([&] {
     PN_CHECK(ctx && batch && opts && energies && res_norms && iters && converged, PNOEOM_ERR_INVALID_ARG, "NULL argument");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     pnoeom::batch_solve(batch, opts, st(cuda_stream), energies, res_norms, iters, converged);
     PN_CHECK(pnoeom::device_status(true, st(cuda_stream)) == 0, PNOEOM_ERR_TIMEOUT,
              "a tensor-core kernel's bounded wait ran out during the solve: results are invalid");
@@ -335,7 +339,7 @@ int pnoeom_gemm_tf32x3(pnoeom_ctx* ctx, const float* A, const float* B, float* C
                        void* cuda_stream) {
   return guard([&] {
     PN_CHECK(ctx, PNOEOM_ERR_INVALID_ARG, "NULL context");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     pnoeom::gemm_tf32x3(A, B, C, M, N, K, alpha, st(cuda_stream));
   });
 }
@@ -343,9 +347,30 @@ int pnoeom_gemm_tf32x3(pnoeom_ctx* ctx, const float* A, const float* B, float* C
 int pnoeom_device_status(pnoeom_ctx* ctx, int clear, int* status) {
   return guard([&] {
     PN_CHECK(ctx && status, PNOEOM_ERR_INVALID_ARG, "NULL argument");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     PN_CUDA(cudaDeviceSynchronize());
     *status = pnoeom::device_status(clear != 0, nullptr);
+  });
+}
+
+int pnoeom_inject_alloc_failure(long long after) {
+  return guard([&] { pnoeom::inject_alloc_failure(after); });
+}
+
+int pnoeom_alloc_live_bytes(long long* bytes) {
+  return guard([&] {
+    PN_CHECK(bytes, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    *bytes = pnoeom::live_alloc_bytes();
+  });
+}
+
+int pnoeom_selftest_bounded_wait(pnoeom_ctx* ctx, long long budget_cycles, void* cuda_stream, int* timed_out) {
+  return guard([&] {
+    PN_CHECK(ctx && timed_out, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    PN_CHECK(budget_cycles >= 1 && budget_cycles <= 2000000000LL, PNOEOM_ERR_INVALID_ARG,
+             "budget_cycles must be in 1 .. 2e9");
+    pnoeom::DeviceScope dev_scope(ctx->device);
+    *timed_out = pnoeom::selftest_bounded_wait(budget_cycles, st(cuda_stream));
   });
 }
 

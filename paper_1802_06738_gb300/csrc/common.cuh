@@ -50,6 +50,11 @@ void* pool_get(size_t bytes);
 void pool_put(void* p, size_t bytes);
 void pool_trim();
 std::recursive_mutex& capture_mutex();
+// Fault injection: after `after` further successful requests (0: the next one), one
+// pool_get fails with PNOEOM_ERR_NOMEM; a negative value disables it.  live_alloc_bytes:
+// bytes of blocks handed out by pool_get and not yet returned, over all threads.
+void inject_alloc_failure(long long after);
+long long live_alloc_bytes();
 
 // Owning device buffer (cached allocator, see pool_get).  Counts bytes into a shared
 // footprint counter so handles can report their device footprint.
@@ -62,9 +67,9 @@ struct DBuf {
   explicit DBuf(size_t count, size_t* ctr = nullptr) { alloc(count, ctr); }
   void alloc(size_t count, size_t* ctr = nullptr) {
     release();
+    if (count) p = (T*)pool_get(count * sizeof(T));   // may throw: nothing recorded yet
     n = count;
     counter = ctr;
-    if (count) p = (T*)pool_get(count * sizeof(T));
     if (counter) *counter += count * sizeof(T);
   }
   void release() {
@@ -88,6 +93,23 @@ struct DBuf {
   void download(T* h, size_t count, cudaStream_t s) const {
     if (count) PN_CUDA(cudaMemcpyAsync(h, p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
   }
+};
+
+// Makes `device` current for the scope of one C entry point and restores the
+// caller's current device on the way out (also when an error is thrown), so a
+// call never leaves another device current for the caller's later work.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int device) {
+    PN_CUDA(cudaGetDevice(&prev));
+    if (prev != device) PN_CUDA(cudaSetDevice(device));
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
 };
 
 // Stage timer for tracing: when the environment variable PNOEOM_LOG_TIMING is

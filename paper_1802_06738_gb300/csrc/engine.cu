@@ -7,6 +7,7 @@
 #include <map>
 #include <chrono>
 #include <cstdlib>
+#include <atomic>
 
 namespace pnoeom {
 
@@ -47,8 +48,22 @@ std::recursive_mutex& capture_mutex() {
   return m;
 }
 
+// Fault injection and accounting of the caching allocator (host side): the
+// countdown makes the allocation request it reaches zero on fail as if the
+// device were out of memory; live_bytes counts blocks handed out and not yet
+// returned (process-wide, rounded sizes).
+static std::atomic<long long> g_fail_countdown{-1};
+static std::atomic<long long> g_live_bytes{0};
+void inject_alloc_failure(long long after) { g_fail_countdown.store(after < 0 ? -1 : after); }
+long long live_alloc_bytes() { return g_live_bytes.load(); }
+
 void* pool_get(size_t bytes) {
   const size_t sz = round_size(bytes);
+  long long c = g_fail_countdown.load();
+  while (c >= 0 && !g_fail_countdown.compare_exchange_weak(c, c - 1)) {}
+  if (c == 0)
+    throw Error(PNOEOM_ERR_NOMEM, "device allocation of " + std::to_string(sz) + " bytes failed: injected failure");
+  g_live_bytes += (long long)sz;
   auto& fb = t_pool.free_blocks;
   auto it = fb.lower_bound(sz);
   if (it != fb.end() && it->first <= sz + sz / 4) {
@@ -67,6 +82,7 @@ void* pool_get(size_t bytes) {
     e = cudaMalloc(&p, sz);
     if (e != cudaSuccess) {
       cudaGetLastError();
+      g_live_bytes -= (long long)sz;
       throw Error(e == cudaErrorMemoryAllocation ? PNOEOM_ERR_NOMEM : PNOEOM_ERR_CUDA,
                   "device allocation of " + std::to_string(sz) + " bytes failed: " + cudaGetErrorString(e));
     }
@@ -75,7 +91,9 @@ void* pool_get(size_t bytes) {
 }
 
 void pool_put(void* p, size_t bytes) {
-  if (p) t_pool.free_blocks.insert({round_size(bytes), p});
+  if (!p) return;
+  g_live_bytes -= (long long)round_size(bytes);
+  t_pool.free_blocks.insert({round_size(bytes), p});
 }
 
 void pool_trim() {

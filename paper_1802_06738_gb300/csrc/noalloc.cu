@@ -59,7 +59,7 @@ extern "C" int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, c
              "sigma_noalloc needs " + std::to_string(need) + " bytes of scratch for " + std::to_string(nvec) +
                  " vectors, more than its fixed " + std::to_string((size_t)PNOEOM_NOALLOC_SCRATCH_BYTES) +
                  "-byte array; pass fewer vectors per call or use sigma()");
-    PN_CUDA(cudaSetDevice(ctx->device));
+    pnoeom::DeviceScope dev_scope(ctx->device);
     void* work = scratch_address(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     if (precision == PNOEOM_FP64)

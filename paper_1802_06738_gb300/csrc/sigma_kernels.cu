@@ -753,8 +753,10 @@ __global__ void __launch_bounds__(256) k_dense_skinny(const DProb* __restrict__ 
 }
 
 // Device status word shared by the tensor-core kernels: bit 0 is set when an mbarrier
-// wait ran out of its clock budget (the kernel then skips the rest of its tile, frees its
-// TMEM and returns).  Read and cleared by pnoeom_device_status.
+// wait ran out of its clock budget (the kernel then issues no further MMA, waits for the
+// ones in flight, frees its TMEM and returns without writing its tile); bit 1 when that
+// second wait ran out too and the TMEM columns were left allocated.  Read and cleared by
+// pnoeom_device_status.
 __device__ int g_tc_status = 0;
 
 constexpr int TC_BM = 128, TC_BN = 64, TC_BK = 32;
@@ -827,15 +829,18 @@ __global__ void __launch_bounds__(128) k_dense_tc(const DProb* __restrict__ prob
       }
     }
   };
+  // Every thread polls the stage's mbarrier, and the CTA then agrees on the outcome
+  // (__syncthreads_and), so a wait that runs out takes every thread down the same path.
   uint32_t parity[2] = {0u, 0u};
   bool ok = true;
+  int issued = 0;   // chunks whose MMAs were issued and committed
   if (nchunk > 0) load(0);
-  for (int c = 0; c < nchunk && ok; ++c) {
+  for (int c = 0; c < nchunk; ++c) {
     const int b = c & 1;
     if (c >= 2) {   // the MMAs of chunk c - 2 read stage b
-      ok = tc::mbar_wait_bounded(mbar + b, parity[b], TC_WAIT_BUDGET);
-      parity[b] ^= 1u;
+      ok = __syncthreads_and(tc::mbar_wait_bounded(mbar + b, parity[b], TC_WAIT_BUDGET) ? 1 : 0) != 0;
       if (!ok) break;
+      parity[b] ^= 1u;
     }
     float* Ah = sAh + b * TC_STAGE;
     float* Al = sAl + b * TC_STAGE;
@@ -876,16 +881,27 @@ __global__ void __launch_bounds__(128) k_dense_tc(const DProb* __restrict__ prob
       }
       tc::mma_commit(mbar + b);
     }
+    issued = c + 1;
     if (c + 1 < nchunk) load(c + 1);
   }
   // the last one or two chunks' MMAs (MMAs complete in issue order: waiting for the last
   // commit covers the earlier ones, but each barrier's phase is consumed to keep them paired)
-  for (int c = max(0, nchunk - 2); c < nchunk && ok; ++c) {
+  for (int c = max(0, issued - 2); c < issued && ok; ++c) {
     const int b = c & 1;
-    ok = tc::mbar_wait_bounded(mbar + b, parity[b], TC_WAIT_BUDGET);
-    parity[b] ^= 1u;
+    ok = __syncthreads_and(tc::mbar_wait_bounded(mbar + b, parity[b], TC_WAIT_BUDGET) ? 1 : 0) != 0;
+    if (ok) parity[b] ^= 1u;
   }
-  if (!ok) atomicOr(&g_tc_status, 1);
+  bool release = true;
+  if (!ok) {
+    // A wait ran out: no further MMA was issued.  The MMAs already committed may still
+    // write TMEM, so the last commit (which covers every earlier one) is waited for once
+    // more before TMEM is released; if that wait runs out as well, the columns are kept
+    // (bit 1) rather than released under a running MMA.
+    const int last = issued - 1;
+    release = last < 0 ||
+              __syncthreads_and(tc::mbar_wait_bounded(mbar + (last & 1), parity[last & 1], TC_WAIT_BUDGET) ? 1 : 0) != 0;
+    if (tid == 0) atomicOr(&g_tc_status, release ? 1 : 3);
+  }
   tc::fence_after_sync();
   if (ok) {
     float* C = mbuf<float>(tab, P.sys, P.c_buf, r) + P.c_off;
@@ -909,7 +925,22 @@ __global__ void __launch_bounds__(128) k_dense_tc(const DProb* __restrict__ prob
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, TC_BN);
+  if (warp == 0 && release) tc::tmem_dealloc(tmem, TC_BN);
+}
+
+// Failure-detection self-test (no MMA, no TMEM): thread 0 initialises an mbarrier that
+// expects one arrival, which nothing ever makes, and polls it for at most `budget`
+// cycles; the wait therefore runs out, and the kernel records it exactly as a
+// tensor-core kernel does (bit 0 of g_tc_status) and reports it in *out.
+__global__ void k_wait_selftest(long long budget, int* out) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+  __syncthreads();
+  const bool ok = __syncthreads_and(tc::mbar_wait_bounded(&bar, 0u, budget) ? 1 : 0) != 0;
+  if (threadIdx.x == 0) {
+    if (!ok) atomicOr(&g_tc_status, 1);
+    *out = ok ? 0 : 1;
+  }
 }
 
 constexpr int VR = 8;   // roots per pass inside a GEMV CTA
@@ -1106,6 +1137,16 @@ void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cud
     k_dense_skinny<T><<<dim3(nprob, t.max_nvec), 256, 0, s>>>(d_probs, t);
   }
   PN_CUDA(cudaGetLastError());
+}
+
+int selftest_bounded_wait(long long budget, cudaStream_t s) {
+  DBuf<int> out(1);
+  k_wait_selftest<<<1, 32, 0, s>>>(budget, out.get());
+  PN_CUDA(cudaGetLastError());
+  int v = 0;
+  out.download(&v, 1, s);
+  PN_CUDA(cudaStreamSynchronize(s));
+  return v;
 }
 
 int device_status(bool clear, cudaStream_t s) {

@@ -100,6 +100,10 @@ void run_dense(const DProb* d_probs, int nprob, const SysTable& t, int tile, cud
 // Reads (and with clear, resets) the tensor-core kernels' device status word, ordered on
 // stream s: 0 when every bounded wait completed.
 int device_status(bool clear, cudaStream_t s);
+// Failure-detection self-test: one CTA waits on an mbarrier that nothing arrives at, for at
+// most budget clock cycles, then records bit 0 of the status word like a tensor-core
+// kernel whose wait ran out.  Returns 1 when the wait ran out (it always should).
+int selftest_bounded_wait(long long budget, cudaStream_t s);
 void gemm_tf32x3(const float* A, const float* B, float* C, int M, int N, int K, float alpha, cudaStream_t s);
 
 }  // namespace pnoeom

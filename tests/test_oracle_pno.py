@@ -200,3 +200,55 @@ def test_ground_state_pno_truncation_of_t2():
                 assert np.abs(Q.T @ tt[i, j]).max() < 1e-12 and np.abs(tt[i, j] @ Q).max() < 1e-12
         errs.append(np.linalg.norm(tt - t2))
     assert errs[0] >= errs[1] >= errs[2] and errs[0] > 0
+
+
+def test_osv_count_is_the_diagonal_density_count_at_a_tenth_of_t_pno():
+    """T_CutOSV = T_CutPNO / 10 (Sec. 3) on the state-averaged D^{ii} (Eq.
+    eom:sa_density): n_i equals the number of eigenvalues of D^{ii} (computed here by
+    SciPy's solver) that are >= T_PNO / 10.  The case is chosen so that counting at
+    T_PNO itself gives a different answer, so a threshold mix-up fails."""
+    import scipy.linalg
+    eps, B, h = _small(4, 12, 36, 52)
+    tp = 1e-5
+    sp = pno.PNOSpace(eps, B, 4, 3, tp)
+    differs = False
+    for i in range(4):
+        w = scipy.linalg.eigvalsh(sp.D[i, i])
+        assert sp.n_i[i] == int(np.sum(w >= tp / 10))
+        differs = differs or int(np.sum(w >= tp)) != sp.n_i[i]
+    assert differs
+    # an explicit T_CutOSV overrides the default
+    sp2 = pno.PNOSpace(eps, B, 4, 3, tp, t_osv=tp)
+    for i in range(4):
+        assert sp2.n_i[i] == int(np.sum(scipy.linalg.eigvalsh(sp.D[i, i]) >= tp))
+
+
+def test_semicanonical_bases_diagonalise_the_virtual_fock_block():
+    """Semicanonical PNOs/OSVs (Sec. 2, PNO-CCSD simulation): every kept basis is
+    orthonormal, spans exactly the kept eigenvectors of its density (SciPy's
+    eigensolver), and U^T f_vv U is diagonal with the recorded fbar on the diagonal,
+    in ascending order."""
+    import scipy.linalg
+    o, v = 4, 12
+    eps, B, h = _small(o, v, 36, 53)
+    tp = 1e-6
+    sp = pno.PNOSpace(eps, B, o, 3, tp)
+    fvv = np.diag(eps[o:])
+    sets = [(sp.U[k], sp.fbar[k], sp.D[k], tp) for k in sp.pairs]
+    sets += [(sp.Ui[i], sp.fbar_i[i], sp.D[i, i], tp / 10) for i in range(o)]
+    checked = 0
+    for U, fb, D, thr in sets:
+        n = U.shape[1]
+        if n == 0:
+            continue
+        assert np.abs(U.T @ U - np.eye(n)).max() < 1e-12
+        w, V = scipy.linalg.eigh(D)
+        Vk = V[:, w >= thr]
+        assert Vk.shape[1] == n
+        assert np.abs(U @ U.T - Vk @ Vk.T).max() < 1e-9
+        F = U.T @ fvv @ U
+        assert np.abs(F - np.diag(np.diag(F))).max() < 1e-12
+        assert np.abs(np.diag(F) - fb).max() < 1e-12
+        assert np.all(np.diff(fb) >= 0)
+        checked += 1
+    assert checked > o
