@@ -39,14 +39,38 @@ from . import ccsd
 DENOM_CLAMP = 1e-4
 
 
+# Row block of the large matrix products below: the products are formed a block of
+# rows at a time (the same sums, in the same order per element), which keeps every
+# single BLAS call to a moderate size.
+ROW_BLOCK = 3600
+
+
+def _rows_matmul(X, Y):
+    """X @ Y, computed a block of rows of X at a time."""
+    out = np.empty((X.shape[0], Y.shape[1]))
+    for r0 in range(0, X.shape[0], ROW_BLOCK):
+        out[r0:r0 + ROW_BLOCK] = X[r0:r0 + ROW_BLOCK] @ Y
+    return out
+
+
 def cis_matrix(eps, B, o):
     v = len(eps) - o
-    g_ovov = np.einsum("Qia,Qjb->iajb", B[:, :o, o:], B[:, :o, o:], optimize=True)
-    g_oovv = np.einsum("Qij,Qab->iajb", B[:, :o, :o], B[:, o:, o:], optimize=True)
-    A = 2.0 * g_ovov - g_oovv
+    nq = B.shape[0]
+    Bov = np.ascontiguousarray(B[:, :o, o:]).reshape(nq, o * v)
+    A = 2.0 * _rows_matmul(Bov.T, Bov)                       # 2 (ia|jb)
+    Boo = np.ascontiguousarray(B[:, :o, :o]).reshape(nq, o * o)
+    Bvv = np.ascontiguousarray(B[:, o:, o:]).reshape(nq, v * v)
+    A4 = A.reshape(o, v, o, v)
+    for i in range(o):                                       # - (ij|ab)
+        A4[i] -= (Boo[:, i * o:(i + 1) * o].T @ Bvv).reshape(o, v, v).transpose(1, 0, 2)
     d = (eps[o:][None, :] - eps[:o][:, None])
-    A = A.reshape(o * v, o * v) + np.diag(d.ravel())
+    A[np.diag_indices_from(A)] += d.ravel()
     return A
+
+
+# Above this many singles the lowest roots are found by an iterative symmetric
+# eigensolver (ARPACK through SciPy) instead of a full dense diagonalisation.
+CIS_DENSE_MAX = 6000
 
 
 def cis(eps, B, o, nroots):
@@ -54,7 +78,14 @@ def cis(eps, B, o, nroots):
     2 sum b^2 = 1, sign fixed by a positive largest-magnitude entry."""
     v = len(eps) - o
     A = cis_matrix(eps, B, o)
-    w, X = np.linalg.eigh(0.5 * (A + A.T))
+    A = 0.5 * (A + A.T)
+    if o * v <= CIS_DENSE_MAX:
+        w, X = np.linalg.eigh(A)
+    else:
+        import scipy.sparse.linalg as sla
+        w, X = sla.eigsh(A, k=nroots, which="SA", tol=1e-14)
+        order = np.argsort(w)
+        w, X = w[order], X[:, order]
     w, X = w[:nroots], X[:, :nroots].T.copy()
     for k in range(nroots):
         m = np.argmax(np.abs(X[k]))
@@ -72,16 +103,24 @@ def _clamp(d):
 def cisd_doubles(eps, B, o, omega, b):
     """CIS(D) doubles B^{ij}_{ab}[i,j,a,b] for one CIS root (Eq. cis_d)."""
     e = np.einsum
+    v = len(eps) - o
+    nq = B.shape[0]
     Bvv, Bvo, Boo = B[:, o:, o:], B[:, o:, :o], B[:, :o, :o]
-    # sum_c b[i,c] (ac|bj) + sum_c b[j,c] (ai|bc)
-    K = e("ic,Qac,Qbj->ijab", b, Bvv, Bvo, optimize=True)
-    K = K + e("jc,Qai,Qbc->ijab", b, Bvo, Bvv, optimize=True)
-    # - sum_l b[l,a] (li|bj) - sum_l b[l,b] (ai|lj)
-    K = K - e("la,Qli,Qbj->ijab", b, Boo, Bvo, optimize=True)
-    K = K - e("lb,Qai,Qlj->ijab", b, Bvo, Boo, optimize=True)
+    # sum_c b[i,c] (ac|bj) - sum_l b[l,a] (li|bj) = sum_Q Z[Q,i,a] B[Q,b,j] with
+    # Z[Q,i,a] = sum_c b[i,c] B[Q,a,c] - sum_l b[l,a] B[Q,l,i]; the other two terms of K
+    # are the same with (i,a) and (j,b) exchanged, using B[Q,a,i] on the left
+    Z = e("ic,Qac->Qia", b, Bvv, optimize=True) - e("la,Qli->Qia", b, Boo, optimize=True)
+    Zm = np.ascontiguousarray(Z).reshape(nq, o * v)
+    Bm = np.ascontiguousarray(Bvo.transpose(0, 2, 1)).reshape(nq, o * v)      # [Q, j, b] = B[Q,b,j]
+    K = _rows_matmul(Zm.T, Bm).reshape(o, v, o, v).transpose(0, 2, 1, 3)       # [i,j,a,b]
+    Bl = np.ascontiguousarray(Bvo.transpose(0, 2, 1)).reshape(nq, o * v)      # [Q, i, a] = B[Q,a,i]
+    K = K + _rows_matmul(Bl.T, Zm).reshape(o, v, o, v).transpose(0, 2, 1, 3)
     eo, ev = eps[:o], eps[o:]
-    d = omega + eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
-    return K / _clamp(d)
+    K = np.ascontiguousarray(K)
+    for i in range(o):        # one occupied index at a time (memory)
+        d = omega + eo[i] + eo[:, None, None] - ev[None, :, None] - ev[None, None, :]
+        K[i] /= _clamp(d)
+    return K
 
 
 def pair_density(Bij, i, j):

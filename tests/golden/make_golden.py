@@ -9,6 +9,8 @@ Calls only oracle/ and the seeded generator.  For a workload it stores:
     block keeps SIGMA_SAMPLES entries at seeded positions instead of all v^2.
 
 Usage: python tests/golden/make_golden.py medium   (about two hours on 8 cores)
+       python tests/golden/make_golden.py large --pno-only
+           (PNO/OSV counts and CIS energies of the large workload, ~10 minutes)
        python tests/golden/make_golden.py medium --sigma-only
            (recomputes only the sigma fields of an existing fixture, ~2 minutes)
 """
@@ -30,6 +32,7 @@ from oracle import ccsd, davidson, eom, hamiltonian as hm, pno  # noqa: E402
 WORKLOADS = {
     "small": dict(o=5, v=20, naux=60, nroots=3, t_pno=1e-7, seed=1, gs="ccsd"),
     "medium": dict(o=20, v=200, naux=600, nroots=6, t_pno=1e-7, seed=2, gs="mp1"),
+    "large": dict(o=60, v=600, naux=1800, nroots=6, t_pno=1e-7, seed=3, gs="mp1"),
 }
 SAMPLE_PAIRS = {"small": [(0, 0), (0, 4), (2, 3), (4, 4)], "medium": [(0, 19), (5, 5), (7, 12), (18, 19), (19, 19)]}
 SIGMA_SAMPLES = 256
@@ -56,6 +59,27 @@ def trial_vector(o, v, seed=123):
     r1 = rng.standard_normal((o, v))
     r2 = rng.standard_normal((o, o, v, v))
     return r1, 0.5 * (r2 + r2.transpose(1, 0, 3, 2))
+
+
+def pno_only(name):
+    """PNO/OSV counts, CIS energies and the occupations nearest the thresholds
+    (oracle PNO construction only; no sigma or solve)."""
+    w = WORKLOADS[name]
+    o = w["o"]
+    t0 = time.time()
+    s = make_system(o, w["v"], w["naux"], w["seed"])
+    sp = pno.PNOSpace(s["eps"], s["B"], o, w["nroots"], w["t_pno"])
+    tp, to = w["t_pno"], w["t_pno"] / 10.0
+    near = lambda ev, t: float(np.min(np.abs(np.log10(np.maximum(np.abs(ev), 1e-300) / t))))
+    out = {"workload": name, **{k: w[k] for k in ("o", "v", "naux", "nroots", "t_pno", "seed", "gs")},
+           "n_ij": sp.n_ij.tolist(), "n_i": sp.n_i.tolist(), "vec_len": int(sp.length),
+           "cis_energies": sp.cis_omega.tolist(),
+           "closest_log10_gap_to_t_pno": min(near(sp.alleig[p], tp) for p in sp.pairs),
+           "closest_log10_gap_to_t_osv": min(near(sp.alleig[(i, i)], to) for i in range(o)),
+           "seconds": time.time() - t0}
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    json.dump(out, open(path, "w"))
+    print(f"wrote {path}: {time.time() - t0:.0f} s", flush=True)
 
 
 def main(name, sigma_only=False):
@@ -97,4 +121,7 @@ def main(name, sigma_only=False):
 
 if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    main(args[0] if args else "small", sigma_only="--sigma-only" in sys.argv)
+    if "--pno-only" in sys.argv:
+        pno_only(args[0])
+    else:
+        main(args[0] if args else "small", sigma_only="--sigma-only" in sys.argv)

@@ -92,9 +92,10 @@ def test_injected_alloc_failure_returns_nomem_without_leak(pkg, ctx, system, aft
     opts = pkg.make_opts(t_pno=1e-6, nroots=3)
     h = ctypes.c_void_p()
     rc = pkg.lib().pno_build(ctx.h, ctypes.byref(sysd), ctypes.byref(opts), None, ctypes.byref(h))
+    msg = pkg.lib().pnoeom_last_error()
     pkg.lib().pnoeom_inject_alloc_failure(-1)
     assert rc == pkg.ERR_NOMEM
-    assert b"injected" in pkg.lib().pnoeom_last_error()
+    assert b"injected" in msg
     assert not h.value
     assert _live(pkg) == before                  # the failed build released what it took
     gp = pkg.PNO(ctx, system["eps"], system["B"], 4, opts=opts)   # and the next build works
