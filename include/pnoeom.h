@@ -55,7 +55,16 @@ enum {
 };
 
 enum { PNOEOM_HOST = 0, PNOEOM_DEVICE = 1 };            /* memory space of pointers */
-enum { PNOEOM_FP64 = 0, PNOEOM_FP32 = 1 };              /* sigma arithmetic */
+/* sigma precision (BASELINE precision policy of the mixed path, Sec. 2 sigma with the
+ * contractions in reduced precision and FP32 accumulation):
+ *   PNOEOM_FP64: FP64 vectors, operator blocks and arithmetic;
+ *   PNOEOM_FP32: FP32 vectors and operator blocks, FP32 arithmetic (the E3 GEMM tiles on
+ *     the tensor cores in 3xTF32);
+ *   PNOEOM_BF16: as FP32, but the dense pair blocks (the 4-virtual and T2 ladders with the
+ *     virtual Fock term, D_p; the singles couplings A_DS and A_S; the occupied global
+ *     blocks) are read from a BF16 copy (rounded to nearest) and multiplied in FP32 with
+ *     FP32 accumulation.  Vectors passed to sigma are float, as for PNOEOM_FP32. */
+enum { PNOEOM_FP64 = 0, PNOEOM_FP32 = 1, PNOEOM_BF16 = 2 };
 
 typedef struct pnoeom_ctx pnoeom_ctx;
 typedef struct pnoeom_pno pnoeom_pno;
@@ -77,11 +86,12 @@ typedef struct {
 /* t_pno: T_CutPNO (occupations >= t_pno kept; 0 keeps the full virtual space);
  * t_osv: T_CutOSV, < 0 means t_pno / 10 (Sec. 3).  nroots_sa: N of the state
  * average (Eq. eom:sa_density); nroots_solve: roots returned by the solver
- * (<= nroots_sa).  precision: PNOEOM_FP64 or PNOEOM_FP32 sigma;
- * refine_fp64: the FP32 phase aims at res_tol and hands over to FP64 sigma when
- * that holds, when its largest residual (below 1e-4) stops halving within three
- * iterations, or when no new direction survives; the FP64 phase then restarts
- * from the N Ritz vectors and runs until the FP64 tolerances hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
+ * (<= nroots_sa).  precision: PNOEOM_FP64, PNOEOM_FP32 or PNOEOM_BF16 sigma;
+ * refine_fp64: the low-precision (FP32 or BF16) phase aims at res_tol and hands over
+ * to FP64 sigma when that holds, when its largest residual (below 1e-4 in FP32, 1e-1 in
+ * BF16) stops halving within three iterations, or when no new direction survives; the
+ * FP64 phase then restarts from the N Ritz vectors and runs until the FP64 tolerances
+ * hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
  * change between iterations; max_subspace <= 0 means 8 * nroots_solve.
  * state_specific: 0 (the default, and the paper's method) builds state-averaged
  * PNOs/OSVs; k in 1..nroots_sa builds them from the CIS(D) pair densities of CIS
@@ -140,7 +150,7 @@ int pno_get_basis(const pnoeom_pno* pno, int pair, double* U, double* fbar);
 
 /* sigma = Hbar R projected into the PNO/OSV spaces (Sec. 2) for nvec packed
  * vectors.  r_dev, s_dev: caller-owned device buffers of nvec * vec_len
- * elements of the chosen precision (double for FP64, float for FP32).
+ * elements: double for PNOEOM_FP64, float for PNOEOM_FP32 and PNOEOM_BF16.
  * Asynchronous on cuda_stream.  Calls on one handle share its scratch (the
  * R-dependent intermediates, grown when a call needs more vectors than any
  * before it): issue them on one stream, or synchronise between calls on
@@ -253,6 +263,12 @@ int pnoeom_server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int
  * vectors on the host (nroots_solve * vec_len doubles). */
 int pno_get_eigenvectors(const pnoeom_pno* pno, double* X);
 
+/* Ritz values of the last davidson_solve on this handle at the moment its
+ * low-precision phase (FP32 or BF16, refine_fp64 set) handed over to the FP64
+ * refinement: the unrefined energies, ascending.  Writes min(n, count) doubles and the
+ * number available in *count (0 when the last solve had no such phase).  Host-only. */
+int pno_solve_lowprec_energies(const pnoeom_pno* pno, int n, double* energies, int* count);
+
 /* Sigma evaluations (one vector of one root each) of the last davidson_solve on
  * this handle, split by the precision they ran in: FP32 (the mixed phase) and
  * FP64 (a plain FP64 solve, or the refinement that follows the FP32 phase).
@@ -308,6 +324,17 @@ int pnoeom_selftest_bounded_wait(pnoeom_ctx* ctx, long long budget_cycles, void*
  * released everything it took. */
 int pnoeom_inject_alloc_failure(long long after);
 int pnoeom_alloc_live_bytes(long long* bytes);
+
+/* Peak rates of the context's device, measured by the library's own microbenchmarks
+ * (the denominators of roofline fractions; no device setting is changed).  Writes up to
+ * nout doubles: [0] FP32 FMA TFLOP/s (SIMT), [1] FP64 FMA TFLOP/s (SIMT), [2] tcgen05
+ * kind::f16 BF16 MMA TFLOP/s, [3] tcgen05 kind::tf32 MMA TFLOP/s (both 128 x 256 tiles,
+ * FP32 accumulation in tensor memory, one CTA per SM), [4] cuBLAS DGEMM TFLOP/s
+ * (n = 4096), [5] cuBLAS DGEMM with the fixed-point FP64 emulation math mode (0 when
+ * unavailable), [6] the largest |emulated - native| / max |native| of that product,
+ * [7] the SM count.  Each rate is the best of a few CUDA-event-timed launches on
+ * cuda_stream.  Blocking; takes a few seconds and about 0.5 GB of device memory. */
+int pnoeom_measure_peaks(pnoeom_ctx* ctx, void* cuda_stream, double* out, int nout);
 
 /* Eigenpairs of a small dense non-symmetric matrix on the host (the Davidson
  * subspace step, Sec. 2).  A: row-major n x n; wr, wi: real and imaginary

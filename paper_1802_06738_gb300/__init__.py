@@ -16,7 +16,7 @@ from .build import build, LIB_PATH  # noqa: F401
 OK = 0
 ERR_INVALID_ARG, ERR_NOMEM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
 HOST, DEVICE = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
 
 
 # kernel classes of the sigma program reported by pno_sigma_timing
@@ -61,7 +61,7 @@ EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", 
            "pnoeom_server_create", "pnoeom_server_destroy", "pnoeom_server_submit", "pnoeom_server_poll",
            "pnoeom_server_wait", "pnoeom_server_stats", "pnoeom_gemm_tf32x3", "pnoeom_device_status",
            "pno_solve_stats", "pnoeom_selftest_bounded_wait", "pnoeom_inject_alloc_failure",
-           "pnoeom_alloc_live_bytes"]
+           "pnoeom_alloc_live_bytes", "pnoeom_measure_peaks", "pno_solve_lowprec_energies"]
 
 
 def lib():
@@ -96,6 +96,7 @@ def lib():
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
         L.pno_solve_stats.argtypes = [vp, i64p, i64p]
+        L.pno_solve_lowprec_energies.argtypes = [vp, i, dp, ip]
         L.pno_get_cis.argtypes = [vp, dp]
         L.pno_get_occupations.argtypes = [vp, dp]
         L.pno_get_cis_vectors.argtypes = [vp, dp]
@@ -106,6 +107,7 @@ def lib():
         L.pnoeom_selftest_bounded_wait.argtypes = [vp, ctypes.c_longlong, vp, ip]
         L.pnoeom_inject_alloc_failure.argtypes = [ctypes.c_longlong]
         L.pnoeom_alloc_live_bytes.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+        L.pnoeom_measure_peaks.argtypes = [vp, vp, dp, i]
         L.pno_set_timing.argtypes = [vp, i]
         L.pno_sigma_timing.argtypes = [vp, i, i, i, ctypes.POINTER(ctypes.c_char_p), ip, dp, dp, dp]
         _lib = L
@@ -153,6 +155,16 @@ class Context:
         N = B.shape[1]
         _check(lib().pnoeom_gemm_tf32x3(self.h, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                                         ctypes.c_void_p(C.data_ptr()), M, N, K, alpha, _stream_ptr(stream)))
+
+    def measure_peaks(self, stream=None):
+        """dict of the device's peak rates measured by the library's microbenchmarks
+        (pnoeom_measure_peaks)."""
+        import numpy as np
+        out = np.zeros(8)
+        _check(lib().pnoeom_measure_peaks(self.h, _stream_ptr(stream), _dptr(out), 8))
+        keys = ["fp32_fma_tflops", "fp64_fma_tflops", "tc_bf16_tflops", "tc_tf32_tflops", "cublas_dgemm_tflops",
+                "cublas_dgemm_emulated_tflops", "dgemm_emulated_max_rel_err", "sm_count"]
+        return dict(zip(keys, map(float, out)))
 
     def device_status(self, clear=True):
         """Status word of the tensor-core kernels (0: every bounded wait completed)."""
@@ -253,7 +265,7 @@ class PNO:
 
     def sigma(self, r, out, precision=FP64, stream=None):
         """sigma for a batch of packed vectors: r, out are CUDA tensors of shape
-        (nvec, length), float64 (FP64) or float32 (FP32)."""
+        (nvec, length), float64 (FP64) or float32 (FP32 and BF16)."""
         nvec = r.shape[0] if r.dim() == 2 else 1
         _check(lib().sigma(self.ctx.h, self.h, nvec, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                            precision, _stream_ptr(stream)))
@@ -300,6 +312,15 @@ class PNO:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(lib().pno_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return dict(fp32=a.value, fp64=b.value)
+
+    def lowprec_energies(self):
+        """Ritz values of the last solve when its FP32/BF16 phase handed over to FP64 (or [])."""
+        import numpy as np
+        n = ctypes.c_int()
+        _check(lib().pno_solve_lowprec_energies(self.h, 0, None, ctypes.byref(n)))
+        e = np.zeros(max(1, n.value))
+        _check(lib().pno_solve_lowprec_energies(self.h, n.value, _dptr(e), ctypes.byref(n)))
+        return e[:n.value]
 
     def eigenvectors(self):
         import numpy as np

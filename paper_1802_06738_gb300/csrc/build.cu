@@ -196,7 +196,122 @@ void eig_lowest(cusolverDnHandle_t h, cudaStream_t s, double* A, double* W, int6
   PN_CHECK(hinfo == 0 && found >= nev, PNOEOM_ERR_CUDA, "partial eigensolver failed (info " + std::to_string(hinfo) + ")");
 }
 
+// Lowest `nev` eigenpairs of a symmetric n x n device matrix A (row-major = column-major)
+// by block Davidson in FP64: start from unit vectors at the smallest diagonal entries,
+// residuals r = A x - theta x preconditioned by 1 / (theta - A_ii) (|.| >= 1e-4), Gram-Schmidt
+// twice, subspace of at most 12 blocks with a restart onto the current Ritz vectors.
+// Converged when every ||r|| <= tol.  Eigenvalues ascending into W (host), eigenvectors
+// into X (device, nev x n row-major).
+void eig_lowest_davidson(cusolverDnHandle_t h, cudaStream_t s, const double* A, int64_t n, int nev, double tol,
+                         double* W, double* X) {
+  const int nb = std::min<int64_t>(n, nev + 4);
+  const int maxsub = (int)std::min<int64_t>(n, 12 * nb);
+  std::vector<double> diag(n);
+  PN_CUDA(cudaMemcpy2DAsync(diag.data(), 8, A, (n + 1) * 8, 8, n, cudaMemcpyDeviceToHost, s));
+  PN_CUDA(cudaStreamSynchronize(s));
+  DBuf<double> V((size_t)maxsub * n), AV((size_t)maxsub * n), T((size_t)nb * n), G((size_t)maxsub * maxsub),
+      Gw(maxsub), C((size_t)maxsub * nb);
+  // V, AV, T store vectors as rows (vector k at k * n)
+  std::vector<int64_t> order(n);
+  for (int64_t e = 0; e < n; ++e) order[e] = e;
+  std::partial_sort(order.begin(), order.begin() + nb, order.end(), [&](int64_t a, int64_t b) { return diag[a] < diag[b]; });
+  {
+    std::vector<double> t((size_t)nb * n, 0.0);
+    for (int k = 0; k < nb; ++k) t[(size_t)k * n + order[k]] = 1.0;
+    V.upload(t.data(), t.size(), s);
+  }
+  auto gemm = [&](const double* a, const double* b, double* c, int M, int N, int K, int lda, int ldb, int ldc, int ta, int tb,
+                  double al, double be) {
+    grouped_gemm<double>({{a, b, c, M, N, K, lda, ldb, ldc, ta, tb, al, be}}, s);
+  };
+  int m = nb;                                     // vectors in V
+  gemm(V.get(), A, AV.get(), m, (int)n, (int)n, (int)n, (int)n, (int)n, 0, 0, 1.0, 0.0);   // AV = V A (A symmetric)
+  std::vector<double> g, ev, res(nb);
+  bool done = false;
+  for (int it = 0; it < 200 && !done; ++it) {
+    gemm(V.get(), AV.get(), G.get(), m, m, (int)n, (int)n, (int)n, m, 0, 1, 1.0, 0.0);       // G = V AV^T
+    eig_dense_sym(h, s, G.get(), Gw.get(), m, 1);                                          // column k = eigenvector k
+    ev.resize(m);
+    Gw.download(ev.data(), m, s);
+    // C (nb x m): the lowest nb eigenvectors as rows
+    g.resize((size_t)m * m);
+    G.download(g.data(), g.size(), s);
+    PN_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> c((size_t)nb * m);
+    for (int k = 0; k < nb; ++k)
+      for (int q = 0; q < m; ++q) c[(size_t)k * m + q] = g[(size_t)k * m + q];
+    C.upload(c.data(), c.size(), s);
+    // Ritz vectors X_k = C V, residuals T_k = C AV - theta_k X_k
+    DBuf<double> Xr((size_t)nb * n);
+    gemm(C.get(), V.get(), Xr.get(), nb, (int)n, m, m, (int)n, (int)n, 0, 0, 1.0, 0.0);
+    gemm(C.get(), AV.get(), T.get(), nb, (int)n, m, m, (int)n, (int)n, 0, 0, 1.0, 0.0);
+    std::vector<double> xr((size_t)nb * n), tr((size_t)nb * n);
+    Xr.download(xr.data(), xr.size(), s);
+    T.download(tr.data(), tr.size(), s);
+    PN_CUDA(cudaStreamSynchronize(s));
+    double worst = 0;
+    for (int k = 0; k < nb; ++k) {
+      double r2 = 0;
+      for (int64_t e = 0; e < n; ++e) {
+        double r = tr[(size_t)k * n + e] - ev[k] * xr[(size_t)k * n + e];
+        tr[(size_t)k * n + e] = r;
+        r2 += r * r;
+      }
+      res[k] = std::sqrt(r2);
+      if (k < nev) worst = std::max(worst, res[k]);
+    }
+    if (worst <= tol) {
+      for (int k = 0; k < nev; ++k) W[k] = ev[k];
+      PN_CUDA(cudaMemcpyAsync(X, Xr.get(), (size_t)nev * n * 8, cudaMemcpyDeviceToDevice, s));
+      done = true;
+      break;
+    }
+    // restart when the next block does not fit
+    if (m + nb > maxsub) {
+      DBuf<double> AX((size_t)nb * n);
+      gemm(C.get(), AV.get(), AX.get(), nb, (int)n, m, m, (int)n, (int)n, 0, 0, 1.0, 0.0);
+      PN_CUDA(cudaMemcpyAsync(V.get(), Xr.get(), (size_t)nb * n * 8, cudaMemcpyDeviceToDevice, s));
+      PN_CUDA(cudaMemcpyAsync(AV.get(), AX.get(), (size_t)nb * n * 8, cudaMemcpyDeviceToDevice, s));
+      m = nb;
+    }
+    // preconditioned residuals, orthogonalised against V (twice) and among themselves
+    int added = 0;
+    for (int k = 0; k < nb; ++k) {
+      if (res[k] <= tol * 1e-3) continue;
+      std::vector<double> tk(n);
+      for (int64_t e = 0; e < n; ++e) {
+        double den = ev[k] - diag[e];
+        if (std::fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
+        tk[e] = tr[(size_t)k * n + e] / den;
+      }
+      DBuf<double> tv(n), ov(m + added);
+      tv.upload(tk.data(), n, s);
+      for (int pass = 0; pass < 2; ++pass) {
+        gemm(V.get(), tv.get(), ov.get(), m + added, 1, (int)n, (int)n, 1, 1, 0, 0, 1.0, 0.0);
+        gemm(V.get(), ov.get(), tv.get(), (int)n, 1, m + added, (int)n, 1, 1, 1, 0, -1.0, 1.0);
+      }
+      tv.download(tk.data(), n, s);
+      PN_CUDA(cudaStreamSynchronize(s));
+      double nrm = 0;
+      for (double x : tk) nrm += x * x;
+      nrm = std::sqrt(nrm);
+      if (nrm < 1e-8) continue;
+      for (double& x : tk) x /= nrm;
+      PN_CUDA(cudaMemcpyAsync(V.get() + (size_t)(m + added) * n, tk.data(), n * 8, cudaMemcpyHostToDevice, s));
+      PN_CUDA(cudaStreamSynchronize(s));
+      ++added;
+    }
+    PN_CHECK(added > 0, PNOEOM_ERR_NOT_CONVERGED, "CIS Davidson: no new direction before convergence");
+    gemm(V.get() + (size_t)m * n, A, AV.get() + (size_t)m * n, added, (int)n, (int)n, (int)n, (int)n, (int)n, 0, 0, 1.0, 0.0);
+    m += added;
+  }
+  PN_CHECK(done, PNOEOM_ERR_NOT_CONVERGED, "CIS Davidson did not converge");
+}
+
 }  // namespace
+
+// Above this many singles the CIS roots come from the Davidson solver above.
+constexpr int64_t CIS_DENSE_MAX = 6000;
 
 // Pool-block bookkeeping on the host.
 struct PoolPlan {
@@ -389,10 +504,16 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     bd.con("Qij", Boo.get(), "Qab", Bvv.get(), "iajb", A.get(), -1.0, 1.0);
     k_cis_diag<<<gsz(ov), 256, 0, s>>>(A.get(), deps.get(), o, v);
     PN_CUDA(cudaGetLastError());
-    eig_lowest(ctx->solver, s, A.get(), W.get(), ov, nr);
     std::vector<double> w(nr);
-    W.download(w.data(), nr, s);
-    PN_CUDA(cudaMemcpyAsync(bcis.data(), A.get(), bcis.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (ov <= CIS_DENSE_MAX) {   // partial dense eigensolve
+      eig_lowest(ctx->solver, s, A.get(), W.get(), ov, nr);
+      W.download(w.data(), nr, s);
+      PN_CUDA(cudaMemcpyAsync(bcis.data(), A.get(), bcis.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    } else {                     // iterative (the dense reduction of a large matrix is slow)
+      DV Xc((size_t)nr * ov);
+      eig_lowest_davidson(ctx->solver, s, A.get(), ov, nr, 1e-11, w.data(), Xc.get());
+      PN_CUDA(cudaMemcpyAsync(bcis.data(), Xc.get(), bcis.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     bd.sync();
     P->cis_omega = w;
     for (int k = 0; k < nr; ++k) {      // normalise 2 sum b^2 = 1, largest entry positive
@@ -421,12 +542,14 @@ void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* 
     for (int k = 0; k < nr; ++k) {
       if (ss > 0 && k != ss - 1) continue;
       b.upload(&bcis[(size_t)k * ov], ov, s);
+      // K^{ij}_{ab} = sum_Q Z[Q,i,a] B[Q,b,j] + sum_Q B[Q,a,i] Z[Q,j,b] with
+      // Z[Q,i,a] = sum_c b[i,c] B[Q,a,c] - sum_l b[l,a] B[Q,l,i]; the second sum is the
+      // first with (i,a) and (j,b) exchanged, so K = M + M^(ij,ab swapped)
       bd.con("ic", b.get(), "Qac", Bvv.get(), "Qia", Z.get());
-      bd.con("Qia", Z.get(), "Qbj", Bvo.get(), "ijab", K.get(), 1.0, 0.0);
-      bd.con("Qai", Bvo.get(), "Qjb", Z.get(), "ijab", K.get(), 1.0, 1.0);
-      bd.con("la", b.get(), "Qli", Boo.get(), "Qia", Z.get());
-      bd.con("Qia", Z.get(), "Qbj", Bvo.get(), "ijab", K.get(), -1.0, 1.0);
-      bd.con("Qai", Bvo.get(), "Qjb", Z.get(), "ijab", K.get(), -1.0, 1.0);
+      bd.con("la", b.get(), "Qli", Boo.get(), "Qia", Z.get(), -1.0, 1.0);
+      bd.con("Qia", Z.get(), "Qbj", Bvo.get(), "ijab", Bt.get(), 1.0, 0.0);
+      PN_CUDA(cudaMemcpyAsync(K.get(), Bt.get(), K.n * 8, cudaMemcpyDeviceToDevice, s));
+      bd.perm(Bt.get(), K.get(), {O, O, V, V}, {1, 0, 3, 2}, 1.0, 1.0);
       k_pair_div<<<gsz(K.n), 256, 0, s>>>(K.get(), deps.get(), o, v, P->cis_omega[k], 1e-4);
       PN_CUDA(cudaGetLastError());
       bd.perm(K.get(), Bt.get(), {O, O, V, V}, {0, 1, 3, 2}, -1.0, 0.0);   // Bt^{ij} = 2 B^{ij} - (B^{ij})^T

@@ -86,6 +86,16 @@ __global__ void k_add_block(double* out, int64_t ldo, const double* X, int64_t l
   }
 }
 
+// flag = 1 when B[Q][a][b] != B[Q][b][a] for some entry (bitwise comparison)
+__global__ void k_asym_flag(int* flag, const double* B, int nq, int v) {
+  GRID_STRIDE(e, (int64_t)nq * v * v) {
+    const int64_t q = e / ((int64_t)v * v);
+    const int r = (int)(e % ((int64_t)v * v));
+    const int a = r / v, b = r % v;
+    if (a < b && B[e] != B[(q * v + b) * v + a]) *flag = 1;
+  }
+}
+
 struct Prog {
   pnoeom_pno* P;
   cudaStream_t s;
@@ -175,6 +185,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   const bool t1 = P->has_t1;
 
   // ---- integral blocks (dressed), Mulliken (pq|rs) = sum_Q B_pq B_rs ------------
+  // Only integrals with at most two virtual indices are formed in full (o^2 v^2 at most);
+  // everything with three or four virtual indices enters through the DF factors, already
+  // contracted with PNO/OSV bases (the "projected-first" routes below).
   DV g_ovov(O * V * O * V), g_oovv(O * O * V * V), g_voov(V * O * O * V), g_oooo(O * O * O * O), g_ooov(O * O * O * V),
       g_ovoo(O * V * O * O), g_oovo(O * O * V * O), g_vooo(V * O * O * O);
   G.con("Qkc", dBov.get(), "Qld", dBov.get(), "kcld", g_ovov.get());
@@ -185,24 +198,34 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   G.con("Qkc", dBov.get(), "Qlj", dBoo.get(), "kclj", g_ovoo.get());
   G.con("Qki", dBoo.get(), "Qbj", dBvo.get(), "kibj", g_oovo.get());
   G.con("Qai", dBvo.get(), "Qkj", dBoo.get(), "aikj", g_vooo.get());
-  DV L_ovov(g_ovov.n);
-  G.perm(g_ovov.get(), L_ovov.get(), {O, V, O, V}, {0, 3, 2, 1}, -1.0);
-  axpby<double>(L_ovov.get(), g_ovov.get(), 2.0, 1.0, L_ovov.n, s);
+  // gS[k,c,l,d] = (kd|lc): g_ovov with its two virtual indices exchanged; L = 2 g - gS
+  DV gS(g_ovov.n), L_ovov(g_ovov.n);
+  G.perm(g_ovov.get(), gS.get(), {O, V, O, V}, {0, 3, 2, 1});
+  PN_CUDA(cudaMemcpyAsync(L_ovov.get(), gS.get(), gS.n * 8, cudaMemcpyDeviceToDevice, s));
+  axpby<double>(L_ovov.get(), g_ovov.get(), 2.0, -1.0, L_ovov.n, s);
   const double* t = t2.get();
   const double* u = u2.get();
+  // uS[x,l,d,a] = u[x,l,a,d]: rows (l,d), columns a, so that sum_a u[x,l,a,d] U[a,A] is one GEMM
+  DV uS(u2.n);
+  G.perm(u, uS.get(), {O, O, V, V}, {0, 1, 3, 2});
+  // the dressed B_vv is symmetric in its two virtual indices unless T1 dressed it
+  bool bsym = !t1;
+  if (bsym) {
+    DBuf<int> flag(1);
+    flag.zero(s);
+    k_asym_flag<<<gsz(dBvv.n), 256, 0, s>>>(flag.get(), dBvv.get(), naux, v);
+    PN_CUDA(cudaGetLastError());
+    int h = 0;
+    flag.download(&h, 1, s);
+    G.sync();
+    bsym = h == 0;
+  }
 
   tm.mark("  integral blocks");
   // ---- R-independent intermediates ------------------------------------------------
   DV W(O * O * O * O);       // W[k,i,l,j] = (ki|lj) + sum_cd t^{cd}_{ij} (kc|ld)
   PN_CUDA(cudaMemcpyAsync(W.get(), g_oooo.get(), W.n * 8, cudaMemcpyDeviceToDevice, s));
   G.con("ijcd", t, "kcld", g_ovov.get(), "kilj", W.get(), 1.0, 1.0);
-  DV Wc(O * O * V * V);      // Wc[k,i,a,c] = (ki|ac) - 1/2 sum_dl t^{ad}_{li} (kd|lc)
-  PN_CUDA(cudaMemcpyAsync(Wc.get(), g_oovv.get(), Wc.n * 8, cudaMemcpyDeviceToDevice, s));
-  G.con("liad", t, "kdlc", g_ovov.get(), "kiac", Wc.get(), -0.5, 1.0);
-  DV Wd(V * O * O * V);      // Wd[a,i,k,c] = L_aikc + 1/2 sum_dl u^{ad}_{il} L_ldkc
-  G.perm(g_oovv.get(), Wd.get(), {O, O, V, V}, {2, 1, 0, 3}, -1.0);
-  axpby<double>(Wd.get(), g_voov.get(), 2.0, 1.0, Wd.n, s);
-  G.con("ilad", u, "ldkc", L_ovov.get(), "aikc", Wd.get(), 0.5, 1.0);
   DV FvvI(V * V), FooI(O * O);
   FvvI.upload(Fvv.data(), Fvv.size(), s);
   FooI.upload(Foo.data(), Foo.size(), s);
@@ -210,108 +233,98 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   G.con("ljcd", u, "kdlc", g_ovov.get(), "kj", FooI.get(), 1.0, 1.0);
   std::vector<double> FooI_h(O * O);
   FooI.download(FooI_h.data(), FooI_h.size(), s);
-  DV Zt(O * O * V * V), Zd(O * O * V * V);   // Z[l,j,d,b], Zd[l,j,d,b]
-  G.con("kdlc", g_ovov.get(), "kjbc", t, "ljdb", Zt.get());
-  G.con("ldkc", L_ovov.get(), "jkbc", u, "ljdb", Zd.get());
-  // singles-singles block (canonical), see the singles part of the derivative residual
-  DV Acan(O * V * O * V), X1(O * O), Y1s(V * V);
+  // singles-singles diagonal parts: Xv = Fvv - sum u (kd|lc), Xo = Foo + sum u (md|kc)
+  DV X1(O * O), Y1s(V * V), Xv(V * V);
   G.con("kicd", u, "mdkc", g_ovov.get(), "mi", X1.get());
   G.con("klac", u, "kdlc", g_ovov.get(), "ad", Y1s.get());
-  G.con("ikac", u, "kcmd", L_ovov.get(), "iamd", Acan.get());
-  G.perm(g_voov.get(), Acan.get(), {V, O, O, V}, {1, 0, 2, 3}, 2.0, 1.0);
-  G.perm(g_oovv.get(), Acan.get(), {O, O, V, V}, {1, 2, 0, 3}, -1.0, 1.0);
-  {
-    DV Xv(V * V), Xo(O * O);
-    Xv.upload(Fvv.data(), Fvv.size(), s);
-    axpby<double>(Xv.get(), Y1s.get(), -1.0, 1.0, Xv.n, s);
-    Xo.upload(Foo.data(), Foo.size(), s);
-    axpby<double>(Xo.get(), X1.get(), 1.0, 1.0, Xo.n, s);
-    k_acan_delta<<<gsz(Acan.n), 256, 0, s>>>(Acan.get(), Xv.get(), Xo.get(), o, v);
-    PN_CUDA(cudaGetLastError());
-    G.sync();
-  }
-  tm.mark("  o^2v^2 intermediates");
-  // v^3 o blocks
-  DV g_vvov(V * V * O * V);    // (ad|kc) at [a,d,k,c]
-  G.con("Qad", dBvv.get(), "Qkc", dBov.get(), "adkc", g_vvov.get());
-  DV Y1(O * O * O * V), Y2(O * O * V * O);
-  G.con("ijcd", t, "bdkc", g_vvov.get(), "ijkb", Y1.get());
-  G.con("ijcd", t, "ackd", g_vvov.get(), "ijak", Y2.get());
-  // Singles -> doubles couplings through the v^3 o integrals, contracted with r1 (OSV index D):
-  //   Qa[y; d,a,b] = sum_kc [(ad|kc) - 1/2 (ac|kd)] u[y,k,b,c] - 1/2 sum_kc (ac|kd) t[k,y,b,c]
-  //   Q1[x; d,a,b] = sum_kc (ac|kd) t[k,x,b,c]
-  // are only needed projected (d on an OSV space, a and b on a pair's PNO space), so the OSV
-  // projection of d is applied to the integrals first (per occupied z):
-  //   Gz[a,D,k,c] = sum_d U^z[d,D] ((ad|kc) - 1/2 (ac|kd)),  Hz[a,D,k,c] = sum_d U^z[d,D] (ac|kd),
-  // and the PNO projection of b to the amplitudes (per pair), see the pair loop below.
-  std::vector<DV> Gz(O), Hz(O);
-  {
-    DV G34(g_vvov.n);
-    G.perm(g_vvov.get(), G34.get(), {V, V, O, V}, {0, 3, 2, 1}, -0.5);
-    axpby<double>(G34.get(), g_vvov.get(), 1.0, 1.0, G34.n, s);
-    for (int z = 0; z < o; ++z) {
-      const int nz = G.no(z);
-      if (!nz) continue;
-      Dims d = G.dm;
-      d['D'] = nz;
-      Gz[z].alloc((size_t)V * nz * O * V);
-      Hz[z].alloc((size_t)V * nz * O * V);
-      G.con(d, "adkc", G34.get(), "dD", G.Uo(z), "aDkc", Gz[z].get());
-      G.con(d, "ackd", g_vvov.get(), "dD", G.Uo(z), "aDkc", Hz[z].get());
-    }
-  }
-  DV tY(O * O * V * V);   // tY[y][k][b][c] = t[k,y,b,c]
-  G.perm(t, tY.get(), {O, O, V, V}, {1, 0, 2, 3});
-  DV Qb(O * O * O * V);
-  {
-    DV Q2(Qb.n), Q5(Qb.n), Q6(Qb.n);
-    G.con("kimc", g_ooov.get(), "kjbc", t, "mijb", Q2.get());
-    G.con("mikc", g_ooov.get(), "jkbc", u, "mijb", Q5.get());
-    G.con("mcki", g_ovoo.get(), "jkbc", u, "mijb", Q6.get());
-    G.perm(Q2.get(), Qb.get(), {O, O, O, V}, {0, 2, 1, 3});
-    axpby<double>(Qb.get(), Q2.get(), 0.5, 1.0, Qb.n, s);
-    axpby<double>(Qb.get(), Q5.get(), -1.0, 1.0, Qb.n, s);
-    axpby<double>(Qb.get(), Q6.get(), 0.5, 1.0, Qb.n, s);
-    G.sync();
-  }
-  // permuted copies used per pair
-  DV gvvov_k(g_vvov.n);                 // [k][a][d][c]
-  G.perm(g_vvov.get(), gvvov_k.get(), {V, V, O, V}, {2, 0, 1, 3});
-  DV Lv_m(g_vvov.n);                    // Lvvov[b,c,m,d] = 2 (bc|md) - (bd|mc), stored [m][b][c][d]
-  {
-    DV Lvvov(g_vvov.n);
-    G.perm(g_vvov.get(), Lvvov.get(), {V, V, O, V}, {0, 3, 2, 1}, -1.0);
-    axpby<double>(Lvvov.get(), g_vvov.get(), 2.0, 1.0, Lvvov.n, s);
-    G.perm(Lvvov.get(), Lv_m.get(), {V, V, O, V}, {2, 0, 1, 3});
-    G.sync();
-  }
-  g_vvov.release();
-  DV gvvvo_j(V * V * V * O);           // (ac|bj) stored [j][a][c][b]
-  {
-    DV g_vvvo(V * V * V * O);
-    G.con("Qac", dBvv.get(), "Qbj", dBvo.get(), "acbj", g_vvvo.get());
-    G.perm(g_vvvo.get(), gvvvo_j.get(), {V, V, V, O}, {3, 0, 1, 2});
-    G.sync();
-  }
+  Xv.upload(Fvv.data(), Fvv.size(), s);
+  axpby<double>(Xv.get(), Y1s.get(), -1.0, 1.0, Xv.n, s);
+  std::vector<double> Xo_h(O * O);
+  X1.download(Xo_h.data(), Xo_h.size(), s);
+  G.sync();
+  for (int e = 0; e < o * o; ++e) Xo_h[e] += Foo[e];
+  // small occupied-heavy blocks
   DV govoo_j(O * O * V * O);           // (kc|lj) stored [j][k][c][l]
   G.perm(g_ovoo.get(), govoo_j.get(), {O, V, O, O}, {3, 0, 1, 2});
   DV gooov_i(O * O * O * V);           // (ki|lc) stored [i][k][l][c]
   G.perm(g_ooov.get(), gooov_i.get(), {O, O, O, V}, {1, 0, 2, 3});
-  DV wa_can(O * O * O * V), wb_can(O * O * O * V);   // [i][j][k][b], [i][j][k][a]
+  DV wa_can(O * O * O * V), wb_can(O * O * O * V);   // (ki|bj) at [i][j][k][b], (ai|kj) at [i][j][k][a]
   G.perm(g_oovo.get(), wa_can.get(), {O, O, V, O}, {1, 3, 0, 2});
-  axpby<double>(wa_can.get(), Y1.get(), 1.0, 1.0, wa_can.n, s);
   G.perm(g_vooo.get(), wb_can.get(), {V, O, O, O}, {1, 3, 2, 0});
-  G.perm(Y2.get(), wb_can.get(), {O, O, V, O}, {0, 1, 3, 2}, 1.0, 1.0);
-  DV Qb_xy(O * O * O * V);             // Qb[m,x,y,b] stored [x][y][m][b]
-  G.perm(Qb.get(), Qb_xy.get(), {O, O, O, V}, {1, 2, 0, 3});
   DV Gam_can(O * O * O * V);           // [y][k][m][d] = 2 (ky|md) - (kd|my)
   G.perm(g_ooov.get(), Gam_can.get(), {O, O, O, V}, {1, 0, 2, 3}, 2.0);
   G.perm(g_ovoo.get(), Gam_can.get(), {O, V, O, O}, {3, 0, 2, 1}, -1.0, 1.0);
-  DV Wdp(Wd.n);                        // Wd[a,i,k,c] stored [i][k][a][c]
-  G.perm(Wd.get(), Wdp.get(), {V, O, O, V}, {1, 2, 0, 3});
-  G.sync();
+  DV G2q(O * O * O * V), G6q(O * O * O * V);   // G2q[i][m][k][c] = (ki|mc), G6q[x][m][k][c] = (mc|kx)
+  G.perm(g_ooov.get(), G2q.get(), {O, O, O, V}, {1, 2, 0, 3});
+  G.perm(g_ovoo.get(), G6q.get(), {O, V, O, O}, {3, 0, 2, 1});
+  DV BvoT(O * N * V);                  // BvoT[j][Q][b] = B[Q,b,j]
+  G.perm(dBvo.get(), BvoT.get(), {N, V, O}, {2, 0, 1});
+  // OSV factors: Uocat (v x L1) = all OSV bases side by side; BUo[Q,a,L] = sum_d Bvv[Q,a,d] Uocat[d,L];
+  // BoU[Q,k,L] = sum_d Bov[Q,k,d] Uocat[d,L]
+  DV Uocat(std::max<int64_t>(1, V * L1)), BUo(std::max<int64_t>(1, N * V * L1)), BoU(std::max<int64_t>(1, N * O * L1));
+  if (L1 > 0) {
+    for (int m = 0; m < o; ++m)
+      if (G.no(m))
+        PN_CUDA(cudaMemcpy2DAsync(Uocat.get() + P->off_i[m], L1 * 8, G.Uo(m), G.no(m) * 8, G.no(m) * 8, V,
+                                  cudaMemcpyDeviceToDevice, s));
+    Dims d = G.dm;
+    d['L'] = L1;
+    G.con(d, "Qad", dBvv.get(), "dL", Uocat.get(), "QaL", BUo.get());
+    G.con(d, "Qkd", dBov.get(), "dL", Uocat.get(), "QkL", BoU.get());
+  }
+  // columns of OSV m of a [rows][L1] factor, gathered into a contiguous [rows][n_m] buffer
+  auto osv_cols = [&](const double* F, int64_t rows, int m, DV& out) {
+    out.alloc(std::max<int64_t>(1, rows * G.no(m)));
+    if (G.no(m))
+      PN_CUDA(cudaMemcpy2DAsync(out.get(), G.no(m) * 8, F + P->off_i[m], L1 * 8, G.no(m) * 8, rows,
+                                cudaMemcpyDeviceToDevice, s));
+  };
 
-  tm.mark("  v^3 o intermediates");
+  tm.mark("  o^2v^2 intermediates");
+  // ---- projected amplitude and integral factors of the ring terms ---------------------------
+  // For every pair {x, y} with PNOs and each of its occupied indices x, four (ov x n) factors
+  // with rows (l, d):
+  //   TU[x]: sum_a t[l,x,a,d] U[a,A]      UU[x]: sum_a u[x,l,a,d] U[a,A]
+  //   GU[x]: sum_c (xd|lc) U[c,C]          LU[x]: sum_c L[l,d,x,c] U[c,C]
+  // stored, for each occupied y, side by side over x ("cat" layout of y: column block of
+  // pair {x, y} at coff[y][x], clen[y] columns in all).
+  std::vector<std::vector<int64_t>> coff(o, std::vector<int64_t>(o, -1));
+  std::vector<int64_t> clen(o, 0), cbase(o + 1, 0);
+  for (int y = 0; y < o; ++y)
+    for (int x = 0; x < o; ++x)
+      if (G.n(x, y)) { coff[y][x] = clen[y]; clen[y] += G.n(x, y); }
+  const int64_t OV = O * V;
+  for (int y = 0; y < o; ++y) cbase[y + 1] = cbase[y] + OV * clen[y];
+  DV TUc(std::max<int64_t>(1, cbase[o])), UUc(std::max<int64_t>(1, cbase[o])), GUc(std::max<int64_t>(1, cbase[o])),
+      LUc(std::max<int64_t>(1, cbase[o]));
+  {
+    std::vector<GemmProb<double>> pr;
+    for (int y = 0; y < o; ++y)
+      for (int x = 0; x < o; ++x) {
+        const int nn = G.n(x, y);
+        if (!nn) continue;
+        const int64_t co = cbase[y] + coff[y][x];
+        const int ld = (int)clen[y];
+        const double* Uq = G.U(x, y);
+        pr.push_back({t + (int64_t)x * OV * V, Uq, TUc.get() + co, (int)OV, nn, v, v, nn, ld, 0, 0, 1.0, 0.0});
+        pr.push_back({uS.get() + (int64_t)x * OV * V, Uq, UUc.get() + co, (int)OV, nn, v, v, nn, ld, 0, 0, 1.0, 0.0});
+        pr.push_back({gS.get() + (int64_t)x * V * OV, Uq, GUc.get() + co, (int)OV, nn, v, (int)OV, nn, ld, 1, 0, 1.0, 0.0});
+        pr.push_back({L_ovov.get() + (int64_t)x * V * OV, Uq, LUc.get() + co, (int)OV, nn, v, (int)OV, nn, ld, 1, 0, 1.0, 0.0});
+      }
+    grouped_gemm<double>(pr, s);
+  }
+  // column block of pair {x, y} (x being the amplitude's or integral's own index) as a
+  // contiguous (ov x n) buffer
+  auto cat_block = [&](const DV& F, int x, int y, DV& out) {
+    const int nn = G.n(x, y);
+    out.alloc(std::max<int64_t>(1, OV * nn));
+    if (nn)
+      PN_CUDA(cudaMemcpy2DAsync(out.get(), nn * 8, F.get() + cbase[y] + coff[y][x], clen[y] * 8, nn * 8, OV,
+                                cudaMemcpyDeviceToDevice, s));
+  };
+  gS.release();
+
+  tm.mark("  ring factors");
   // ---- pool layout ------------------------------------------------------------------
   auto nP = [&](int p) { return (int64_t)P->nij[p]; };
   int64_t pool = 0;
@@ -324,26 +337,38 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   const int64_t off_Ucat = take(V * nsum);
   std::vector<int64_t> offS((size_t)npairs * npairs);
   for (int p = 0; p < npairs; ++p) for (int q = 0; q < npairs; ++q) offS[(size_t)p * npairs + q] = take(nP(p) * nP(q));
-  auto idx3 = [&](int a, int b, int c) { return ((size_t)a * o + b) * o + c; };
-  std::vector<int64_t> offMC(O * O * O), offMD(O * O * O), offMZ(O * O * O), offMZd(O * O * O);
-  for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) for (int k = 0; k < o; ++k) {
-    offMC[idx3(i, j, k)] = take((int64_t)G.n(i, j) * G.n(k, j));
-    offMD[idx3(i, j, k)] = take((int64_t)G.n(i, j) * G.n(j, k));
-    offMZ[idx3(k, i, j)] = take((int64_t)G.n(k, i) * G.n(i, j));
-    offMZd[idx3(k, i, j)] = take((int64_t)G.n(i, k) * G.n(i, j));
+  // ring blocks, one (clen[y] x clen[y]) matrix per occupied y and family:
+  //   MC[i,j,k] = U(i,j)^T Wc[k,i] U(k,j)  at block (i, k) of y = j
+  //   MD[i,j,k] = U(i,j)^T Wd[.,i,k,.] U(j,k)  at block (i, k) of y = j
+  //   MZ[k,i,j] = U(k,i)^T Zt[k,j] U(i,j)  at block (k, j) of y = i
+  //   MZd[k,i,j] = U(i,k)^T Zd[k,j] U(i,j)  at block (k, j) of y = i
+  std::vector<int64_t> offMCc(o), offMDc(o), offMZc(o), offMZdc(o);
+  for (int y = 0; y < o; ++y) {
+    offMCc[y] = take(clen[y] * clen[y]);
+    offMDc[y] = take(clen[y] * clen[y]);
+    offMZc[y] = take(clen[y] * clen[y]);
+    offMZdc[y] = take(clen[y] * clen[y]);
   }
+  auto ring_off = [&](const std::vector<int64_t>& base, int y, int r, int c) {
+    return base[y] + coff[y][r] * clen[y] + coff[y][c];
+  };
+  // blocks read by the GEMV kernel start on POOL_ALIGN-element boundaries and have leading
+  // dimensions rounded up to POOL_ALIGN (the padding stays zero)
+  auto pad = [](int64_t x) { return (x + POOL_ALIGN - 1) / POOL_ALIGN * POOL_ALIGN; };
+  auto take_al = [&](int64_t n) { pool = pad(pool); return take(n); };
+  const int64_t L1p = pad(L1), Lp = pad(L), Op = pad(O);
   std::vector<int64_t> offGh(O * O), offTh(O * O), offG4(O * O), offT4(O * O);
   for (int x = 0; x < o; ++x) for (int y = 0; y < o; ++y) {
     int64_t nn = G.n(x, y);
     offGh[x * o + y] = take(nn * V);
     offTh[x * o + y] = take(nn * V);
-    offG4[x * o + y] = take(O * nn * nn);
-    offT4[x * o + y] = take(nn * nn * O);
+    offG4[x * o + y] = take_al(O * pad(nn * nn));
+    offT4[x * o + y] = take_al(nn * nn * Op);
   }
-  std::vector<int64_t> offD(npairs), offADS(npairs), offAS(o);
-  for (int p = 0; p < npairs; ++p) offD[p] = take(nP(p) * nP(p) * nP(p) * nP(p));
-  for (int p = 0; p < npairs; ++p) offADS[p] = take(nP(p) * nP(p) * L1);
-  for (int i = 0; i < o; ++i) offAS[i] = take((int64_t)G.no(i) * L);
+  std::vector<int64_t> offD(npairs), offADS(npairs);
+  for (int p = 0; p < npairs; ++p) offD[p] = take_al(nP(p) * nP(p) * pad(nP(p) * nP(p)));
+  for (int p = 0; p < npairs; ++p) offADS[p] = take_al(nP(p) * nP(p) * L1p);
+  const int64_t off_AS = take_al(L1 * Lp);     // singles rows: row off_i[i] + A of OSV i, ld Lp
   P->pool64.alloc(std::max<int64_t>(1, pool), fp);
   P->pool64.zero(s);
   double* pl = P->pool64.get();
@@ -368,20 +393,42 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
 
   tm.mark("  overlaps");
   // ---- mixed-pair ring blocks -------------------------------------------------------------
+  // rank-(ov) parts, one GEMM per occupied y and family (Wc, Wd, Zt, Zd reassociated:
+  //   -1/2 sum_{l,d} t[l,i,a,d] (kd|lc) -> -1/2 TU[i]^T GU[k];  1/2 sum u[i,l,a,d] L[l,d,k,c] -> 1/2 UU[i]^T LU[k];
+  //   Zt[k,j][d,b] = sum (md|kc) t[m,j,b,c] -> GU[k]^T TU[j];  Zd[k,j][d,b] = sum L[k,d,m,c] u[j,m,b,c] -> LU[k]^T UU[j])
   {
-    std::vector<Prog::PJ> jobs;
-    const int64_t vv = V * V;
-    for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) for (int k = 0; k < o; ++k) {
-      jobs.push_back({G.U(i, j), G.n(i, j), Wc.get() + ((int64_t)k * o + i) * vv, v, 0, G.U(k, j), G.n(k, j),
-                      pl + offMC[idx3(i, j, k)], G.n(k, j), 1.0, 0.0});
-      jobs.push_back({G.U(i, j), G.n(i, j), Wdp.get() + ((int64_t)i * o + k) * vv, v, 0, G.U(j, k), G.n(j, k),
-                      pl + offMD[idx3(i, j, k)], G.n(j, k), 1.0, 0.0});
-      jobs.push_back({G.U(k, i), G.n(k, i), Zt.get() + ((int64_t)k * o + j) * vv, v, 0, G.U(i, j), G.n(i, j),
-                      pl + offMZ[idx3(k, i, j)], G.n(i, j), 1.0, 0.0});
-      jobs.push_back({G.U(i, k), G.n(i, k), Zd.get() + ((int64_t)k * o + j) * vv, v, 0, G.U(i, j), G.n(i, j),
-                      pl + offMZd[idx3(k, i, j)], G.n(i, j), 1.0, 0.0});
+    std::vector<GemmProb<double>> pr;
+    for (int y = 0; y < o; ++y) {
+      const int cl = (int)clen[y];
+      if (!cl) continue;
+      const int64_t b = cbase[y];
+      pr.push_back({TUc.get() + b, GUc.get() + b, pl + offMCc[y], cl, cl, (int)OV, cl, cl, cl, 1, 0, -0.5, 0.0});
+      pr.push_back({UUc.get() + b, LUc.get() + b, pl + offMDc[y], cl, cl, (int)OV, cl, cl, cl, 1, 0, 0.5, 0.0});
+      pr.push_back({GUc.get() + b, TUc.get() + b, pl + offMZc[y], cl, cl, (int)OV, cl, cl, cl, 1, 0, 1.0, 0.0});
+      pr.push_back({LUc.get() + b, UUc.get() + b, pl + offMZdc[y], cl, cl, (int)OV, cl, cl, cl, 1, 0, 1.0, 0.0});
     }
-    G.project(jobs);
+    grouped_gemm<double>(pr, s);
+    GUc.release();
+    LUc.release();
+    // one-integral parts: MC += U(i,j)^T (ki|ac) U(k,j); MD += U(i,j)^T (2 (ai|kc) - (ki|ac)) U(j,k)
+    // (jobs writing the same block go to separate calls)
+    std::vector<Prog::PJ> j1, j2;
+    const int64_t vv = V * V;
+    for (int j = 0; j < o; ++j)
+      for (int i = 0; i < o; ++i) {
+        if (!G.n(i, j)) continue;
+        for (int k = 0; k < o; ++k) {
+          if (!G.n(k, j)) continue;
+          j1.push_back({G.U(i, j), G.n(i, j), g_oovv.get() + ((int64_t)k * o + i) * vv, v, 0, G.U(k, j), G.n(k, j),
+                        pl + ring_off(offMCc, j, i, k), (int)clen[j], 1.0, 1.0});
+          j1.push_back({G.U(i, j), G.n(i, j), g_voov.get() + (int64_t)i * OV + (int64_t)k * V, (int)(O * O * V), 0,
+                        G.U(j, k), G.n(j, k), pl + ring_off(offMDc, j, i, k), (int)clen[j], 2.0, 1.0});
+          j2.push_back({G.U(i, j), G.n(i, j), g_oovv.get() + ((int64_t)k * o + i) * vv, v, 0, G.U(j, k), G.n(j, k),
+                        pl + ring_off(offMDc, j, i, k), (int)clen[j], -1.0, 1.0});
+        }
+      }
+    G.project(j1);
+    G.project(j2);
   }
   tm.mark("  ring blocks");
   // ---- E3 / E4 blocks ---------------------------------------------------------------------------
@@ -400,10 +447,11 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     std::vector<Prog::PJ> jobs;
     for (int l = 0; l < o; ++l) for (int j = 0; j < o; ++j) {
       int nn = G.n(l, j);
+      if (!nn) continue;
       // G4 rows k: U(l,j)^T X_k U(l,j), X_k[c,d] = (kd|lc)
       for (int k = 0; k < o; ++k)
         jobs.push_back({G.U(l, j), nn, g_ovov.get() + (int64_t)k * V * O * V + (int64_t)l * V, o * v, 1, G.U(l, j), nn,
-                        pl + offG4[l * o + j] + (int64_t)k * nn * nn, nn, 1.0, 0.0});
+                        pl + offG4[l * o + j] + (int64_t)k * pad(nn * nn), nn, 1.0, 0.0});
     }
     G.project(jobs);
   }
@@ -414,6 +462,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) {
       int nn = G.n(i, j);
       tb3[i * o + j].alloc(std::max<int64_t>(1, O * nn * nn));
+      if (!nn) continue;
       for (int k = 0; k < o; ++k)
         jobs.push_back({G.U(i, j), nn, t + ((int64_t)i * o + k) * V * V, v, 0, G.U(i, j), nn,
                         tb3[i * o + j].get() + (int64_t)k * nn * nn, nn, 1.0, 0.0});
@@ -421,7 +470,10 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     G.project(jobs);
     for (int i = 0; i < o; ++i) for (int j = 0; j < o; ++j) {
       int64_t nn = G.n(i, j);
-      if (nn) G.perm(tb3[i * o + j].get(), pl + offT4[i * o + j], {O, nn * nn}, {1, 0});
+      if (!nn) continue;
+      DV tmp(nn * nn * O);
+      G.perm(tb3[i * o + j].get(), tmp.get(), {O, nn * nn}, {1, 0});
+      PN_CUDA(cudaMemcpy2DAsync(pl + offT4[i * o + j], Op * 8, tmp.get(), O * 8, O * 8, nn * nn, cudaMemcpyDeviceToDevice, s));
     }
   }
 
@@ -429,12 +481,31 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   // R1 column blocks shared by all pairs: Lv1[b,c,(m,D)] = sum_d (2 (bc|md) - (bd|mc)) U^m[d,D],
   // GamAll[y][k][(m,D)] = sum_d (2 (ky|md) - (kd|my)) U^m[d,D]
   DV Lv1(std::max<int64_t>(1, V * V * L1)), GamAll(std::max<int64_t>(1, O * O * L1));
-  {
+  if (L1 > 0) {
+    Dims d = G.dm;
+    d['L'] = L1;
+    {   // 2 (bc|md) U^m: 2 sum_Q B[Q,b,c] BoU[Q,m,(m,D)]
+      DV QL(N * L1);
+      for (int m = 0; m < o; ++m)
+        if (G.no(m))
+          PN_CUDA(cudaMemcpy2DAsync(QL.get() + P->off_i[m], L1 * 8, BoU.get() + (int64_t)m * L1 + P->off_i[m], O * L1 * 8,
+                                    G.no(m) * 8, N, cudaMemcpyDeviceToDevice, s));
+      G.con(d, "Qbc", dBvv.get(), "QL", QL.get(), "bcL", Lv1.get(), 2.0, 0.0);
+    }
+    for (int m = 0; m < o; ++m) {   // - (bd|mc) U^m: - sum_Q BUo[Q,b,(m,D)] B[Q,m,c]
+      const int nm = G.no(m);
+      if (!nm) continue;
+      Dims dm2 = G.dm;
+      dm2['D'] = nm;
+      DV BUm, Bm(N * V), tmp(V * V * nm);
+      osv_cols(BUo.get(), N * V, m, BUm);
+      PN_CUDA(cudaMemcpy2DAsync(Bm.get(), V * 8, dBov.get() + (int64_t)m * V, OV * 8, V * 8, N, cudaMemcpyDeviceToDevice, s));
+      G.con(dm2, "QbD", BUm.get(), "Qc", Bm.get(), "bcD", tmp.get());
+      G.add_block(Lv1.get() + P->off_i[m], L1, tmp.get(), nm, (int)(V * V), nm, -1.0);
+    }
     std::vector<GemmProb<double>> pr;
     for (int m = 0; m < o; ++m) {
       if (!G.no(m)) continue;
-      pr.push_back({Lv_m.get() + (int64_t)m * V * V * V, G.Uo(m), Lv1.get() + P->off_i[m], v * v, G.no(m), v, v, G.no(m),
-                    (int)L1, 0, 0, 1.0, 0.0});
       for (int y = 0; y < o; ++y)
         pr.push_back({Gam_can.get() + (int64_t)y * O * O * V + (int64_t)m * V, G.Uo(m), GamAll.get() + (int64_t)y * O * L1 + P->off_i[m],
                       o, G.no(m), v, o * v, G.no(m), (int)L1, 0, 0, 1.0, 0.0});
@@ -442,7 +513,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     grouped_gemm<double>(pr, s);
   }
 
-  // ---- pair-diagonal dense blocks D_p --------------------------------------------------------
+  tm.mark("  singles factors");
+  // ---- pair-diagonal dense blocks D_p, singles -> doubles blocks A_DS_p, V_bar rows ------
+  double* AS = pl + off_AS;
   for (int p = 0; p < npairs; ++p) {
     const int i = P->pair_i[p], j = P->pair_j[p];
     const int nn = (int)nP(p);
@@ -450,58 +523,105 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     const double* Up = G.U(i, j);
     Dims d = G.dm;
     for (char c : std::string("ABCD")) d[c] = nn;
-    DV Bb(N * nn * nn);
-    {
-      std::vector<Prog::PJ> jobs;
-      for (int q = 0; q < naux; ++q)
-        jobs.push_back({Up, nn, dBvv.get() + (int64_t)q * V * V, v, 0, Up, nn, Bb.get() + (int64_t)q * nn * nn, nn, 1.0, 0.0});
-      G.project(jobs);
+    d['K'] = OV;
+    // DF factors of the pair: BU[Q,a,B] = sum_d Bvv[Q,a,d] U[d,B], BUt[Q,d,B] = sum_b Bvv[Q,b,d] U[b,B]
+    DV BU(N * V * nn), BUt_own;
+    G.con(d, "Qad", dBvv.get(), "dB", Up, "QaB", BU.get());
+    const double* BUt = BU.get();
+    if (!bsym) {
+      BUt_own.alloc(N * V * nn);
+      G.con(d, "Qbd", dBvv.get(), "bB", Up, "QdB", BUt_own.get());
+      BUt = BUt_own.get();
     }
-    double* Dp = pl + offD[p];
-    G.con(d, "QAC", Bb.get(), "QBD", Bb.get(), "ABCD", Dp);         // ladder
-    DV tb(O * O * nn * nn), gb(O * O * nn * nn);
-    {
-      std::vector<Prog::PJ> jobs;
-      for (int k = 0; k < o; ++k) for (int l = 0; l < o; ++l) {
-        jobs.push_back({Up, nn, t + ((int64_t)k * o + l) * V * V, v, 0, Up, nn, tb.get() + ((int64_t)k * o + l) * nn * nn, nn, 1.0, 0.0});
-        jobs.push_back({Up, nn, g_ovov.get() + (int64_t)k * V * O * V + (int64_t)l * V, o * v, 0, Up, nn,
-                        gb.get() + ((int64_t)k * o + l) * nn * nn, nn, 1.0, 0.0});
-      }
-      G.project(jobs);
+    DV Dtmp((int64_t)nn * nn * nn * nn);   // D_p, copied into its padded pool block at the end
+    double* Dp = Dtmp.get();
+    {   // ladder: Bb[Q,A,C] = U^T B^Q U, D_p = sum_Q Bb[Q,A,C] Bb[Q,B,D]
+      DV Bb(N * nn * nn);
+      G.con(d, "aA", Up, "QaC", BU.get(), "QAC", Bb.get());
+      G.con(d, "QAC", Bb.get(), "QBD", Bb.get(), "ABCD", Dp);
     }
-    G.con(d, "klAB", tb.get(), "klCD", gb.get(), "ABCD", Dp, 1.0, 1.0);   // T2 ladder
+    // T2 ladder: sum_kl tb[kl]_AB gb[kl]_CD, gb[kl]_CD = sum_Q Bh[Q,k,C] Bh[Q,l,D], tb[kl] = U^T t[k,l] U
+    DV Bh(N * O * nn), tb(O * O * nn * nn);
+    G.con(d, "Qkc", dBov.get(), "cC", Up, "QkC", Bh.get());
+    {
+      DV gb(O * O * nn * nn), X(O * O * V * nn);
+      G.con(d, "QkC", Bh.get(), "QlD", Bh.get(), "klCD", gb.get());
+      G.con(d, "klab", t, "bB", Up, "klaB", X.get());
+      G.con(d, "aA", Up, "klaB", X.get(), "klAB", tb.get());
+      G.con(d, "klAB", tb.get(), "klCD", gb.get(), "ABCD", Dp, 1.0, 1.0);
+    }
     DV Fb(nn * nn);
     G.project({{Up, nn, FvvI.get(), v, 0, Up, nn, Fb.get(), nn, 1.0, 0.0}});
     k_add_fock_kron<<<gsz((size_t)nn * nn * nn * nn), 256, 0, s>>>(Dp, Fb.get(), nn);
     PN_CUDA(cudaGetLastError());
+    PN_CUDA(cudaMemcpy2DAsync(pl + offD[p], pad(nn * nn) * 8, Dp, (int64_t)nn * nn * 8, (int64_t)nn * nn * 8, (int64_t)nn * nn,
+                              cudaMemcpyDeviceToDevice, s));
+
+    // P_x[Q,A,D] = sum_a U[a,A] (B^Q U^x)[a,D] for the pair's OSVs x = i, j
+    const int ni = G.no(i), nj = G.no(j);
+    DV Pi, Pj;
+    auto make_P = [&](int x, DV& out) {
+      const int nx = G.no(x);
+      if (!nx) return;
+      DV BUx;
+      osv_cols(BUo.get(), N * V, x, BUx);
+      Dims dx = d;
+      dx['D'] = nx;
+      out.alloc(N * nn * nx);
+      G.con(dx, "aA", Up, "QaD", BUx.get(), "QAD", out.get());
+    };
+    make_P(i, Pi);
+    if (j != i) make_P(j, Pj);
+    const DV& Pjr = j != i ? Pj : Pi;
+
+    // ---- V_bar rows of A_S (sigma1 from R2 through (ad|kc)): for the pair's OSV owners x with k
+    // the other index, Vb[A,C,D] = sum_{a,c,d} U^x[a,A] (ad|kc) U[c,C] U[d,D]
+    //   = sum_Q (U^x^T B^Q U)[A,D] Bh[Q,k,C]; added as 2 Vb - Vb^T (CD) in the orientation of
+    //   the stored block
+    for (int side = 0; side < (i == j ? 1 : 2); ++side) {
+      const int x = side == 0 ? j : i, k = side == 0 ? i : j;
+      const int nx = G.no(x);
+      if (!nx) continue;
+      Dims dx = d;
+      dx['X'] = nx;
+      DV Px(N * nx * nn), Bk(N * nn), Vb(nx * nn * nn), Vt(nx * nn * nn);
+      G.con(dx, "aX", G.Uo(x), "QaD", BU.get(), "QXD", Px.get());
+      PN_CUDA(cudaMemcpy2DAsync(Bk.get(), nn * 8, Bh.get() + (int64_t)k * nn, O * nn * 8, nn * 8, N, cudaMemcpyDeviceToDevice, s));
+      G.con(dx, "QXD", Px.get(), "QC", Bk.get(), "XCD", Vb.get());
+      G.perm(Vb.get(), Vt.get(), {nx, nn, nn}, {0, 2, 1});
+      const bool direct = k <= x;
+      double* rows = AS + P->off_i[x] * Lp + P->off_ij[p];
+      G.add_block(rows, Lp, direct ? Vb.get() : Vt.get(), nn * nn, nx, nn * nn, 2.0);
+      G.add_block(rows, Lp, direct ? Vt.get() : Vb.get(), nn * nn, nx, nn * nn, -1.0);
+    }
 
     // ---- singles -> doubles dense block A_DS_p (n^2 x L1) --------------------------------------
     double* Y = pl + offADS[p];
-    const int ni = G.no(i), nj = G.no(j);
     // (c1)+(c3): columns of OSV i and OSV j
     for (int side = 0; side < 2; ++side) {
       const int x = side == 0 ? i : j;      // OSV whose r1 enters
       const int nx = side == 0 ? ni : nj;
       if (!nx) continue;
       d['C'] = nx;
-      DV T1(nn * V * V), T2(nn * nx * V), K3(nn * nn * nx), H(O * O * nx);
-      if (side == 0) {  // sum_c U^i[c,C] (ac|bj): X3 = (ac|bj) at [a][c][b] for this j
-        const double* X3 = gvvvo_j.get() + (int64_t)j * V * V * V;
-        G.con(d, "aA", Up, "acb", X3, "Acb", T1.get());
-        G.con(d, "Acb", T1.get(), "cC", G.Uo(i), "ACb", T2.get());
-        G.con(d, "ACb", T2.get(), "bB", Up, "ABC", K3.get());
+      DV K3(nn * nn * nx), H(O * O * nx);
+      if (side == 0) {  // sum U[a,A] (ac|bj) U^i[c,C] U[b,B] = sum_Q P_i[Q,A,C] (sum_b B[Q,b,j] U[b,B])
+        DV bj(N * nn);
+        G.con(d, "Qb", BvoT.get() + (int64_t)j * N * V, "bB", Up, "QB", bj.get());
+        G.con(d, "QAC", Pi.get(), "QB", bj.get(), "ABC", K3.get());
         G.con(d, "kcl", govoo_j.get() + (int64_t)j * O * V * O, "cC", G.Uo(i), "klC", H.get());
-      } else {          // sum_c U^j[c,C] (ai|bc): (ai|bc) = X3'[b][c][a] for this i
-        const double* X3 = gvvvo_j.get() + (int64_t)i * V * V * V;
-        G.con(d, "bca", X3, "aA", Up, "bcA", T1.get());
-        G.con(d, "bcA", T1.get(), "cC", G.Uo(j), "bAC", T2.get());
-        G.con(d, "bAC", T2.get(), "bB", Up, "ABC", K3.get());
+      } else {          // sum U[a,A] (ai|bc) U^j[c,C] U[b,B] = sum_Q (sum_a B[Q,a,i] U[a,A]) P_j[Q,B,C]
+        DV ai(N * nn);
+        G.con(d, "Qa", BvoT.get() + (int64_t)i * N * V, "aA", Up, "QA", ai.get());
+        G.con(d, "QA", ai.get(), "QBC", Pjr.get(), "ABC", K3.get());
         G.con(d, "klc", gooov_i.get() + (int64_t)i * O * O * V, "cC", G.Uo(j), "klC", H.get());
       }
       G.con(d, "klAB", tb.get(), "klC", H.get(), "ABC", K3.get(), 1.0, 1.0);
-      G.add_block(Y + P->off_i[x], L1, K3.get(), nx, nn * nn, nx, 1.0);
+      G.add_block(Y + P->off_i[x], L1p, K3.get(), nx, nn * nn, nx, 1.0);
     }
-    // (c1)+(c2): outer products with S(ij,k) r1_k
+    // (c1)+(c2): outer products with S(ij,k) r1_k; wa[k,B] = -sum_b U[b,B] ((ki|bj) + Y1[i,j,k,b]),
+    // wb[k,A] = -sum_a U[a,A] ((ai|kj) + Y2[i,j,a,k]) with the T2 parts through the DF factors:
+    //   sum_b U[b,B] Y1[i,j,k,b] = sum_{Q,c} B[Q,k,c] sum_d t[i,j,c,d] BUt[Q,d,B]
+    //   sum_a U[a,A] Y2[i,j,a,k] = sum_{Q,d} B[Q,k,d] sum_c t[i,j,c,d] BUt[Q,c,A]
     {
       DV Sk(nn * std::max<int64_t>(1, L1)), wa(O * nn), wb(O * nn);
       std::vector<GemmProb<double>> pr;
@@ -511,42 +631,69 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       pr.push_back({wa_can.get() + ((int64_t)i * o + j) * O * V, Up, wa.get(), o, nn, v, v, nn, nn, 0, 0, -1.0, 0.0});
       pr.push_back({wb_can.get() + ((int64_t)i * o + j) * O * V, Up, wb.get(), o, nn, v, v, nn, nn, 0, 0, -1.0, 0.0});
       grouped_gemm<double>(pr, s);
+      const double* tij = t + ((int64_t)i * o + j) * V * V;
+      DV Z(N * V * nn);
+      G.con(d, "cd", tij, "QdB", BUt, "QcB", Z.get());
+      G.con(d, "Qkc", dBov.get(), "QcB", Z.get(), "kB", wa.get(), -1.0, 1.0);
+      G.con(d, "cd", tij, "QcA", BUt, "QdA", Z.get());
+      G.con(d, "Qkd", dBov.get(), "QdA", Z.get(), "kA", wb.get(), -1.0, 1.0);
       for (int k = 0; k < o; ++k) {
         if (!G.no(k)) continue;
-        G.kron(Y + P->off_i[k], L1, Sk.get() + P->off_i[k], (int)L1, wa.get() + (int64_t)k * nn, nn, G.no(k), 0, 1.0);
-        G.kron(Y + P->off_i[k], L1, Sk.get() + P->off_i[k], (int)L1, wb.get() + (int64_t)k * nn, nn, G.no(k), 1, 1.0);
+        G.kron(Y + P->off_i[k], L1p, Sk.get() + P->off_i[k], (int)L1, wa.get() + (int64_t)k * nn, nn, G.no(k), 0, 1.0);
+        G.kron(Y + P->off_i[k], L1p, Sk.get() + P->off_i[k], (int)L1, wb.get() + (int64_t)k * nn, nn, G.no(k), 1, 1.0);
       }
     }
+    // exchange factors of the Qa / Q1 terms: Yx[A,c,k,D] = sum_Q BUt[Q,c,A] BoU[Q,k,(x,D)] for the
+    // pair's OSVs x (sum_{a,d} U[a,A] U^x[d,D] (ac|kd) = Yx[A,c,k,D])
+    DV Yi, Yj;
+    auto make_Y = [&](int x, DV& out) {
+      const int nx = G.no(x);
+      if (!nx) return;
+      DV BoUx;
+      osv_cols(BoU.get(), N * O, x, BoUx);
+      Dims dx = d;
+      dx['D'] = nx;
+      out.alloc(nn * V * O * nx);
+      G.con(dx, "QcA", BUt, "QkD", BoUx.get(), "AckD", out.get());
+    };
+    make_Y(i, Yi);
+    if (j != i) make_Y(j, Yj);
+    auto Yof = [&](int x) -> const DV& { return x == i ? Yi : Yj; };
+    auto Pof = [&](int x) -> const DV& { return x == i ? Pi : Pjr; };
     // ordered (x,y) contributions (the P-symmetrised part): (i,j) and, if i < j, (j,i) transposed
     for (int ord = 0; ord < (i == j ? 1 : 2); ++ord) {
       const int x = ord == 0 ? i : j, y = ord == 0 ? j : i;
       DV Yc(nn * nn * std::max<int64_t>(1, L1));
       Yc.zero(s);
       d['L'] = L1;
-      // Qa (OSV x) and -Q1 (OSV y), projected: PNO projection of b on the amplitudes,
-      // ut[k,c,B] = sum_b U[b,B] u[y,k,b,c], ty[k,c,B] = sum_b U[b,B] t[k,y,b,c], tx likewise for x
-      {
-        DV ut((size_t)O * V * nn), ty((size_t)O * V * nn), tx((size_t)O * V * nn);
-        G.con(d, "kbc", u + (int64_t)y * O * V * V, "bB", Up, "kcB", ut.get());
-        G.con(d, "kbc", tY.get() + (int64_t)y * O * V * V, "bB", Up, "kcB", ty.get());
-        G.con(d, "kbc", tY.get() + (int64_t)x * O * V * V, "bB", Up, "kcB", tx.get());
-        for (int side = 0; side < 2; ++side) {
-          const int z = side == 0 ? x : y;
-          const int nz = G.no(z);
-          if (!nz) continue;
-          d['D'] = nz;
-          DV T1((size_t)V * nz * nn), K3((size_t)nn * nn * nz);
-          if (side == 0) {
-            G.con(d, "aDkc", Gz[z].get(), "kcB", ut.get(), "aDB", T1.get());
-            G.con(d, "aDkc", Hz[z].get(), "kcB", ty.get(), "aDB", T1.get(), -0.5, 1.0);
-          } else {
-            G.con(d, "aDkc", Hz[z].get(), "kcB", tx.get(), "aDB", T1.get(), -1.0, 0.0);
-          }
-          G.con(d, "aDB", T1.get(), "aA", Up, "ABD", K3.get());
-          G.add_block(Yc.get() + P->off_i[z], L1, K3.get(), nz, nn * nn, nz, 1.0);
-        }
+      // W factors of the pair: ut[k,c,B] = sum_b U[b,B] u[y,k,b,c] = UU[y], ty = sum_b U[b,B] t[k,y,b,c] = TU[y],
+      // tx = TU[x]
+      DV ut, ty, tx;
+      cat_block(UUc, y, x, ut);
+      cat_block(TUc, y, x, ty);
+      cat_block(TUc, x, y, tx);
+      // Qa (OSV x): sum U[a,A] U^x[d,D] [(ad|kc) ut - 1/2 (ac|kd) (ut + ty)][k,c,B];
+      // Q1 (OSV y): - sum U[a,A] U^y[d,D] (ac|kd) tx[k,c,B]
+      if (G.no(x)) {
+        const int nx = G.no(x);
+        Dims dx = d;
+        dx['D'] = nx;
+        DV wq(N * nn), K3(nn * nn * nx), W0(OV * nn);
+        G.con(dx, "QK", dBov.get(), "KB", ut.get(), "QB", wq.get());
+        G.con(dx, "QAD", Pof(x).get(), "QB", wq.get(), "ABD", K3.get());
+        PN_CUDA(cudaMemcpyAsync(W0.get(), ut.get(), W0.n * 8, cudaMemcpyDeviceToDevice, s));
+        axpby<double>(W0.get(), ty.get(), 1.0, 1.0, W0.n, s);
+        G.con(dx, "AckD", Yof(x).get(), "kcB", W0.get(), "ABD", K3.get(), -0.5, 1.0);
+        G.add_block(Yc.get() + P->off_i[x], L1, K3.get(), nx, nn * nn, nx, 1.0);
       }
-      d['D'] = nn;
+      if (G.no(y)) {
+        const int ny = G.no(y);
+        Dims dy = d;
+        dy['D'] = ny;
+        DV K3(nn * nn * ny);
+        G.con(dy, "AckD", Yof(y).get(), "kcB", tx.get(), "ABD", K3.get(), -1.0, 0.0);
+        G.add_block(Yc.get() + P->off_i[y], L1, K3.get(), ny, nn * nn, ny, 1.0);
+      }
       if (L1 > 0) {
         // Lambda: sum_c t[x,y,a,c] (2 (bc|md) - (bd|mc)) U^m[d,D]
         DV T2(nn * V * L1);
@@ -554,14 +701,20 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         G.con(d, "AbL", T2.get(), "bB", Up, "ABL", Yc.get(), 1.0, 1.0);
         // e2m: - sum_k tb3[x,k,y] Gam_y[k, L]
         G.con(d, "kAB", tb3[x * o + y].get(), "kL", GamAll.get() + (int64_t)y * O * L1, "ABL", Yc.get(), -1.0, 1.0);
-        // qb kron: S(xy,m)[A,C] qb[x,y,m][B]
+        // qb kron: S(xy,m)[A,C] qb[x,y,m][B], qb = sum_b Qb[m,x,y,b] U[b,B] with
+        // Qb[m,x,y,b] = Q2[m,y,x,b] + 1/2 Q2[m,x,y,b] - Q5[m,x,y,b] + 1/2 Q6[m,x,y,b]:
+        //   Q2 part: G2q[y] tx + 1/2 G2q[x] ty;  Q5: -g_ooov[m,x,(k,c)] ut;  Q6: 1/2 G6q[x] ut
         DV Sk(nn * L1), qb(O * nn), e2a(O * nn);
         std::vector<GemmProb<double>> pr;
         for (int m = 0; m < o; ++m)
           if (G.no(m))
             pr.push_back({Up, G.Uo(m), Sk.get() + P->off_i[m], nn, G.no(m), v, nn, G.no(m), (int)L1, 1, 0, 1.0, 0.0});
-        pr.push_back({Qb_xy.get() + ((int64_t)x * o + y) * O * V, Up, qb.get(), o, nn, v, v, nn, nn, 0, 0, 1.0, 0.0});
         grouped_gemm<double>(pr, s);
+        const int ov = (int)OV;
+        grouped_gemm<double>({{G2q.get() + (int64_t)y * O * OV, tx.get(), qb.get(), o, nn, ov, ov, nn, nn, 0, 0, 1.0, 0.0}}, s);
+        grouped_gemm<double>({{G2q.get() + (int64_t)x * O * OV, ty.get(), qb.get(), o, nn, ov, ov, nn, nn, 0, 0, 0.5, 1.0}}, s);
+        grouped_gemm<double>({{g_ooov.get() + (int64_t)x * OV, ut.get(), qb.get(), o, nn, ov, (int)(O * OV), nn, nn, 0, 0, -1.0, 1.0}}, s);
+        grouped_gemm<double>({{G6q.get() + (int64_t)x * O * OV, ut.get(), qb.get(), o, nn, ov, ov, nn, nn, 0, 0, 0.5, 1.0}}, s);
         for (int m = 0; m < o; ++m)
           if (G.no(m))
             G.kron(Yc.get() + P->off_i[m], L1, Sk.get() + P->off_i[m], (int)L1, qb.get() + (int64_t)m * nn, nn, G.no(m), 0, 1.0);
@@ -586,43 +739,66 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         }
       }
       // accumulate into A_DS_p: (i,j) as is, (j,i) with rows transposed; for i == j both
-      if (ord == 0) G.add_block(Y, L1, Yc.get(), L1, nn * nn, (int)L1, 1.0, 0);
-      if (ord == 1 || i == j) G.add_block(Y, L1, Yc.get(), L1, nn * nn, (int)L1, 1.0, nn);
+      if (ord == 0) G.add_block(Y, L1p, Yc.get(), L1, nn * nn, (int)L1, 1.0, 0);
+      if (ord == 1 || i == j) G.add_block(Y, L1p, Yc.get(), L1, nn * nn, (int)L1, 1.0, nn);
     }
     // no synchronisation per pair: temporaries return to this thread's cache and are
     // reused in stream order, so the host plans the next pair while this one runs
   }
+  TUc.release();
+  UUc.release();
+  BUo.release();
 
   tm.mark("  pair loop (D, A_DS)");
-  // ---- singles rows A_S_i (n_i x L) --------------------------------------------------------------
+  // ---- singles rows A_S (L1 x L; the V_bar parts were added in the pair loop) ---------------
+  if (L1 > 0) {
+    // singles-singles: U^i^T [sum_{k,c} u[i,k,a,c] L[k,c,m,d] + 2 (ai|md) - (mi|ad) + delta_im Xv - delta_ad Xo[m,i]] U^m
+    // with the first term as UUo[i]^T LUo[m]: UUo[i][(k,c),A] = sum_a u[i,k,a,c] U^i[a,A],
+    // LUo[m][(k,c),D] = sum_d L[m,d,k,c] U^m[d,D]
+    DV UUo(OV * L1), LUo(OV * L1);
+    std::vector<GemmProb<double>> pr;
+    for (int m = 0; m < o; ++m) {
+      const int nm = G.no(m);
+      if (!nm) continue;
+      pr.push_back({uS.get() + (int64_t)m * OV * V, G.Uo(m), UUo.get() + P->off_i[m], (int)OV, nm, v, v, nm, (int)L1, 0, 0, 1.0, 0.0});
+      pr.push_back({L_ovov.get() + (int64_t)m * V * OV, G.Uo(m), LUo.get() + P->off_i[m], (int)OV, nm, v, (int)OV, nm, (int)L1, 1, 0, 1.0, 0.0});
+    }
+    grouped_gemm<double>(pr, s);
+    grouped_gemm<double>({{UUo.get(), LUo.get(), AS, (int)L1, (int)L1, (int)OV, (int)L1, (int)L1, (int)Lp, 1, 0, 1.0, 1.0}}, s);
+    std::vector<Prog::PJ> ja, jb, jc;
+    DV eye(V * V);
+    {
+      std::vector<double> I((size_t)V * V, 0.0);
+      for (int a = 0; a < v; ++a) I[(size_t)a * v + a] = 1.0;
+      eye.upload(I.data(), I.size(), s);
+    }
+    for (int i = 0; i < o; ++i) {
+      if (!G.no(i)) continue;
+      for (int m = 0; m < o; ++m) {
+        if (!G.no(m)) continue;
+        double* out = AS + P->off_i[i] * Lp + P->off_i[m];
+        ja.push_back({G.Uo(i), G.no(i), g_voov.get() + (int64_t)i * OV + (int64_t)m * V, (int)(O * O * V), 0, G.Uo(m), G.no(m),
+                      out, (int)Lp, 2.0, 1.0});
+        jb.push_back({G.Uo(i), G.no(i), g_oovv.get() + ((int64_t)m * o + i) * V * V, v, 0, G.Uo(m), G.no(m), out, (int)Lp,
+                      -1.0, 1.0});
+        if (m == i) jc.push_back({G.Uo(i), G.no(i), Xv.get(), v, 0, G.Uo(i), G.no(i), out, (int)Lp, 1.0, 1.0});
+      }
+    }
+    G.project(ja);
+    G.project(jb);
+    G.project(jc);
+    std::vector<Prog::PJ> jd;   // - Xo[m,i] U^i^T U^m
+    for (int i = 0; i < o; ++i)
+      for (int m = 0; m < o; ++m)
+        if (G.no(i) && G.no(m) && Xo_h[m * o + i] != 0.0)
+          jd.push_back({G.Uo(i), G.no(i), eye.get(), v, 0, G.Uo(m), G.no(m), AS + P->off_i[i] * Lp + P->off_i[m], (int)Lp,
+                        -Xo_h[m * o + i], 1.0});
+    G.project(jd);
+  }
   for (int i = 0; i < o; ++i) {
     const int ni = G.no(i);
     if (!ni) continue;
-    double* Ai = pl + offAS[i];
-    {   // singles-singles
-      std::vector<Prog::PJ> jobs;
-      for (int m = 0; m < o; ++m)
-        if (G.no(m))
-          jobs.push_back({G.Uo(i), ni, Acan.get() + (int64_t)i * V * O * V + (int64_t)m * V, o * v, 0, G.Uo(m), G.no(m),
-                          Ai + P->off_i[m], (int)L, 1.0, 0.0});
-      G.project(jobs);
-    }
-    Dims d = G.dm;
-    d['A'] = ni;
-    for (int k = 0; k < o; ++k) {   // V_bar term: ordered (k, i), stored q = {k, i}
-      const int q = P->pidx[k][i];
-      const int nq = (int)nP(q);
-      if (!nq) continue;
-      d['C'] = nq; d['D'] = nq;
-      DV T1(ni * V * V), T2(ni * nq * V), Vb(ni * nq * nq), Vt(Vb.n);
-      G.con(d, "adc", gvvov_k.get() + (int64_t)k * V * V * V, "aA", G.Uo(i), "Adc", T1.get());
-      G.con(d, "Adc", T1.get(), "cC", G.U(k, i), "ACd", T2.get());
-      G.con(d, "ACd", T2.get(), "dD", G.U(k, i), "ACD", Vb.get());
-      G.perm(Vb.get(), Vt.get(), {ni, nq, nq}, {0, 2, 1});
-      const bool direct = k <= i;
-      G.add_block(Ai + P->off_ij[q], L, direct ? Vb.get() : Vt.get(), nq * nq, ni, nq * nq, 2.0);
-      G.add_block(Ai + P->off_ij[q], L, direct ? Vt.get() : Vb.get(), nq * nq, ni, nq * nq, -1.0);
-    }
+    double* Ai = AS + P->off_i[i] * Lp;
     {   // h_bar term (and F_ov term with T1): -S(i,kl) UR^{kl} h
       DV S(ni * std::max<int64_t>(1, L - L1)), hb((int64_t)O * O * v);
       std::vector<GemmProb<double>> pr;
@@ -645,8 +821,8 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         const double* w = hb.get() + ((int64_t)k * o + l) * V;
         double* out = Ai + P->off_ij[q];
         const int lds = (int)(L - L1);
-        if (k <= l) { G.kron(out, L, Sq, lds, w, nn, ni, 2, -2.0); G.kron(out, L, Sq, lds, w, nn, ni, 3, 1.0); }
-        else { G.kron(out, L, Sq, lds, w, nn, ni, 3, -2.0); G.kron(out, L, Sq, lds, w, nn, ni, 2, 1.0); }
+        if (k <= l) { G.kron(out, Lp, Sq, lds, w, nn, ni, 2, -2.0); G.kron(out, Lp, Sq, lds, w, nn, ni, 3, 1.0); }
+        else { G.kron(out, Lp, Sq, lds, w, nn, ni, 3, -2.0); G.kron(out, Lp, Sq, lds, w, nn, ni, 2, 1.0); }
       }
       if (t1) {   // + S(i,ik) UR^{ik} fb, fb = U(i,k)^T Fov[k]
         DV dFov(O * V), fb(O * V);
@@ -663,8 +839,8 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
           const double* w = fb.get() + (int64_t)k * V;
           double* out = Ai + P->off_ij[q];
           const int lds = (int)(L - L1);
-          if (i <= k) { G.kron(out, L, Sq, lds, w, nn, ni, 2, 2.0); G.kron(out, L, Sq, lds, w, nn, ni, 3, -1.0); }
-          else { G.kron(out, L, Sq, lds, w, nn, ni, 3, 2.0); G.kron(out, L, Sq, lds, w, nn, ni, 2, -1.0); }
+          if (i <= k) { G.kron(out, Lp, Sq, lds, w, nn, ni, 2, 2.0); G.kron(out, Lp, Sq, lds, w, nn, ni, 3, -1.0); }
+          else { G.kron(out, Lp, Sq, lds, w, nn, ni, 3, 2.0); G.kron(out, Lp, Sq, lds, w, nn, ni, 2, -1.0); }
         }
       }
     }
@@ -702,7 +878,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   auto add_gemv = [&](std::vector<VProb>& L_, int64_t aoff, int M, int K, int lda, int xbuf, int64_t xoff, int xs, int xvn,
                       int cbuf, int64_t coff, int cs, int cvn, double al) {
     if (M <= 0 || K <= 0 || al == 0.0) return;
-    for (int m0 = 0; m0 < M; m0 += 64)
+    for (int m0 = 0; m0 < M; m0 += GEMV_ROWS)
       for (int k0 = 0; k0 < K; k0 += GEMV_KC) {
         VProb q{};
         q.a_off = aoff; q.x_off = xoff; q.c_off = coff;
@@ -746,9 +922,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
            B_POOL, offGh[k * o + l], v, 0, 2.0, -0.5);
     // FoR[:, j] += G4[(l,j)] vec(2 R^{lj} - R^{lj T})   (here (l, j) = (k, l))
     const int lj_l = k, lj_j = l;
-    add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? nn : 0, B_WORK,
+    add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, (int)pad(nn * nn), B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? nn : 0, B_WORK,
              P->work_for + lj_j, o, 0, 2.0);
-    add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, nn * nn, B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? 0 : nn, B_WORK,
+    add_gemv(G.vp1, offG4[lj_l * o + lj_j], o, nn * nn, (int)pad(nn * nn), B_RIN, Ro(lj_l, lj_j), 1, Rt(lj_l, lj_j) ? 0 : nn, B_WORK,
              P->work_for + lj_j, o, 0, -1.0);
   }
   add_dense(G.dp1, DENSE_TILE_TC, 256, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, off_Ucat, (int)nsum, 0, (int)nsum, B_WORK, P->work_y, v,
@@ -760,11 +936,11 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   for (int p = 0; p < npairs; ++p) {
     const int nn = (int)nP(p);
     if (!nn) continue;
-    add_gemv(G.vp2, offD[p], nn * nn, nn * nn, nn * nn, B_RIN, P->off_ij[p], 1, 0, B_SOUT, P->off_ij[p], 1, 0, 1.0);
-    add_gemv(G.vp2, offADS[p], nn * nn, (int)L1, (int)L1, B_RIN, 0, 1, 0, B_SOUT, P->off_ij[p], 1, 0, 1.0);
+    add_gemv(G.vp2, offD[p], nn * nn, nn * nn, (int)pad(nn * nn), B_RIN, P->off_ij[p], 1, 0, B_SOUT, P->off_ij[p], 1, 0, 1.0);
+    add_gemv(G.vp2, offADS[p], nn * nn, (int)L1, (int)L1p, B_RIN, 0, 1, 0, B_SOUT, P->off_ij[p], 1, 0, 1.0);
   }
   for (int i = 0; i < o; ++i)
-    add_gemv(G.vp2, offAS[i], G.no(i), (int)L, (int)L, B_RIN, 0, 1, 0, B_SOUT, P->off_i[i], 1, 0, 1.0);
+    add_gemv(G.vp2, off_AS + P->off_i[i] * Lp, G.no(i), (int)L, (int)Lp, B_RIN, 0, 1, 0, B_SOUT, P->off_i[i], 1, 0, 1.0);
   // ordered (i,j) contributions go to stored {i,j}; transposed when i > j; twice when i == j
   auto targets = [&](int i, int j, std::vector<int>& tcs) {
     tcs.clear();
@@ -779,7 +955,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     for (int tc : tcs) {
       const int64_t co = P->off_ij[pij];
       // E4 phase 2: -sum_k FoR[k,j] vec(tb3[i,k,j])
-      add_gemv(G.vp2, offT4[i * o + j], nij * nij, o, o, B_WORK, P->work_for + j, o, 0, B_SOUT, co, 1, tc ? nij : 0, -1.0);
+      add_gemv(G.vp2, offT4[i * o + j], nij * nij, o, (int)Op, B_WORK, P->work_for + j, o, 0, B_SOUT, co, 1, tc ? nij : 0, -1.0);
       // E3 phase 2: Th[i,j] FvR^T U(i,j) = Th[i,j] Z[:, columns of pair {i,j}]
       add_dense(G.dp3, 32, 1 << 30, B_SOUT, co, nij, tc, nij, nij, B_POOL, offTh[i * o + j], v, 0, v, B_WORK,
                 P->work_z + zc[pij], (int)nsum, 0, 1.0);
@@ -787,23 +963,23 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         const int nkj = G.n(k, j), nki = G.n(k, i), njk = G.n(j, k), nik = G.n(i, k);
         const int pkj = blk(k, j), pki = blk(k, i), pjk = blk(j, k), pik = blk(i, k);
         // C1: -1/2 MC[i,j,k] R^{kj T} S(kj,ij)
-        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMC[idx3(i, j, k)], nkj, 0, nkj, B_RIN, Ro(k, j), nkj,
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, ring_off(offMCc, j, i, k), (int)clen[j], 0, nkj, B_RIN, Ro(k, j), nkj,
                1 - Rt(k, j), nkj, B_POOL, Sblk(pkj, pij), nij, 0, -0.5);
         // C2: -MC[j,i,k] R^{ki T} S(ki,ij)
-        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMC[idx3(j, i, k)], nki, 0, nki, B_RIN, Ro(k, i), nki,
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, ring_off(offMCc, i, j, k), (int)clen[i], 0, nki, B_RIN, Ro(k, i), nki,
                1 - Rt(k, i), nki, B_POOL, Sblk(pki, pij), nij, 0, -1.0);
         // C3: +1/4 S(ij,ki) R^{ki} MZ[k,i,j]
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pki), nki, 0, nki, B_RIN, Ro(k, i), nki, Rt(k, i),
-               nki, B_POOL, offMZ[idx3(k, i, j)], nij, 0, 0.25);
+               nki, B_POOL, ring_off(offMZc, i, k, j), (int)clen[i], 0, 0.25);
         // C4: +1/2 S(ij,kj) R^{kj} MZ[k,j,i]
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pkj), nkj, 0, nkj, B_RIN, Ro(k, j), nkj, Rt(k, j),
-               nkj, B_POOL, offMZ[idx3(k, j, i)], nij, 0, 0.5);
+               nkj, B_POOL, ring_off(offMZc, j, k, i), (int)clen[j], 0, 0.5);
         // D1: MD[i,j,k] (R^{jk T} - 1/2 R^{jk}) S(jk,ij)
-        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, offMD[idx3(i, j, k)], njk, 0, njk, B_RIN, Ro(j, k), njk,
+        add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, ring_off(offMDc, j, i, k), (int)clen[j], 0, njk, B_RIN, Ro(j, k), njk,
                1 - Rt(j, k), njk, B_POOL, Sblk(pjk, pij), nij, 0, 1.0, -0.5);
         // D2: S(ij,ik) (1/2 R^{ik} - 1/4 R^{ik T}) MZd[k,i,j]
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik, Rt(i, k),
-               nik, B_POOL, offMZd[idx3(k, i, j)], nij, 0, 0.5, -0.5);
+               nik, B_POOL, ring_off(offMZdc, i, k, j), (int)clen[i], 0, 0.5, -0.5);
         // E2: -Foo~[k,j] S(ij,ik) R^{ik} S(ik,ij)
         add_sw(G.sp2, B_SOUT, co, nij, tc, nij, nij, B_POOL, Sblk(pij, pik), nik, 0, nik, B_RIN, Ro(i, k), nik, Rt(i, k),
                nik, B_POOL, Sblk(pik, pij), nij, 0, -FooI_h[k * o + j]);
@@ -867,7 +1043,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       std::set<std::pair<int64_t, int64_t>> vec_blocks;
       double pe = 0, fl = 0;
       for (const VProb& q : Lst) {
-        const int rows = std::min(64, q.M - q.m0);
+        const int rows = std::min(GEMV_ROWS, q.M - q.m0);
         pe += (double)rows * q.klen;
         fl += 2.0 * rows * q.klen;
         vec_blocks.insert({q.x_off + ((int64_t)q.x_buf << 40), (int64_t)q.K * q.x_stride});
@@ -994,6 +1170,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   // FP32 copy of the pool for the mixed-precision sigma
   P->pool32.alloc(P->pool64.n, fp);
   d2f(P->pool32.get(), P->pool64.get(), P->pool64.n, s);
+  // BF16 copy for the BF16 sigma (its dense GEMV blocks)
+  P->pool16.alloc(P->pool64.n, fp);
+  d2bf(P->pool16.get(), P->pool64.get(), P->pool64.n, s);
   G.sync();
 }
 

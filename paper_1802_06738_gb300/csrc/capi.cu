@@ -187,9 +187,9 @@ int sigma(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, const void* r_dev, v
     pnoeom::DeviceScope dev_scope(ctx->device);
     auto* P = const_cast<pnoeom_pno*>(pno);
     if (precision == PNOEOM_FP64)
-      pnoeom::apply_sigma<double>(P, nvec, (const double*)r_dev, (double*)s_dev, st(cuda_stream));
-    else if (precision == PNOEOM_FP32)
-      pnoeom::apply_sigma<float>(P, nvec, (const float*)r_dev, (float*)s_dev, st(cuda_stream));
+      pnoeom::apply_sigma<double>(P, nvec, (const double*)r_dev, (double*)s_dev, st(cuda_stream), false);
+    else if (precision == PNOEOM_FP32 || precision == PNOEOM_BF16)
+      pnoeom::apply_sigma<float>(P, nvec, (const float*)r_dev, (float*)s_dev, st(cuda_stream), precision == PNOEOM_BF16);
     else
       throw pnoeom::Error(PNOEOM_ERR_INVALID_ARG, "unknown precision");
   });
@@ -236,7 +236,8 @@ int pnoeom_batch_sigma(pnoeom_ctx* ctx, pnoeom_batch* batch, const int* nvec, co
                        void* const* s_dev, int precision, void* cuda_stream) {
   return guard([&] {
     PN_CHECK(ctx && batch && nvec && r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL argument");
-    PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32, PNOEOM_ERR_INVALID_ARG, "unknown precision");
+    PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32 || precision == PNOEOM_BF16, PNOEOM_ERR_INVALID_ARG,
+             "unknown precision");
     pnoeom::DeviceScope dev_scope(ctx->device);
     pnoeom::batch_sigma(batch, nvec, r_dev, s_dev, precision, st(cuda_stream));
   });
@@ -303,6 +304,15 @@ int pno_get_eigenvectors(const pnoeom_pno* pno, double* X) {
   return guard([&] {
     PN_CHECK(pno && X, PNOEOM_ERR_INVALID_ARG, "NULL argument");
     std::copy(pno->last_X.begin(), pno->last_X.end(), X);
+  });
+}
+
+int pno_solve_lowprec_energies(const pnoeom_pno* pno, int n, double* energies, int* count) {
+  return guard([&] {
+    PN_CHECK(pno && (n <= 0 || energies), PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    const int c = (int)pno->last_lowprec_w.size();
+    if (count) *count = c;
+    for (int k = 0; k < std::min(n, c); ++k) energies[k] = pno->last_lowprec_w[k];
   });
 }
 

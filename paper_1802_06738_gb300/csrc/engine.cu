@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cstdlib>
 #include <atomic>
+#include <cuda_bf16.h>
 
 namespace pnoeom {
 
@@ -543,6 +544,15 @@ template <typename T> void scale(T* y, T a, size_t n, cudaStream_t s) {
 void d2f(float* y, const double* x, size_t n, cudaStream_t s) {
   if (!n) return;
   k_d2f<<<grid_for(n), 256, 0, s>>>(y, x, n);
+  PN_CUDA(cudaGetLastError());
+}
+__global__ void k_d2bf(__nv_bfloat16* y, const double* x, size_t n) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x)
+    y[e] = __double2bfloat16(x[e]);
+}
+void d2bf(void* y, const double* x, size_t n, cudaStream_t s) {
+  if (!n) return;
+  k_d2bf<<<grid_for(n), 256, 0, s>>>((__nv_bfloat16*)y, x, n);
   PN_CUDA(cudaGetLastError());
 }
 void f2d(double* y, const float* x, size_t n, cudaStream_t s) {

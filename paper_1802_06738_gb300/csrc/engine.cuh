@@ -47,5 +47,6 @@ template <typename T> void axpby(T* y, const T* x, T a, T b, size_t n, cudaStrea
 template <typename T> void scale(T* y, T a, size_t n, cudaStream_t s);
 void d2f(float* y, const double* x, size_t n, cudaStream_t s);
 void f2d(double* y, const float* x, size_t n, cudaStream_t s);
+void d2bf(void* y, const double* x, size_t n, cudaStream_t s);   // y: __nv_bfloat16[n], rounded to nearest
 
 }  // namespace pnoeom

@@ -33,12 +33,12 @@ void* scratch_address(int device) {
 }
 
 template <typename T>
-void sigma_into_scratch(const pnoeom_pno* P, int nvec, const T* r, T* out, T* work, cudaStream_t s) {
+void sigma_into_scratch(const pnoeom_pno* P, int nvec, const T* r, T* out, T* work, cudaStream_t s, bool bf16) {
   using namespace pnoeom;
-  SysTable t;
+  SysTable t{};
   t.nsys = 1;
   t.max_nvec = nvec;
-  t.s[0] = sysbuf(P, nvec, r, out, work, sizeof(T) == 4);
+  t.s[0] = sysbuf(P, nvec, r, out, work, sizeof(T) == 4, bf16);
   const int64_t ol = P->L, wl = P->work_len;
   run_program<T>(P->prog, t, &ol, &wl, s, nullptr);
 }
@@ -52,7 +52,8 @@ extern "C" int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, c
     PN_CHECK(nvec >= 0, PNOEOM_ERR_INVALID_ARG, "nvec < 0");
     if (nvec == 0) return;
     PN_CHECK(r_dev && s_dev, PNOEOM_ERR_INVALID_ARG, "NULL vector");
-    PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32, PNOEOM_ERR_INVALID_ARG, "unknown precision");
+    PN_CHECK(precision == PNOEOM_FP64 || precision == PNOEOM_FP32 || precision == PNOEOM_BF16, PNOEOM_ERR_INVALID_ARG,
+             "unknown precision");
     const size_t elem = precision == PNOEOM_FP64 ? 8 : 4;
     const size_t need = (size_t)nvec * (size_t)pno->work_len * elem;
     PN_CHECK(need <= PNOEOM_NOALLOC_SCRATCH_BYTES, PNOEOM_ERR_UNSUPPORTED,
@@ -63,8 +64,8 @@ extern "C" int sigma_noalloc(pnoeom_ctx* ctx, const pnoeom_pno* pno, int nvec, c
     void* work = scratch_address(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     if (precision == PNOEOM_FP64)
-      sigma_into_scratch<double>(pno, nvec, (const double*)r_dev, (double*)s_dev, (double*)work, s);
+      sigma_into_scratch<double>(pno, nvec, (const double*)r_dev, (double*)s_dev, (double*)work, s, false);
     else
-      sigma_into_scratch<float>(pno, nvec, (const float*)r_dev, (float*)s_dev, (float*)work, s);
+      sigma_into_scratch<float>(pno, nvec, (const float*)r_dev, (float*)s_dev, (float*)work, s, precision == PNOEOM_BF16);
   });
 }

@@ -3,6 +3,7 @@
 #include "common.cuh"
 #include "engine.cuh"
 #include "sigma_prog.cuh"
+#include <cuda_bf16.h>
 #include <functional>
 #include <condition_variable>
 #include <deque>
@@ -73,6 +74,7 @@ struct pnoeom_pno {
   // sigma program
   pnoeom::DBuf<double> pool64;
   pnoeom::DBuf<float> pool32;
+  pnoeom::DBuf<__nv_bfloat16> pool16;          // BF16 copy (dense GEMV blocks of the BF16 sigma)
   pnoeom::Program prog;
   double tune_ms[pnoeom::NTUNE] = {0};
   static constexpr int NCLS = 6;             // kernel classes of the sigma program (timing)
@@ -88,6 +90,7 @@ struct pnoeom_pno {
   std::vector<double> last_X;
   int last_nroots = 0;
   int64_t last_sigma_evals[2] = {0, 0};   // FP32 / FP64 sigma evaluations of the last solve
+  std::vector<double> last_lowprec_w;     // Ritz values at the hand-over of the last mixed solve
   // per-call scratch kept across calls
   pnoeom::DBuf<double> work64; pnoeom::DBuf<float> work32;
   // tracing: per kernel class, operator elements read once per launch,
@@ -152,7 +155,7 @@ void batch_sigma(pnoeom_batch* B, const int* nvec, const void* const* r, void* c
 void batch_solve(pnoeom_batch* B, const pnoeom_opts* opts, cudaStream_t s, double* energies, double* res_norms,
                  int* iters, int* converged);
 // per-system launch entry of a sigma call
-SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32);
+SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32, bool bf16);
 // zero the outputs and work of every system in the table, then launch the program
 // (timing hook: if rec != nullptr, rec(cls, launch) wraps each kernel class)
 template <typename T>
@@ -161,7 +164,7 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
 void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts, cudaStream_t s,
                   pnoeom_pno* P);
 template <typename T>
-void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s);
+void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s, bool bf16);
 void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaStream_t s,
                   double* energies, double* res_norms, int* iters, int* converged);
 }  // namespace pnoeom

@@ -3,6 +3,7 @@
 #include <mutex>
 #include "sigma_prog.cuh"
 #include "tc.cuh"
+#include <cuda_bf16.h>
 
 namespace pnoeom {
 namespace {
@@ -943,59 +944,135 @@ __global__ void k_wait_selftest(long long budget, int* out) {
   }
 }
 
-constexpr int VR = 8;   // roots per pass inside a GEMV CTA
-
-// One (64-row, K-chunk) tile of one dense block per CTA (split-K, atomic
-// accumulation).  The K-chunk of every root's input vector is staged in shared
-// memory; each warp owns 8 rows and its lanes stride K, so the block rows are
-// read from HBM once, coalesced, for all roots.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
-  extern __shared__ unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);   // VR x GEMV_KC
-  const VProb P = probs[blockIdx.x];
-  const int nroots = tab.s[P.sys].nvec;
-  const T* A = (const T*)tab.s[P.sys].pool + P.a_off;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const T alpha = (T)P.alpha;
-  const int kl = P.klen;
-  for (int r0 = 0; r0 < nroots; r0 += VR) {
-    const int nr = min(VR, nroots - r0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < nr * kl; e += blockDim.x) {
-      const int q = e / kl, kk = e % kl;
-      int xk = P.k0 + kk;
-      if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
-      xs[q * GEMV_KC + kk] = cbuf<T>(tab, P.sys, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
-    }
-    __syncthreads();
-    for (int ml = warp; ml < 64; ml += 8) {
-      const int m = P.m0 + ml;
-      if (m >= P.M) break;
-      const T* a = A + (int64_t)m * P.lda + P.k0;
-      T acc[VR];
+// Dense block times vectors, one (GV_ROWS-row, K-chunk) tile of one block per CTA (split-K,
+// atomic accumulation).  The K chunk of up to R vectors is staged in shared memory (zero
+// beyond the block's K); each warp owns 4 rows and its lanes read 16-byte vectors of
+// consecutive columns, so a warp streams 512 contiguous bytes of every row per step while
+// each staged x vector is reused for 4 rows; the 4 x R partial sums stay in registers over
+// the whole chunk and are reduced across the warp once.  The pool rows must start on
+// 16-byte boundaries (block offsets and leading dimensions are multiples of 8 elements).
+// TA is the pool's element type: the arithmetic type T, or bf16 for the BF16 copy.
+template <typename TA> struct PoolVec;
+template <> struct PoolVec<float> {
+  static constexpr int N = 4;
+  __device__ static void load(const float* p, float (&v)[4]) { ld4(p, v); }
+};
+template <> struct PoolVec<double> {
+  static constexpr int N = 2;
+  __device__ static void load(const double* p, double (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+};
+template <> struct PoolVec<__nv_bfloat16> {
+  static constexpr int N = 8;
+  __device__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
+    const uint4 q = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-      for (int q = 0; q < VR; ++q) acc[q] = T(0);
-      for (int kk = lane; kk < kl; kk += 32) {
-        const T av = a[kk];
-#pragma unroll
-        for (int q = 0; q < VR; ++q) acc[q] += av * xs[q * GEMV_KC + kk];
-      }
-#pragma unroll
-      for (int q = 0; q < VR; ++q) {
-        T v = acc[q];
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        acc[q] = v;
-      }
-      if (lane == 0) {
-        int cm = m;
-        if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
-        for (int q = 0; q < nr; ++q)
-          atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[q]);
-      }
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[k]));
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
     }
   }
+};
+
+template <typename T, typename TA, int R>
+__device__ __forceinline__ void gemv_tile(const VProb& P, const SysTable& tab, T* xs) {
+  constexpr int VEC = PoolVec<TA>::N;
+  const int nroots = tab.s[P.sys].nvec;
+  const TA* A = (const TA*)(sizeof(TA) == 2 ? tab.s[P.sys].pool16 : tab.s[P.sys].pool) + P.a_off;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kl = P.klen, klp = (kl + VEC - 1) / VEC * VEC;
+  const T alpha = (T)P.alpha;
+  const TA* arow[4];
+  bool rv[4];
+#pragma unroll
+  for (int rr = 0; rr < 4; ++rr) {
+    const int m = P.m0 + warp * 4 + rr;
+    rv[rr] = m < P.M && warp * 4 + rr < GEMV_ROWS;
+    arow[rr] = A + (int64_t)(rv[rr] ? m : P.m0) * P.lda + P.k0;
+  }
+  for (int r0 = 0; r0 < nroots; r0 += R) {
+    const int nr = min(R, nroots - r0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * klp; e += blockDim.x) {
+      const int q = e / klp, kk = e - q * klp;
+      T val = T(0);
+      if (kk < kl) {
+        int xk = P.k0 + kk;
+        if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
+        val = cbuf<T>(tab, P.sys, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
+      }
+      xs[q * GEMV_KC + kk] = val;
+    }
+    __syncthreads();
+    T acc[4][R];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+      for (int q = 0; q < R; ++q) acc[rr][q] = T(0);
+    for (int kk = lane * VEC; kk < klp; kk += 32 * VEC) {
+      T a[4][VEC];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        if (rv[rr]) PoolVec<TA>::load(arow[rr] + kk, a[rr]);
+        else {
+#pragma unroll
+          for (int w = 0; w < VEC; ++w) a[rr][w] = T(0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        if (q < nr) {
+          const T* xq = xs + q * GEMV_KC + kk;
+#pragma unroll
+          for (int w = 0; w < VEC; ++w) {
+            const T xv = xq[w];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) acc[rr][q] += a[rr][w] * xv;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        T v = acc[rr][q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        acc[rr][q] = v;
+      }
+    // lane 4 * q + rr (q < R <= 8) adds the sum of row rr, vector q
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        if (lane == 4 * q + rr && rv[rr] && q < nr) {
+          const int m = P.m0 + warp * 4 + rr;
+          int cm = m;
+          if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
+          atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[rr][q]);
+        }
+  }
 }
+
+// In FP32 a system whose table entry carries the BF16 pool copy reads its blocks from it.
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);   // R x GEMV_KC
+  const VProb P = probs[blockIdx.x];
+  if constexpr (sizeof(T) == 4) {
+    if (tab.s[P.sys].pool16) gemv_tile<float, __nv_bfloat16, R>(P, tab, xs);
+    else gemv_tile<float, float, R>(P, tab, xs);
+  } else {
+    gemv_tile<T, T, R>(P, tab, xs);
+  }
+}
+
 
 }  // namespace
 
@@ -1028,9 +1105,10 @@ void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_e
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s) {
   if (nprob <= 0 || t.max_nvec <= 0) return;
-  const size_t smem = (size_t)VR * GEMV_KC * sizeof(T);
-  ensure_dynamic_smem((const void*)k_gemv<T>, smem);
-  k_gemv<T><<<nprob, 256, smem, s>>>(d_probs, t);
+  constexpr int R = sizeof(T) == 4 ? 8 : 4;
+  const size_t smem = (size_t)R * GEMV_KC * sizeof(T);
+  ensure_dynamic_smem((const void*)k_gemv<T, R>, smem);
+  k_gemv<T, R><<<nprob, 256, smem, s>>>(d_probs, t);
   PN_CUDA(cudaGetLastError());
 }
 

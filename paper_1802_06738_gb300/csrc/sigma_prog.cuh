@@ -51,13 +51,16 @@ struct VProb {
   double alpha;
 };
 
-constexpr int GEMV_KC = 1024;         // K chunk staged in shared memory per GEMV tile
+constexpr int GEMV_KC = 2048;         // K chunk staged in shared memory per GEMV tile
+constexpr int GEMV_ROWS = 32;         // rows of a GEMV tile
+constexpr int POOL_ALIGN = 8;         // GEMV blocks: offsets and leading dimensions are multiples of this
 constexpr int SMALL_DIM = 64;         // sandwich problems with all dims <= this use the shared-memory kernel
 
 // Per-system buffers of one launch.  nvec = number of vectors of that system
 // in this call (0: the system takes no part).
 struct SysBuf {
   const void* pool;
+  const void* pool16;                 // BF16 copy of the pool, or NULL: in FP32 a non-NULL copy is what the GEMV blocks read
   const void* rin; int64_t rin_stride;
   void* work; int64_t work_stride;
   void* sout; int64_t sout_stride;

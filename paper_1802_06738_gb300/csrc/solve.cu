@@ -21,9 +21,10 @@ static DBuf<T>& work_of(pnoeom_pno* P);
 template <> DBuf<double>& work_of<double>(pnoeom_pno* P) { return P->work64; }
 template <> DBuf<float>& work_of<float>(pnoeom_pno* P) { return P->work32; }
 
-SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32) {
+SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32, bool bf16) {
   SysBuf b{};
   b.pool = fp32 ? (const void*)P->pool32.get() : (const void*)P->pool64.get();
+  b.pool16 = fp32 && bf16 ? (const void*)P->pool16.get() : nullptr;
   b.rin = r; b.rin_stride = P->L;
   b.work = work; b.work_stride = P->work_len;
   b.sout = out; b.sout_stride = P->L;
@@ -174,20 +175,20 @@ template void run_program<double>(const Program&, const SysTable&, const int64_t
 template void run_program<float>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*);
 
 template <typename T>
-void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s) {
+void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s, bool bf16) {
   if (nvec <= 0) return;
   DBuf<T>& work = work_of<T>(P);
   const size_t need = (size_t)nvec * P->work_len;
   if (work.n < need) work.alloc(need, &P->footprint);
-  SysTable t;
+  SysTable t{};
   t.nsys = 1;
   t.max_nvec = nvec;
-  t.s[0] = sysbuf(P, nvec, r, out, work.get(), sizeof(T) == 4);
+  t.s[0] = sysbuf(P, nvec, r, out, work.get(), sizeof(T) == 4, bf16);
   const int64_t ol = P->L, wl = P->work_len;
   run_program<T>(P->prog, t, &ol, &wl, s, P);
 }
-template void apply_sigma<double>(pnoeom_pno*, int, const double*, double*, cudaStream_t);
-template void apply_sigma<float>(pnoeom_pno*, int, const float*, float*, cudaStream_t);
+template void apply_sigma<double>(pnoeom_pno*, int, const double*, double*, cudaStream_t, bool);
+template void apply_sigma<float>(pnoeom_pno*, int, const float*, float*, cudaStream_t, bool);
 
 // Autotuner: time the FP32 sigma of nroots_sa vectors for every candidate group size of the
 // grouped small-sandwich kernel and every roots-per-CTA choice (CUDA events on the build
@@ -198,10 +199,10 @@ void autotune(pnoeom_pno* P, cudaStream_t s) {
   r.zero(s);
   DBuf<float>& work = work_of<float>(P);
   if (work.n < (size_t)nv * P->work_len) work.alloc((size_t)nv * P->work_len, &P->footprint);
-  SysTable t;
+  SysTable t{};
   t.nsys = 1;
   t.max_nvec = nv;
-  t.s[0] = sysbuf(P, nv, r.get(), o.get(), work.get(), true);
+  t.s[0] = sysbuf(P, nv, r.get(), o.get(), work.get(), true, false);
   tune_sets<float>(P->prog, t, s, P->tune_ms);
   // diagnostic overrides of the tuned small-kernel variants (tests force each variant):
   // PNOEOM_SMALL_PB (2 or 4, sets whose problems all have A and B), PNOEOM_SMALL_SHAPE
@@ -437,11 +438,11 @@ struct Dav {
   }
   void sigma(const double* V, double* S, int nv, int prec) {
     if (!nv) return;
-    if (prec == PNOEOM_FP64) { apply_sigma<double>(P, nv, V, S, s); return; }
+    if (prec == PNOEOM_FP64) { apply_sigma<double>(P, nv, V, S, s, false); return; }
     size_t n = (size_t)nv * L;
     if (f_in.n < n) { f_in.alloc(n); f_out.alloc(n); }
     k_d2f_<<<gsz(n), 256, 0, s>>>(f_in.get(), V, n);
-    apply_sigma<float>(P, nv, f_in.get(), f_out.get(), s);
+    apply_sigma<float>(P, nv, f_in.get(), f_out.get(), s, prec == PNOEOM_BF16);
     k_f2d_<<<gsz(n), 256, 0, s>>>(S, f_out.get(), n);
     PN_CUDA(cudaGetLastError());
   }
@@ -491,6 +492,8 @@ struct DavState {
   double res_tol, e_tol;
   bool refine;
   int prec;
+  bool bf16 = false;        // the low-precision phase reads the BF16 pool copy for its dense blocks
+  double switch_res = 1e-4; // level below which a stalled low-precision phase hands over to FP64
   Dav D;
   DBuf<double> V, S, X, R;
   DBuf<float> fin, fout;    // FP32 copies of the pending vectors and their sigma
@@ -500,9 +503,8 @@ struct DavState {
   bool done = false, converged = false;
   bool trace = std::getenv("PNOEOM_LOG_DAVIDSON") != nullptr;
   std::vector<double> w, rn, w_old;
+  std::vector<double> w_lowprec;   // Ritz values when the low-precision phase handed over (mixed solves)
   std::vector<double> rhist;   // largest residual norm of every FP32 iteration (mixed solves)
-  // Level below which a stalled FP32 phase hands over to the FP64 refinement.
-  static constexpr double SWITCH_RES = 1e-4;
 
   DavState(pnoeom_pno* P_, const pnoeom_opts* opts, cudaStream_t s_) : P(P_), s(s_), L(P_->L), D{P_, s_, P_->L} {
     nroots = opts->nroots_solve;
@@ -512,10 +514,14 @@ struct DavState {
     max_iter = opts->max_iter > 0 ? opts->max_iter : 100;
     res_tol = opts->res_tol > 0 ? opts->res_tol : 1e-7;
     e_tol = opts->e_tol > 0 ? opts->e_tol : 1e-10;
-    prec = opts->precision == PNOEOM_FP32 ? PNOEOM_FP32 : PNOEOM_FP64;
+    prec = (opts->precision == PNOEOM_FP32 || opts->precision == PNOEOM_BF16) ? PNOEOM_FP32 : PNOEOM_FP64;
+    bf16 = opts->precision == PNOEOM_BF16;
+    // the BF16 blocks carry about 3 significant digits, so that phase stalls far above the
+    // FP32 one's floor and hands over as soon as its residuals stop halving below 0.1
+    switch_res = bf16 ? 1e-1 : 1e-4;
     refine = prec == PNOEOM_FP32 && opts->refine_fp64;
     // mixed precision: the FP32 phase aims at the final residual tolerance too and hands
-    // over to the FP64 refinement when that holds or, below SWITCH_RES, when its largest
+    // over to the FP64 refinement when that holds or, below switch_res, when its largest
     // residual stops halving within three iterations (the error floor of the FP32 sigma)
     std::vector<int64_t> offs;
     std::vector<int> ns;
@@ -577,7 +583,7 @@ struct DavState {
       for (double x : rn) rmax = std::max(rmax, x);
       rhist.push_back(rmax);
       const size_t k = rhist.size();
-      if (rmax < SWITCH_RES && k >= 4 && rmax > 0.5 * rhist[k - 4]) { finish_or_refine(); return; }
+      if (rmax < switch_res && k >= 4 && rmax > 0.5 * rhist[k - 4]) { finish_or_refine(); return; }
     }
     std::vector<int> add;
     for (int q = 0; q < nr; ++q) if (rn[q] >= res_tol) add.push_back(q);
@@ -628,6 +634,7 @@ struct DavState {
     if (prec == PNOEOM_FP32 && refine) {
       // FP64 refinement, started from the current Ritz vectors: the subspace collapses onto
       // them (orthonormalised) and only their sigma is evaluated again, in FP64
+      w_lowprec = w;
       prec = PNOEOM_FP64;
       w_old.clear();
       int mm = 0;
@@ -728,14 +735,14 @@ void eval_states(const Program& prog, std::vector<DavState*>& st, const std::vec
     if (prec == PNOEOM_FP64) {
       DBuf<double>& w = (*work64)[k];
       if (w.n < need) w.alloc(need);
-      t.s[k] = sysbuf(d->P, n, d->V.get() + (int64_t)d->p0 * d->L, d->S.get() + (int64_t)d->p0 * d->L, w.get(), false);
+      t.s[k] = sysbuf(d->P, n, d->V.get() + (int64_t)d->p0 * d->L, d->S.get() + (int64_t)d->p0 * d->L, w.get(), false, false);
     } else {
       DBuf<float>& w = (*work32)[k];
       if (w.n < need) w.alloc(need);
       const size_t len = (size_t)n * d->L;
       if (d->fin.n < len) { d->fin.alloc(len); d->fout.alloc(len); }
       d2f(d->fin.get(), d->V.get() + (int64_t)d->p0 * d->L, len, s);
-      t.s[k] = sysbuf(d->P, n, d->fin.get(), d->fout.get(), w.get(), true);
+      t.s[k] = sysbuf(d->P, n, d->fin.get(), d->fout.get(), w.get(), true, d->bf16);
     }
   }
   if (prec == PNOEOM_FP64) run_program<double>(prog, t, ol.data(), wl.data(), s, timing_owner);
@@ -758,6 +765,7 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
   d.results(energies, res_norms, iters);
   P->last_sigma_evals[0] = d.sigma_evals_prec[0];
   P->last_sigma_evals[1] = d.sigma_evals_prec[1];
+  P->last_lowprec_w = d.w_lowprec;
   *converged = d.converged ? 1 : 0;
 }
 
@@ -833,7 +841,7 @@ void batch_merge(pnoeom_batch* B, cudaStream_t s, bool tune) {
     r[k].zero(s);
     if (B->w32[k].n < (size_t)nv * P->work_len) B->w32[k].alloc((size_t)nv * P->work_len);
     t.max_nvec = std::max(t.max_nvec, nv);
-    t.s[k] = sysbuf(P, nv, r[k].get(), o[k].get(), B->w32[k].get(), true);
+    t.s[k] = sysbuf(P, nv, r[k].get(), o[k].get(), B->w32[k].get(), true, false);
   }
   tune_sets<float>(G, t, s, B->tune_ms);
 }
@@ -890,7 +898,7 @@ void batch_sigma(pnoeom_batch* B, const int* nvec, const void* const* r, void* c
     void* w;
     if (prec == PNOEOM_FP64) { if (B->w64[k].n < need) B->w64[k].alloc(need); w = B->w64[k].get(); }
     else { if (B->w32[k].n < need) B->w32[k].alloc(need); w = B->w32[k].get(); }
-    t.s[k] = sysbuf(P, nv, r[k], out[k], w, prec == PNOEOM_FP32);
+    t.s[k] = sysbuf(P, nv, r[k], out[k], w, prec != PNOEOM_FP64, prec == PNOEOM_BF16);
   }
   graph_launch(B, s, [&] {
     if (prec == PNOEOM_FP64) run_program<double>(B->prog, t, ol.data(), wl.data(), s, nullptr);
