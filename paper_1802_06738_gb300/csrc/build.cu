@@ -279,11 +279,16 @@ void eig_lowest_davidson(cusolverDnHandle_t h, cudaStream_t s, const double* A, 
     for (int k = 0; k < nb; ++k) {
       if (res[k] <= tol * 1e-3) continue;
       std::vector<double> tk(n);
+      double n0 = 0;
       for (int64_t e = 0; e < n; ++e) {
         double den = ev[k] - diag[e];
         if (std::fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
         tk[e] = tr[(size_t)k * n + e] / den;
+        n0 += tk[e] * tk[e];
       }
+      n0 = std::sqrt(n0);
+      if (!(n0 > 0)) continue;
+      for (double& x : tk) x /= n0;   // unit length before the projection: what survives it is new
       DBuf<double> tv(n), ov(m + added);
       tv.upload(tk.data(), n, s);
       for (int pass = 0; pass < 2; ++pass) {
@@ -295,7 +300,7 @@ void eig_lowest_davidson(cusolverDnHandle_t h, cudaStream_t s, const double* A, 
       double nrm = 0;
       for (double x : tk) nrm += x * x;
       nrm = std::sqrt(nrm);
-      if (nrm < 1e-8) continue;
+      if (nrm < 1e-6) continue;
       for (double& x : tk) x /= nrm;
       PN_CUDA(cudaMemcpyAsync(V.get() + (size_t)(m + added) * n, tk.data(), n * 8, cudaMemcpyHostToDevice, s));
       PN_CUDA(cudaStreamSynchronize(s));

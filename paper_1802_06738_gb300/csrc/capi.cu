@@ -136,11 +136,14 @@ int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, cons
       PN_CUDA(cudaEventElapsedTime(&x, e.second.first, e.second.second));
       t += x; ++n;   // n: sigma calls recorded
     }
-    const double es = precision == PNOEOM_FP32 ? 4.0 : 8.0;
+    // element sizes: vectors 8 (FP64) or 4 bytes; operator blocks likewise, except the dense
+    // GEMV blocks of the BF16 sigma (classes 1 and 3), read as 2-byte BF16
+    const double es = precision == PNOEOM_FP64 ? 8.0 : 4.0;
+    const double ep = precision == PNOEOM_BF16 && (k == 1 || k == 3) ? 2.0 : es;
     if (name) *name = names[k];
     if (launches) *launches = pno->prof_launches[k];
     if (ms) *ms = t;
-    if (bytes) *bytes = es * (pno->prof_pool_elems[k] + (double)nvec * pno->prof_vec_elems[k]);
+    if (bytes) *bytes = ep * pno->prof_pool_elems[k] + es * (double)nvec * pno->prof_vec_elems[k];
     if (flops) *flops = (double)nvec * pno->prof_flops[k];
   });
 }

@@ -50,10 +50,23 @@ def test_traffic_reported_only_for_the_captured_kernel_source(tmp_path, monkeypa
     kernel = src / "sigma_kernels.cu"
     kernel.write_text("// kernel v1\n")
     digest = hashlib.sha256(kernel.read_bytes()).hexdigest()
-    (tmp_path / "profiles" / "sandwich_sigma_traffic_medium.md").write_text(
+    (tmp_path / "profiles" / "sigma_traffic_medium.md").write_text(
         f"traffic per call (bytes): sandwich->sigma = 1234\n\nkernel source sha256: {digest}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic("sandwich->sigma") == 1234.0
-    assert bench.ncu_traffic("dense->sigma") is None
+    assert bench.ncu_traffic("sandwich->sigma", "medium") == 1234.0
+    assert bench.ncu_traffic("dense->sigma", "medium") is None
+    assert bench.ncu_traffic("sandwich->sigma", "large") is None     # no capture of that workload
     kernel.write_text("// kernel v2\n")
-    assert bench.ncu_traffic("sandwich->sigma") is None
+    assert bench.ncu_traffic("sandwich->sigma", "medium") is None
+
+
+def test_reference_arm_prints_the_same_metric(capsys):
+    """The oracle arm uses the GPU arm's metric string; for a workload the oracle cannot
+    reach within the run it prints its unavailable line with the reason."""
+    import types
+    args = types.SimpleNamespace(workload="large", steps=3, warmup=1, gpus=1)
+    bench.run_reference(args, 1, 0)
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert "unavailable" in line and "o=60" in line["config"]["workload"]

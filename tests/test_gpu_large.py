@@ -1,0 +1,88 @@
+"""The large workload at full size on the GPU (o = 60, v = 600, naux = 1800, 6 roots,
+T_CutPNO = 1e-7, MP1 T2, seed 3; the BF16 sigma with FP64 refinement of Sec. 2's
+Davidson, the configuration the benchmark times).
+
+Oracle results come from tests/golden/oracle_large.json (written by
+tests/golden/make_golden.py large --pno-only, which calls only oracle/):
+  * the PNO/OSV counts (compared exactly) and the six CIS energies;
+the oracle's sigma and Davidson energies are not available at this size, so the
+rest is checked through properties that hold at any size:
+  * sigma is linear (FP64, to rounding);
+  * the FP32 and BF16 sigma agree with the FP64 one within the bounds their
+    number formats give;
+  * the BF16 + FP64-refinement solve reaches the FP64 solve's energies (|dE| <= 1e-5 Eh,
+    the pass bar of this workload) and every refined residual is below res_tol.
+The build takes a few minutes; the module builds once.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden", "oracle_large.json")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def large():
+    import paper_1802_06738_gb300 as pkg
+    from synthetic import make_system
+    gold = json.load(open(GOLD))
+    pkg.build()
+    ctx = pkg.Context(0)
+    s = make_system(gold["o"], gold["v"], gold["naux"], gold["seed"])
+    opts = pkg.make_opts(t_pno=gold["t_pno"], nroots=gold["nroots"], precision=pkg.BF16, refine_fp64=1)
+    gp = pkg.PNO(ctx, s["eps"], s["B"], gold["o"], opts=opts)
+    del s
+    return pkg, ctx, gp, gold
+
+
+def test_large_pno_counts_and_cis(large):
+    _, _, gp, gold = large
+    assert np.array_equal(np.asarray(gp.n_ij), np.asarray(gold["n_ij"]))
+    assert np.array_equal(np.asarray(gp.n_i), np.asarray(gold["n_i"]))
+    assert gp.length == gold["vec_len"]
+    assert np.abs(gp.cis_energies() - np.asarray(gold["cis_energies"])).max() < 1e-10
+
+
+def test_large_sigma_linear_and_precisions(large):
+    pkg, _, gp, _ = large
+    g = torch.Generator(device="cuda:0").manual_seed(11)
+    x = torch.randn(2, gp.length, device="cuda:0", dtype=torch.float64, generator=g)
+    sx = torch.empty_like(x)
+    gp.sigma(x, sx, precision=pkg.FP64)
+    comb = (0.7 * x[0] - 1.3 * x[1])[None, :].contiguous()
+    sc = torch.empty_like(comb)
+    gp.sigma(comb, sc, precision=pkg.FP64)
+    ref = 0.7 * sx[0] - 1.3 * sx[1]
+    scale = float(ref.abs().max())
+    assert float((sc[0] - ref).abs().max()) <= 1e-11 * scale
+    x32 = x.float()
+    for prec, tol in ((pkg.FP32, 1e-5), (pkg.BF16, 2e-2)):
+        s32 = torch.empty_like(x32)
+        gp.sigma(x32, s32, precision=prec)
+        torch.cuda.synchronize()
+        err = float((s32.double() - sx).abs().max()) / float(sx.abs().max())
+        assert err <= tol, (prec, err)
+
+
+def test_large_bf16_refined_energies_match_fp64(large):
+    pkg, ctx, gp, gold = large
+    nr = gold["nroots"]
+    e64, rn64, it64, c64 = gp.davidson_solve(pkg.make_opts(t_pno=gold["t_pno"], nroots=nr, precision=pkg.FP64,
+                                                           max_iter=300))
+    assert c64 and np.all(rn64 < 1e-7)
+    e, rn, it, conv = gp.davidson_solve(pkg.make_opts(t_pno=gold["t_pno"], nroots=nr, precision=pkg.BF16,
+                                                      refine_fp64=1, max_iter=300))
+    assert conv and np.all(rn < 1e-7)
+    assert np.abs(e - e64).max() <= 1e-5
+    low = gp.lowprec_energies()
+    assert len(low) == nr and np.all(np.isfinite(low))
+    # lowest excitation energies above zero and below the CIS ones plus a few eV
+    assert np.all(e > 0) and np.all(np.diff(e) >= -1e-12)
+    assert ctx.device_status() == 0
