@@ -15,6 +15,9 @@ eom           EOM-CCSD sigma: Jacobian-vector definition and explicit terms
 pno           CIS, CIS(D) doubles, state-averaged pair densities, PNOs/OSVs,
               projector and packed PNO vector layout
 davidson      non-symmetric Davidson solver with the PNO-space preconditioner
+pno_direct    the PNO-space sigma evaluated pair by pair from projected blocks and DF
+              factors, without canonical R2/sigma2 or three- and four-virtual integrals
+              ("O2"; pinned against pno.PNOSigma)
 
 Parity status: every function here is pinned by a test under ``tests/``
 against brute force, a closed form, an invariant or a textbook special case,
