@@ -487,7 +487,7 @@ def main():
 
     # --- full Davidson solves: latency (mixed + FP64 refinement, and plain FP64)
     lat_mixed, lat_fp64 = [], []
-    e_mixed = e_fp64 = e_low = None
+    e_mixed = e_fp64 = e_low = e_low16 = None
     it_mixed = it_fp64 = None
     rn_mixed = rn_fp64 = None
     ev_mixed = ev_fp64 = {"fp32": 0, "fp64": 0}
@@ -497,7 +497,8 @@ def main():
         e_mixed, rn_mixed, it_mixed, conv_m = gp.davidson_solve(opts_mixed, stream=stream)
         torch.cuda.synchronize(); lat_mixed.append(time.perf_counter() - t0)
         ev_mixed = gp.solve_stats()
-        e_low = gp.lowprec_energies()
+        e_low = gp.lowprec_energies(pkg.FP32)
+        e_low16 = gp.lowprec_energies(pkg.BF16) if w["mixed"] == "BF16" else []
         t0 = time.perf_counter()
         e_fp64, rn_fp64, it_fp64, conv_64 = gp.davidson_solve(opts_fp64, stream=stream)
         torch.cuda.synchronize(); lat_fp64.append(time.perf_counter() - t0)
@@ -640,8 +641,10 @@ def main():
         "solve": {"mixed_refined": {**lat(lat_mixed), "iterations": it_mixed, **in_solve(ev_mixed, lat_mixed),
                                     "energies": list(map(float, e_mixed)),
                                     "residual_norms": list(map(float, rn_mixed)),
-                                    "unrefined_energies": list(map(float, e_low)),
-                                    "unrefined_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low, e_fp64)]},
+                                    "unrefined_fp32_phase_energies": list(map(float, e_low)),
+                                    "unrefined_fp32_phase_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low, e_fp64)],
+                                    "unrefined_bf16_phase_energies": list(map(float, e_low16)),
+                                    "unrefined_bf16_phase_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low16, e_fp64)]},
                   "fp64": {**lat(lat_fp64), "iterations": it_fp64, **in_solve(ev_fp64, lat_fp64),
                            "energies": list(map(float, e_fp64)), "residual_norms": list(map(float, rn_fp64))},
                   "max_abs_dE_mixed_vs_fp64": float(np.abs(np.asarray(e_mixed) - np.asarray(e_fp64)).max()),

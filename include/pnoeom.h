@@ -87,10 +87,11 @@ typedef struct {
  * t_osv: T_CutOSV, < 0 means t_pno / 10 (Sec. 3).  nroots_sa: N of the state
  * average (Eq. eom:sa_density); nroots_solve: roots returned by the solver
  * (<= nroots_sa).  precision: PNOEOM_FP64, PNOEOM_FP32 or PNOEOM_BF16 sigma;
- * refine_fp64: the low-precision (FP32 or BF16) phase aims at res_tol and hands over
- * to FP64 sigma when that holds, when its largest residual (below 1e-4 in FP32, 1e-1 in
- * BF16) stops halving within three iterations, or when no new direction survives; the
- * FP64 phase then restarts from the N Ritz vectors and runs until the FP64 tolerances
+ * refine_fp64: the low-precision phase aims at res_tol and hands over to the next
+ * precision (BF16 -> FP32 -> FP64 for PNOEOM_BF16, FP32 -> FP64 for PNOEOM_FP32) when that
+ * holds, when its largest residual (below 1e-1 in BF16, 1e-4 in FP32) stops halving
+ * within three iterations, or when no new direction survives; each phase restarts from
+ * the N Ritz vectors of the last, and the FP64 phase runs until the FP64 tolerances
  * hold.  res_tol: residual 2-norm per root; e_tol: eigenvalue
  * change between iterations; max_subspace <= 0 means 8 * nroots_solve.
  * state_specific: 0 (the default, and the paper's method) builds state-averaged
@@ -263,11 +264,14 @@ int pnoeom_server_stats(pnoeom_server* srv, size_t* used_bytes, int* queued, int
  * vectors on the host (nroots_solve * vec_len doubles). */
 int pno_get_eigenvectors(const pnoeom_pno* pno, double* X);
 
-/* Ritz values of the last davidson_solve on this handle at the moment its
- * low-precision phase (FP32 or BF16, refine_fp64 set) handed over to the FP64
- * refinement: the unrefined energies, ascending.  Writes min(n, count) doubles and the
- * number available in *count (0 when the last solve had no such phase).  Host-only. */
-int pno_solve_lowprec_energies(const pnoeom_pno* pno, int n, double* energies, int* count);
+/* Ritz values of the last davidson_solve on this handle at the moment one of its
+ * low-precision phases handed over (refine_fp64 set): phase = PNOEOM_BF16, when the BF16
+ * phase of a PNOEOM_BF16 solve handed over to its FP32 phase; PNOEOM_FP32, when the FP32
+ * phase (of a PNOEOM_FP32 solve, or the second phase of a PNOEOM_BF16 one) handed over to
+ * the FP64 refinement.  These are the unrefined energies of that precision, ascending.
+ * Writes min(n, count) doubles and the number available in *count (0 when the last solve
+ * had no such phase).  Host-only. */
+int pno_solve_lowprec_energies(const pnoeom_pno* pno, int phase, int n, double* energies, int* count);
 
 /* Sigma evaluations (one vector of one root each) of the last davidson_solve on
  * this handle, split by the precision they ran in: FP32 (the mixed phase) and

@@ -169,10 +169,16 @@ def denominators(eps, o):
 
 def mp1_t2(eps, B, o):
     """First-order amplitudes t^{ab}_{ij} = (ai|bj) / (f_ii + f_jj - f_aa - f_bb)
-    (Eq. T1 of the paper: G^{ij}_{ab} = <ab|ij> = (ai|bj))."""
-    g = np.einsum("Qai,Qbj->ijab", B[:, o:, :o], B[:, o:, :o], optimize=True)
-    _, d2 = denominators(eps, o)
-    return g / d2
+    (Eq. T1 of the paper: G^{ij}_{ab} = <ab|ij> = (ai|bj)).  Formed one occupied i at a
+    time (the same sums; it keeps the large systems within host memory)."""
+    v = len(eps) - o
+    eo, ev = eps[:o], eps[o:]
+    Bia = np.ascontiguousarray(B[:, o:, :o].transpose(0, 2, 1))      # [Q, i, a] = B[Q, a, i]
+    t = np.empty((o, o, v, v))
+    for i in range(o):
+        g = np.einsum("Qa,Qjb->jab", Bia[:, i, :], Bia, optimize=True)   # (ai|bj)
+        t[i] = g / (eo[i] + eo[:, None, None] - ev[None, :, None] - ev[None, None, :])
+    return t
 
 
 def solve_ccsd(eps, B, o, tol=1e-11, maxiter=200):

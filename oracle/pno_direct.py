@@ -49,10 +49,11 @@ class PNOSigmaDirect:
         self.Boo = np.ascontiguousarray(Bd[:, :o, :o])
         self.Bov = np.ascontiguousarray(Bd[:, :o, o:])
         self.Bvo = np.ascontiguousarray(Bd[:, o:, :o])
-        self.Bvv = np.ascontiguousarray(Bd[:, o:, o:])
+        self.Bvv = Bd[:, o:, o:]
         nq = self.Bov.shape[0]
         self.t = t2
-        self.u = 2.0 * t2 - t2.swapaxes(2, 3)
+        self.u = np.multiply(t2, 2.0)
+        self.u -= t2.swapaxes(2, 3)                                   # u = 2 t - t(ab swapped)
         # (kc|ld) at [k,c,l,d]
         Bm = self.Bov.reshape(nq, o * v)
         self.g = np.empty((o * v, o * v))

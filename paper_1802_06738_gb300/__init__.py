@@ -96,7 +96,7 @@ def lib():
         L.davidson_solve.argtypes = [vp, vp, ctypes.POINTER(Opts), vp, dp, dp, ip]
         L.pno_get_eigenvectors.argtypes = [vp, dp]
         L.pno_solve_stats.argtypes = [vp, i64p, i64p]
-        L.pno_solve_lowprec_energies.argtypes = [vp, i, dp, ip]
+        L.pno_solve_lowprec_energies.argtypes = [vp, i, i, dp, ip]
         L.pno_get_cis.argtypes = [vp, dp]
         L.pno_get_occupations.argtypes = [vp, dp]
         L.pno_get_cis_vectors.argtypes = [vp, dp]
@@ -313,13 +313,14 @@ class PNO:
         _check(lib().pno_solve_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
         return dict(fp32=a.value, fp64=b.value)
 
-    def lowprec_energies(self):
-        """Ritz values of the last solve when its FP32/BF16 phase handed over to FP64 (or [])."""
+    def lowprec_energies(self, phase=FP32):
+        """Ritz values of the last solve when its BF16 (phase=BF16) or FP32 (phase=FP32)
+        phase handed over to the next precision (or [])."""
         import numpy as np
         n = ctypes.c_int()
-        _check(lib().pno_solve_lowprec_energies(self.h, 0, None, ctypes.byref(n)))
+        _check(lib().pno_solve_lowprec_energies(self.h, phase, 0, None, ctypes.byref(n)))
         e = np.zeros(max(1, n.value))
-        _check(lib().pno_solve_lowprec_energies(self.h, n.value, _dptr(e), ctypes.byref(n)))
+        _check(lib().pno_solve_lowprec_energies(self.h, phase, n.value, _dptr(e), ctypes.byref(n)))
         return e[:n.value]
 
     def eigenvectors(self):

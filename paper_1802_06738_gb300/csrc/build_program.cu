@@ -96,6 +96,17 @@ __global__ void k_asym_flag(int* flag, const double* B, int nq, int v) {
   }
 }
 
+// tb[l,k] = tb[k,l]^T for l > k (blocks of n x n, [k][l][A][B])
+__global__ void k_mirror_lower(double* tb, int o, int n) {
+  GRID_STRIDE(e, (int64_t)o * o * n * n) {
+    const int64_t blk = e / ((int64_t)n * n);
+    const int l = (int)(blk / o), k = (int)(blk % o);   // block [l][k]
+    if (l <= k) continue;
+    const int r = (int)(e % ((int64_t)n * n)), A = r / n, B = r % n;
+    tb[e] = tb[((int64_t)k * o + l) * n * n + (int64_t)B * n + A];
+  }
+}
+
 struct Prog {
   pnoeom_pno* P;
   cudaStream_t s;
@@ -365,6 +376,8 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     offG4[x * o + y] = take_al(O * pad(nn * nn));
     offT4[x * o + y] = take_al(nn * nn * Op);
   }
+  // Lv1 (v^2 x L1): the R1 part of the virtual global term, applied per call into FvR
+  const int64_t off_Lv1 = take_al(V * V * L1p);
   std::vector<int64_t> offD(npairs), offADS(npairs);
   for (int p = 0; p < npairs; ++p) offD[p] = take_al(nP(p) * nP(p) * pad(nP(p) * nP(p)));
   for (int p = 0; p < npairs; ++p) offADS[p] = take_al(nP(p) * nP(p) * L1p);
@@ -481,6 +494,8 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   // R1 column blocks shared by all pairs: Lv1[b,c,(m,D)] = sum_d (2 (bc|md) - (bd|mc)) U^m[d,D],
   // GamAll[y][k][(m,D)] = sum_d (2 (ky|md) - (kd|my)) U^m[d,D]
   DV Lv1(std::max<int64_t>(1, V * V * L1)), GamAll(std::max<int64_t>(1, O * O * L1));
+  // Lv1 is also a pool block (rows b*v + c, padded): sum_L Lv1[b,c,L] r_L is the v x v R1 part
+  // of the E3 factor (it adds to FvR; the E3 products then apply t projected on both sides)
   if (L1 > 0) {
     Dims d = G.dm;
     d['L'] = L1;
@@ -503,6 +518,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       G.con(dm2, "QbD", BUm.get(), "Qc", Bm.get(), "bcD", tmp.get());
       G.add_block(Lv1.get() + P->off_i[m], L1, tmp.get(), nm, (int)(V * V), nm, -1.0);
     }
+    PN_CUDA(cudaMemcpy2DAsync(pl + off_Lv1, L1p * 8, Lv1.get(), L1 * 8, L1 * 8, V * V, cudaMemcpyDeviceToDevice, s));
     std::vector<GemmProb<double>> pr;
     for (int m = 0; m < o; ++m) {
       if (!G.no(m)) continue;
@@ -546,8 +562,22 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     {
       DV gb(O * O * nn * nn), X(O * O * V * nn);
       G.con(d, "QkC", Bh.get(), "QlD", Bh.get(), "klCD", gb.get());
-      G.con(d, "klab", t, "bB", Up, "klaB", X.get());
-      G.con(d, "aA", Up, "klaB", X.get(), "klAB", tb.get());
+      // tb[kl] = U^T t[k,l] U for k <= l; tb[lk] = tb[kl]^T (t[l,k] = t[k,l]^T)
+      {
+        std::vector<GemmProb<double>> pr;
+        for (int k = 0; k < o; ++k)   // X[k,l,a,B] = sum_b t[k,l,a,b] U[b,B], l >= k
+          pr.push_back({t + ((int64_t)k * o + k) * V * V, Up, X.get() + ((int64_t)k * o + k) * V * nn, (o - k) * v, nn, v, v,
+                        nn, nn, 0, 0, 1.0, 0.0});
+        grouped_gemm<double>(pr, s);
+        pr.clear();
+        for (int k = 0; k < o; ++k)
+          for (int l = k; l < o; ++l)
+            pr.push_back({Up, X.get() + ((int64_t)k * o + l) * V * nn, tb.get() + ((int64_t)k * o + l) * nn * nn, nn, nn, v,
+                          nn, nn, nn, 1, 0, 1.0, 0.0});
+        grouped_gemm<double>(pr, s);
+        k_mirror_lower<<<gsz((size_t)o * o * nn * nn), 256, 0, s>>>(tb.get(), o, nn);
+        PN_CUDA(cudaGetLastError());
+      }
       G.con(d, "klAB", tb.get(), "klCD", gb.get(), "ABCD", Dp, 1.0, 1.0);
     }
     DV Fb(nn * nn);
@@ -695,10 +725,8 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
         G.add_block(Yc.get() + P->off_i[y], L1, K3.get(), ny, nn * nn, ny, 1.0);
       }
       if (L1 > 0) {
-        // Lambda: sum_c t[x,y,a,c] (2 (bc|md) - (bd|mc)) U^m[d,D]
-        DV T2(nn * V * L1);
-        G.con(d, "Ac", pl + offTh[x * o + y], "bcL", Lv1.get(), "AbL", T2.get());
-        G.con(d, "AbL", T2.get(), "bB", Up, "ABL", Yc.get(), 1.0, 1.0);
+        // (the Lambda term, sum_c t[x,y,a,c] sum_{m,d} (2 (bc|md) - (bd|mc)) r_m,d, is applied per
+        // call through FvR: see Lv1 above)
         // e2m: - sum_k tb3[x,k,y] Gam_y[k, L]
         G.con(d, "kAB", tb3[x * o + y].get(), "kL", GamAll.get() + (int64_t)y * O * L1, "ABL", Yc.get(), -1.0, 1.0);
         // qb kron: S(xy,m)[A,C] qb[x,y,m][B], qb = sum_b Qb[m,x,y,b] U[b,B] with
@@ -929,6 +957,9 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   }
   add_dense(G.dp1, DENSE_TILE_TC, 256, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, off_Ucat, (int)nsum, 0, (int)nsum, B_WORK, P->work_y, v,
             0, -1.0);
+  // FvR[b,c] += sum_L Lv1[b,c,L] r1_L (the Lambda term of the singles couplings)
+  if (L1 > 0)
+    add_gemv(G.vp1, off_Lv1, (int)(V * V), (int)L1, (int)L1p, B_RIN, 0, 1, 0, B_WORK, P->work_fvr, 1, 0, 1.0);
   // Phase 2 prologue: Z = FvR^T U_cat (v x sum n_p), read by the E3 products below
   add_dense(G.dp2, DENSE_TILE_TC, 1 << 30, B_WORK, P->work_z, (int)nsum, 0, v, (int)nsum, B_WORK, P->work_fvr, v, 1, v, B_POOL, off_Ucat,
             (int)nsum, 0, 1.0);

@@ -310,12 +310,14 @@ int pno_get_eigenvectors(const pnoeom_pno* pno, double* X) {
   });
 }
 
-int pno_solve_lowprec_energies(const pnoeom_pno* pno, int n, double* energies, int* count) {
+int pno_solve_lowprec_energies(const pnoeom_pno* pno, int phase, int n, double* energies, int* count) {
   return guard([&] {
     PN_CHECK(pno && (n <= 0 || energies), PNOEOM_ERR_INVALID_ARG, "NULL argument");
-    const int c = (int)pno->last_lowprec_w.size();
+    PN_CHECK(phase == PNOEOM_BF16 || phase == PNOEOM_FP32, PNOEOM_ERR_INVALID_ARG, "phase must be PNOEOM_BF16 or PNOEOM_FP32");
+    const std::vector<double>& w = pno->last_phase_w[phase == PNOEOM_BF16 ? 0 : 1];
+    const int c = (int)w.size();
     if (count) *count = c;
-    for (int k = 0; k < std::min(n, c); ++k) energies[k] = pno->last_lowprec_w[k];
+    for (int k = 0; k < std::min(n, c); ++k) energies[k] = w[k];
   });
 }
 

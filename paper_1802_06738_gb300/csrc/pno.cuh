@@ -90,7 +90,7 @@ struct pnoeom_pno {
   std::vector<double> last_X;
   int last_nroots = 0;
   int64_t last_sigma_evals[2] = {0, 0};   // FP32 / FP64 sigma evaluations of the last solve
-  std::vector<double> last_lowprec_w;     // Ritz values at the hand-over of the last mixed solve
+  std::vector<double> last_phase_w[2];    // Ritz values when the BF16 / FP32 phase of the last mixed solve handed over
   // per-call scratch kept across calls
   pnoeom::DBuf<double> work64; pnoeom::DBuf<float> work32;
   // tracing: per kernel class, operator elements read once per launch,

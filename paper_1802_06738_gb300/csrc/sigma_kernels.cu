@@ -1138,6 +1138,7 @@ static void launch_small(const SProb* d_probs, const int* d_group_start, int ngr
   int nb = (smem_of(rpc, 2) > two_per_sm && smem_of(rpc, 1) <= two_per_sm) ? 1 : 2;
   if (nbsel == 1 || nbsel == 2) nb = nbsel;
   while (rpc > 1 && smem_of(rpc, nb) > limit) --rpc;
+  if (nb == 2 && smem_of(rpc, 2) > limit) nb = 1;   // the tuned double buffering does not fit (FP64)
   PN_CHECK(smem_of(rpc, nb) <= limit && tiles <= NT * MAXT, PNOEOM_ERR_UNSUPPORTED,
            "PNO blocks too large for the grouped sandwich kernel");
   if (nb == 2)

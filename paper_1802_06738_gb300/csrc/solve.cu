@@ -492,8 +492,8 @@ struct DavState {
   double res_tol, e_tol;
   bool refine;
   int prec;
-  bool bf16 = false;        // the low-precision phase reads the BF16 pool copy for its dense blocks
-  double switch_res = 1e-4; // level below which a stalled low-precision phase hands over to FP64
+  bool bf16 = false;        // the current low-precision phase reads the BF16 pool copy for its dense blocks
+  double switch_res = 1e-4; // level below which a stalled low-precision phase hands over
   Dav D;
   DBuf<double> V, S, X, R;
   DBuf<float> fin, fout;    // FP32 copies of the pending vectors and their sigma
@@ -503,7 +503,7 @@ struct DavState {
   bool done = false, converged = false;
   bool trace = std::getenv("PNOEOM_LOG_DAVIDSON") != nullptr;
   std::vector<double> w, rn, w_old;
-  std::vector<double> w_lowprec;   // Ritz values when the low-precision phase handed over (mixed solves)
+  std::vector<double> w_phase[2];  // Ritz values when the BF16 phase [0] and the FP32 phase [1] handed over
   std::vector<double> rhist;   // largest residual norm of every FP32 iteration (mixed solves)
 
   DavState(pnoeom_pno* P_, const pnoeom_opts* opts, cudaStream_t s_) : P(P_), s(s_), L(P_->L), D{P_, s_, P_->L} {
@@ -517,7 +517,8 @@ struct DavState {
     prec = (opts->precision == PNOEOM_FP32 || opts->precision == PNOEOM_BF16) ? PNOEOM_FP32 : PNOEOM_FP64;
     bf16 = opts->precision == PNOEOM_BF16;
     // the BF16 blocks carry about 3 significant digits, so that phase stalls far above the
-    // FP32 one's floor and hands over as soon as its residuals stop halving below 0.1
+    // FP32 one's floor: it hands over to an FP32 phase as soon as its residuals stop halving
+    // below 0.1, and the FP32 phase to FP64 as in a plain FP32 mixed solve
     switch_res = bf16 ? 1e-1 : 1e-4;
     refine = prec == PNOEOM_FP32 && opts->refine_fp64;
     // mixed precision: the FP32 phase aims at the final residual tolerance too and hands
@@ -632,10 +633,13 @@ struct DavState {
 
   void finish_or_refine() {
     if (prec == PNOEOM_FP32 && refine) {
-      // FP64 refinement, started from the current Ritz vectors: the subspace collapses onto
-      // them (orthonormalised) and only their sigma is evaluated again, in FP64
-      w_lowprec = w;
-      prec = PNOEOM_FP64;
+      // the next phase (BF16 -> FP32 -> FP64) starts from the current Ritz vectors: the
+      // subspace collapses onto them (orthonormalised) and only their sigma is evaluated
+      // again, in the next precision
+      w_phase[bf16 ? 0 : 1] = w;
+      rhist.clear();
+      if (bf16) { bf16 = false; switch_res = 1e-4; }
+      else prec = PNOEOM_FP64;
       w_old.clear();
       int mm = 0;
       for (int q = 0; q < nr; ++q) {
@@ -765,7 +769,8 @@ void run_davidson(pnoeom_ctx* ctx, pnoeom_pno* P, const pnoeom_opts* opts, cudaS
   d.results(energies, res_norms, iters);
   P->last_sigma_evals[0] = d.sigma_evals_prec[0];
   P->last_sigma_evals[1] = d.sigma_evals_prec[1];
-  P->last_lowprec_w = d.w_lowprec;
+  P->last_phase_w[0] = d.w_phase[0];
+  P->last_phase_w[1] = d.w_phase[1];
   *converged = d.converged ? 1 : 0;
 }
 

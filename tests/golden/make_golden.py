@@ -11,6 +11,9 @@ Calls only oracle/ and the seeded generator.  For a workload it stores:
 Usage: python tests/golden/make_golden.py medium   (about two hours on 8 cores)
        python tests/golden/make_golden.py large --pno-only
            (PNO/OSV counts and CIS energies of the large workload, ~10 minutes)
+       python tests/golden/make_golden.py large --sigma-samples
+           (per-pair oracle sigma of the blockwise trial vector for sampled pair blocks and
+            singles rows of the large workload, added to its fixture; ~30 minutes)
        python tests/golden/make_golden.py medium --sigma-only
            (recomputes only the sigma fields of an existing fixture, ~2 minutes)
 """
@@ -59,6 +62,72 @@ def trial_vector(o, v, seed=123):
     r1 = rng.standard_normal((o, v))
     r2 = rng.standard_normal((o, o, v, v))
     return r1, 0.5 * (r2 + r2.transpose(1, 0, 3, 2))
+
+
+def trial_r1(o, v, seed=321):
+    """Seeded canonical singles of the blockwise trial vector."""
+    return np.random.default_rng(seed).standard_normal((o, v))
+
+
+def trial_r2_block(v, i, j, seed=321):
+    """Canonical doubles block r2[i, j] (v x v) of the blockwise trial vector: pair i <= j
+    draws from its own seeded stream, r2[j, i] = r2[i, j]^T, r2[i, i] symmetric."""
+    a, b = min(i, j), max(i, j)
+    x = np.random.default_rng([seed, a, b]).standard_normal((v, v))
+    if a == b:
+        x = 0.5 * (x + x.T)
+    return x if i <= j else x.T
+
+
+def sigma_samples(name, npairs_sample=8):
+    """Sigma of the blockwise trial vector for a sample of pair blocks and singles, by the
+    per-pair oracle (oracle.pno_direct), in the canonical basis: SIGMA_SAMPLES seeded
+    entries of each sampled pair block and the whole sampled singles rows.  The sample
+    takes pairs of every size class (sorted by n_ij, evenly spaced) and three occupied
+    orbitals with OSVs."""
+    from oracle.pno_direct import PNOSigmaDirect
+    w = WORKLOADS[name]
+    o, v = w["o"], w["v"]
+    t0 = time.time()
+    s = make_system(o, v, w["naux"], w["seed"])
+    eps, B = s["eps"], s["B"]
+    sp = pno.PNOSpace(eps, B, o, w["nroots"], w["t_pno"])
+    sp.D = None                                               # densities not needed any more
+    print(f"PNO spaces {time.time() - t0:.0f} s", flush=True)
+    t2 = ccsd.mp1_t2(eps, B, o)
+    h = hm.hcore_from_fock(eps, B, o)
+    o2 = PNOSigmaDirect(None, t2, h, B, o, sp)
+    print(f"O2 setup {time.time() - t0:.0f} s", flush=True)
+    r1 = trial_r1(o, v)
+    vec = np.zeros(sp.length)
+    for i in range(o):
+        vec[sp.off_i[i]:sp.off_i[i + 1]] = sp.Ui[i].T @ r1[i]
+    for p, (i, j) in enumerate(sp.pairs):
+        if sp.n_ij[p]:
+            U = sp.U[i, j]
+            vec[sp.off_ij[p]:sp.off_ij[p + 1]] = (U.T @ trial_r2_block(v, i, j) @ U).ravel()
+    nz = [p for p in np.argsort(sp.n_ij, kind="stable") if sp.n_ij[p] > 0]
+    pick = sorted({int(nz[int(round(k * (len(nz) - 1) / (npairs_sample - 1)))]) for k in range(npairs_sample)})
+    occ = [i for i in range(o) if sp.n_i[i] > 0]
+    occ_pick = sorted({occ[0], occ[len(occ) // 2], occ[-1]})
+    sig = o2(vec, pairs=pick, singles=occ_pick)
+    print(f"sigma samples {time.time() - t0:.0f} s", flush=True)
+    rng = np.random.default_rng(7)
+    smp, s1 = {}, {}
+    for p in pick:
+        i, j = sp.pairs[p]
+        U = sp.U[i, j]
+        blk = U @ sig[sp.off_ij[p]:sp.off_ij[p + 1]].reshape(sp.n_ij[p], sp.n_ij[p]) @ U.T
+        pos = rng.integers(0, v, size=(SIGMA_SAMPLES, 2))
+        smp[f"{i},{j}"] = [[int(a), int(b), float(blk[a, b])] for a, b in pos]
+    for i in occ_pick:
+        s1[str(i)] = (sp.Ui[i] @ sig[sp.off_i[i]:sp.off_i[i + 1]]).tolist()
+    path = os.path.join(HERE, f"oracle_{name}.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    out.update({"sigma_trial": "blockwise (make_golden.trial_r1 / trial_r2_block, seed 321)",
+                "sigma_pair_samples": smp, "sigma_singles_rows": s1, "sigma_seconds": time.time() - t0})
+    json.dump(out, open(path, "w"))
+    print(f"wrote sigma samples to {path}: {time.time() - t0:.0f} s", flush=True)
 
 
 def pno_only(name):
@@ -123,5 +192,7 @@ if __name__ == "__main__":
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     if "--pno-only" in sys.argv:
         pno_only(args[0])
+    elif "--sigma-samples" in sys.argv:
+        sigma_samples(args[0])
     else:
         main(args[0] if args else "small", sigma_only="--sigma-only" in sys.argv)

@@ -81,8 +81,9 @@ def test_large_bf16_refined_energies_match_fp64(large):
                                                       refine_fp64=1, max_iter=300))
     assert conv and np.all(rn < 1e-7)
     assert np.abs(e - e64).max() <= 1e-5
-    low = gp.lowprec_energies()
-    assert len(low) == nr and np.all(np.isfinite(low))
+    for phase in (pkg.BF16, pkg.FP32):
+        low = gp.lowprec_energies(phase)
+        assert len(low) == nr and np.all(np.isfinite(low))
     # lowest excitation energies above zero and below the CIS ones plus a few eV
     assert np.all(e > 0) and np.all(np.diff(e) >= -1e-12)
     assert ctx.device_status() == 0
