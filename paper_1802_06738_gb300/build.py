@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libpnoeom.so")
-SOURCES = ["engine.cu", "sigma_kernels.cu", "build.cu", "build_program.cu", "solve.cu", "capi.cu", "noalloc.cu", "peaks.cu"]
+SOURCES = ["engine.cu", "sigma_kernels.cu", "build.cu", "build_program.cu", "solve.cu", "capi.cu", "noalloc.cu", "peaks.cu", "sandwich_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1189,6 +1189,13 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
     }
   };
   Program& PR = P->prog;
+  {
+    std::unordered_map<int64_t, std::pair<int64_t, int>> s_transpose;
+    for (int p = 0; p < npairs; ++p)
+      for (int q = 0; q < npairs; ++q)
+        if (nP(p) && nP(q)) s_transpose[Sblk(p, q)] = {Sblk(q, p), (int)nP(p)};
+    build_tcs(P, G.sp2, s_transpose, s, fp);
+  }
   make_sets(G.sp1, PR.small1, PR.h_gen1);
   make_sets(G.sp2, PR.small2, PR.h_gen2);
   PR.h_v1 = G.vp1;

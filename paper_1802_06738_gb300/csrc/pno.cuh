@@ -1,5 +1,6 @@
 // Handle state of one built system (pnoeom_pno) and internal entry points.
 #pragma once
+#include <unordered_map>
 #include "common.cuh"
 #include "engine.cuh"
 #include "sigma_prog.cuh"
@@ -47,6 +48,16 @@ struct Program {
   SmallSet small1[3], small2[3];   // small sandwich problems per size bucket
   int smem_elems = 1;
   int group_choice = 2, rpc_choice = NRPC_CAND - 1;   // fastest single candidate for every set (reported)
+  // tensor-core sandwich path of the BF16 sigma (single-system calls): jobs, rounds,
+  // sub-terms, copies, X blocks; gen2x: the phase-2 problems it does not cover (dims
+  // above TCS_MAXN), run by the generic kernel alongside it
+  DBuf<TcsJob> tcs_jobs; DBuf<TcsSlot> tcs_slots; DBuf<TcsRec> tcs_recs;
+  DBuf<int64_t> tcs_xblk;
+  int n_tcs_jobs = 0, n_tcs_xblk = 0;
+  int64_t tcs_xstride = 0;         // elements of one vector's X images
+  DBuf<SProb> gen2x;
+  int n_gen2x = 0;
+  std::vector<SProb> h_gen2x;
   std::vector<SProb> h_gen1, h_gen2;
   std::vector<VProb> h_v1, h_v2;
   std::vector<DProb> h_d1, h_d2, h_d3;
@@ -75,6 +86,8 @@ struct pnoeom_pno {
   pnoeom::DBuf<double> pool64;
   pnoeom::DBuf<float> pool32;
   pnoeom::DBuf<__nv_bfloat16> pool16;          // BF16 copy (dense GEMV blocks of the BF16 sigma)
+  pnoeom::DBuf<__nv_bfloat16> tcimg;           // BF16 operand images of the tensor-core sandwich path
+  pnoeom::DBuf<__nv_bfloat16> ximg;            // per-call X images (nvec x prog.tcs_xstride)
   pnoeom::Program prog;
   double tune_ms[pnoeom::NTUNE] = {0};
   static constexpr int NCLS = 6;             // kernel classes of the sigma program (timing)
@@ -156,6 +169,10 @@ void batch_solve(pnoeom_batch* B, const pnoeom_opts* opts, cudaStream_t s, doubl
                  int* iters, int* converged);
 // per-system launch entry of a sigma call
 SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* work, bool fp32, bool bf16);
+// Tensor-core sandwich lists of the BF16 sigma from the phase-2 sandwich problems;
+// s_transpose maps the pool offset of an overlap block S(a, b) to (offset of S(b, a), n_a).
+void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
+               const std::unordered_map<int64_t, std::pair<int64_t, int>>& s_transpose, cudaStream_t s, size_t* fp);
 // zero the outputs and work of every system in the table, then launch the program
 // (timing hook: if rec != nullptr, rec(cls, launch) wraps each kernel class)
 template <typename T>

@@ -1237,7 +1237,7 @@ int device_status(bool clear, cudaStream_t s) {
     PN_CUDA(cudaMemcpyToSymbolAsync(g_tc_status, &z, sizeof(int), 0, cudaMemcpyHostToDevice, s));
     PN_CUDA(cudaStreamSynchronize(s));
   }
-  return v;
+  return v | tcs_status(clear, s);
 }
 
 template void run_sandwich<double>(const SProb*, int, const SysTable&, int, cudaStream_t);

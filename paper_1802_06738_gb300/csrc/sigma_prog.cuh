@@ -8,6 +8,7 @@
 // SOUT (output vector of the root).
 #pragma once
 #include "common.cuh"
+#include <cuda_bf16.h>
 
 namespace pnoeom {
 
@@ -51,6 +52,63 @@ struct VProb {
   double alpha;
 };
 
+// Tensor-core sandwich path (BF16 operands, FP32 accumulation in TMEM).  Output pair
+// blocks are packed into "bins" of at most 128 rows (each block padded to 16 rows: its
+// slot); one CTA evaluates, for one vector, every sandwich term of every block of a bin:
+//   C_s += A_t (sN_t X + sT_t X^T) B_t          (slot s of term t, X = stored vector block q)
+// in rounds that each take one vector block q and at most one term per slot:
+//   GEMM1  D1 = [A_t stacked by slot] [X; X^T]^T     (M = 128, N = 2 nk, K = nk)
+//   T      = sN D1[:, :nk] + sT D1[:, nk:]           per row (slot), zero for slots without a term
+//   GEMM2  D2 += T [B_t^T stacked by slot]^T         (M = 128, N = bin rows, K = nk)
+// and adds the diagonal slot blocks of D2 to the output.  Operands are BF16 images in an
+// "M-outer" no-swizzle core-matrix layout, element (r, k) of an R x K image at byte
+//   (r / 8) * (K16 * 16) + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2     (K16 = K rounded up to 16)
+// so images stack along M by concatenation.
+constexpr int TCS_MAXN = 80;             // n_out and nk of terms on this path
+constexpr int TCS_ROWS = 128;            // rows of a bin
+constexpr int TCS_MAXSLOTS = 8;
+constexpr int TCS_NSLOT = 8;             // rounds in flight (stage barriers / headers)
+constexpr int TCS_HDR = 128;             // bytes of a round header
+constexpr int TCS_CONV_WARPS = 8;        // warps forming T: two per TMEM lane quarter, alternate 16-column chunks
+constexpr int TCS_THREADS = 32 * (TCS_CONV_WARPS + 2);   // + one bulk-copy warp and one MMA-issue warp
+
+struct TcsJob {                          // one bin (CTA x vector)
+  int r0, r1;                            // round records [r0, r1) (a bin's rounds may be split over jobs)
+  int s0, ns;                            // slots [s0, s0 + ns)
+  int rows16;                            // rows of the bin (sum of slot rows)
+  int sys;
+  int kmax16;                            // largest K of the job's rounds (sizes the TMEM buffers of GEMM1)
+  int pad;
+};
+struct TcsSlot {
+  int64_t c_off;                         // output block offset (n_out x n_out, row-major)
+  int n_out;
+  int row0;                              // first row of the slot in the bin
+};
+struct TcsTerm {
+  int slot;
+  float sN, sT;
+};
+struct TcsCopy {                         // bulk copy into the round's stage area
+  int64_t src;                           // element offset: image pool (kind 0) or the vector's X images (kind 1)
+  uint32_t dst;                          // byte offset from the round's start
+  uint32_t bytes;
+  int kind;
+  int pad;
+};
+constexpr int TCS_REC_COPIES = 16;
+// One round, fixed size (the copy warp prefetches records many rounds ahead with bulk copies).
+struct TcsRec {
+  uint32_t bytes;                        // area of the round: A tile + B tile + X tile
+  uint32_t tx;                           // bytes its copies deliver (slots without a term get none)
+  int nk16;                              // K of the round (vector block rows, rounded up to 16)
+  int nt, nc;                            // terms, copies
+  int pad[3];
+  TcsTerm terms[TCS_MAXSLOTS];
+  TcsCopy copies[TCS_REC_COPIES];
+};
+static_assert(sizeof(TcsRec) == 512, "round record");
+
 constexpr int GEMV_KC = 2048;         // K chunk staged in shared memory per GEMV tile
 constexpr int GEMV_ROWS = 32;         // rows of a GEMV tile
 constexpr int POOL_ALIGN = 8;         // GEMV blocks: offsets and leading dimensions are multiples of this
@@ -61,6 +119,8 @@ constexpr int SMALL_DIM = 64;         // sandwich problems with all dims <= this
 struct SysBuf {
   const void* pool;
   const void* pool16;                 // BF16 copy of the pool, or NULL: in FP32 a non-NULL copy is what the GEMV blocks read
+  const void* tcimg;                  // BF16 operand images of the tensor-core sandwich path, or NULL
+  void* ximg; int64_t ximg_stride;    // per-vector BF16 images of the vector blocks (X and X^T), or NULL
   const void* rin; int64_t rin_stride;
   void* work; int64_t work_stride;
   void* sout; int64_t sout_stride;
@@ -93,6 +153,15 @@ void run_sandwich(const SProb* d_probs, int nprob, const SysTable& t, int smem_e
 template <typename T>
 void run_sandwich_small(const SProb* d_probs, const int* d_group_start, int ngroups, const SysTable& t, int dm, int dk1,
                         int dk2, int dn, int roots_per_cta, int pb, int nbsel, int shape, cudaStream_t s);
+// Tensor-core sandwich path: X images of every vector (one launch), then the bins (one
+// launch, grid bins x vectors).  xblk: per stored block (vector offset, n, image offset).
+void run_sandwich_tc(const TcsJob* d_jobs, int njobs, const TcsSlot* d_slots, const TcsRec* d_recs,
+                     const int64_t* d_xblk, int nxblk, const SysTable& t, cudaStream_t s);
+// Builds BF16 images from an FP64 pool: desc = nimg x {src, ld, trans, rows, K, dst}.
+// Status word of the tensor-core sandwich kernel (same bits as device_status); clear resets it.
+int tcs_status(bool clear, cudaStream_t s);
+void make_tc_images(const double* pool, __nv_bfloat16* img, const int64_t* d_desc, int nimg, cudaStream_t s);
+
 template <typename T>
 void run_gemv(const VProb* d_probs, int nprob, const SysTable& t, cudaStream_t s);
 // Output tiles of a dense list: DENSE_TILE_TC = 128 rows x 64 columns (tensor cores in

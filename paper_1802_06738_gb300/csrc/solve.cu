@@ -25,6 +25,7 @@ SysBuf sysbuf(const pnoeom_pno* P, int nvec, const void* r, void* out, void* wor
   SysBuf b{};
   b.pool = fp32 ? (const void*)P->pool32.get() : (const void*)P->pool64.get();
   b.pool16 = fp32 && bf16 ? (const void*)P->pool16.get() : nullptr;
+  b.tcimg = fp32 && bf16 && P->prog.n_tcs_jobs > 0 ? (const void*)P->tcimg.get() : nullptr;
   b.rin = r; b.rin_stride = P->L;
   b.work = work; b.work_stride = P->work_len;
   b.sout = out; b.sout_stride = P->L;
@@ -157,15 +158,25 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     run_dense<T>(prog.d2.get(), prog.n_d2, t, DENSE_TILE_TC, s);
     run_dense<T>(prog.d3.get(), prog.n_d3, t, 32, s);
   });
+  // BF16 single-system calls: the phase-2 sandwiches on the tensor cores (blocks above
+  // TCS_MAXN on the generic kernel)
+  const bool tcs = sizeof(T) == 4 && t.nsys == 1 && t.s[0].pool16 && t.s[0].tcimg && t.s[0].ximg &&
+                   prog.n_tcs_jobs > 0;
   timed(2, [&] {
-    n2 = small(prog.small2);
-    run_sandwich<T>(prog.gen2.get(), prog.n_gen2, t, prog.smem_elems, s);
+    if (tcs) {
+      run_sandwich_tc(prog.tcs_jobs.get(), prog.n_tcs_jobs, prog.tcs_slots.get(), prog.tcs_recs.get(),
+                      prog.tcs_xblk.get(), prog.n_tcs_xblk, t, s);
+      run_sandwich<T>(prog.gen2x.get(), prog.n_gen2x, t, prog.smem_elems, s);
+    } else {
+      n2 = small(prog.small2);
+      run_sandwich<T>(prog.gen2.get(), prog.n_gen2, t, prog.smem_elems, s);
+    }
   });
   timed(3, [&] { run_gemv<T>(prog.v2.get(), prog.n_v2, t, s); });
   if (P) {   // kernel launches per class in this call
     P->prof_launches[0] += n0 + (prog.n_gen1 > 0);
     P->prof_launches[1] += prog.n_v1 > 0;
-    P->prof_launches[2] += n2 + (prog.n_gen2 > 0);
+    P->prof_launches[2] += tcs ? 2 + (prog.n_gen2x > 0) : n2 + (prog.n_gen2 > 0);
     P->prof_launches[3] += prog.n_v2 > 0;
     P->prof_launches[4] += prog.n_d1 > 0;
     P->prof_launches[5] += (prog.n_d2 > 0) + (prog.n_d3 > 0);
@@ -184,6 +195,12 @@ void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s, bo
   t.nsys = 1;
   t.max_nvec = nvec;
   t.s[0] = sysbuf(P, nvec, r, out, work.get(), sizeof(T) == 4, bf16);
+  if (t.s[0].tcimg) {   // X images of the tensor-core sandwich path
+    const size_t needx = (size_t)nvec * P->prog.tcs_xstride;
+    if (P->ximg.n < needx) P->ximg.alloc(needx, &P->footprint);
+    t.s[0].ximg = P->ximg.get();
+    t.s[0].ximg_stride = P->prog.tcs_xstride;
+  }
   const int64_t ol = P->L, wl = P->work_len;
   run_program<T>(P->prog, t, &ol, &wl, s, P);
 }
