@@ -50,9 +50,10 @@ constexpr int TCS_RING = (TCS_SMEM - 2 * TCS_TBUF - TCS_NSLOT * TCS_HDR - TCS_DQ
 constexpr uint32_t TCS_D2_COL = 512 - TCS_ROWS;     // TMEM column of D2 (bin rows <= 128 columns)
 constexpr int TCS_MAXD1 = 4;                         // GEMM1 buffers: as many as fit below D2, at most 4
 static_assert(TCS_D2_COL >= 2 * 2 * TCS_KMAX, "TMEM budget: two GEMM1 buffers of the largest K");
-// largest round: A and B tiles of 128 rows and the two-variant X tile, all with K = TCS_KMAX
-constexpr uint32_t TCS_MAX_ROUND = (2 * TCS_ROWS + 2 * TCS_KMAX) * TCS_KMAX * 2;
-static_assert(2 * TCS_MAX_ROUND <= (uint32_t)TCS_RING, "ring must hold two rounds");
+// largest round area (a single vector block of K = TCS_KMAX with 128-row tiles must fit), and
+// the ring holds at least two of them
+static_assert((2 * TCS_ROWS + 2 * TCS_KMAX) * TCS_KMAX * 2 <= TCS_MAX_AREA, "round area");
+static_assert(2 * TCS_MAX_AREA <= TCS_RING, "ring must hold two rounds");
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(tc::smem_u32(bar)), "r"(bytes)
@@ -157,14 +158,18 @@ __global__ void __launch_bounds__(128) k_tcs_make_img(const double* __restrict__
 }
 
 // Round header in shared memory (written by the copy warp): start of the round's area in
-// the ring, K, the mask of slots with a term, and the per-slot coefficients.
-struct RoundHdr {
-  uint32_t start;
-  int nk16;
-  uint32_t mask;
-  int pad;
+// the ring, its sub-blocks (K, GEMM1 columns, T columns, tile offset, mask of slots with a
+// term, per-slot coefficients) and the columns of T.
+struct SubHdr {
+  int nk16, dc, tk;
+  uint32_t a_off, mask;
   float sN[TCS_MAXSLOTS];
   float sT[TCS_MAXSLOTS];
+};
+struct RoundHdr {
+  uint32_t start;
+  int nsub, ktot, pad;
+  SubHdr sub[TCS_MAXSUB];
 };
 static_assert(sizeof(RoundHdr) <= TCS_HDR, "round header");
 
@@ -180,8 +185,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
   uint64_t* full = bars;                     // [NSLOT] a round's images landed
   uint64_t* empty = bars + TCS_NSLOT;        // [NSLOT] the round's GEMM2 completed (its ring area is free)
   uint64_t* g1 = bars + 2 * TCS_NSLOT;       // [TCS_MAXD1] GEMM1 into D1 buffer b completed
-  uint64_t* g2 = g1 + TCS_MAXD1;             // [2] GEMM2 that read T tile b completed
-  uint64_t* tready = g2 + 2;                 // [2] T tile b formed (one arrival per T-forming thread)
+  uint64_t* tready = g1 + TCS_MAXD1;         // [2] T tile b formed (one arrival per T-forming thread)
   uint64_t* dqb = tready + 2;                // [2] half h of the record queue (TCS_DQ / 2 records) landed
   uint32_t* misc = reinterpret_cast<uint32_t*>(dqb + 2);
   // misc: [0] TMEM base, [1] abort flag, [2] keep-TMEM flag
@@ -197,7 +201,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
   for (int e = tid; e < TCS_RING / 16; e += TCS_THREADS) reinterpret_cast<uint4*>(ring)[e] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) tc::tmem_alloc(misc, 512);
   if (tid == 0) {
-    for (int b = 0; b < 2 * TCS_NSLOT + TCS_MAXD1 + 2; ++b) tc::mbar_init(bars + b, 1);
+    for (int b = 0; b < 2 * TCS_NSLOT + TCS_MAXD1; ++b) tc::mbar_init(bars + b, 1);
     tc::mbar_init(tready, 32 * TCS_CONV_WARPS);
     tc::mbar_init(tready + 1, 32 * TCS_CONV_WARPS);
     tc::mbar_init(dqb, 1);
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
   const uint32_t tmem = misc[0];
   const int R = J.r1 - J.r0;
   const int rows16 = J.rows16;
-  // GEMM1 buffers of 2 kmax16 columns each below D2: round r uses buffer r % nd1
-  const uint32_t d1w = 2u * (uint32_t)J.kmax16;
+  // GEMM1 buffers of d1w columns each below D2: round r uses buffer r % nd1
+  const uint32_t d1w = (uint32_t)J.d1w;
   const int nd1 = min(TCS_MAXD1, (int)(TCS_D2_COL / d1w));
   long long* trace = (blockIdx.x == 0 && blockIdx.y == 0) ? g_tcs_trace : nullptr;
 
@@ -260,9 +264,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
           0xffffffffu, (lane < TCS_NSLOT && my_rk >= tail && start < my_re && my_rs < start + bytes) ? my_rk : r - TCS_NSLOT);
       if (need >= tail) {
         if (lane == 0) {
-          if (trace && r < TCS_TRACE_ROUNDS) trace[12 * r + 10] = clock64();
           ok = tcs_wait(empty + need % TCS_NSLOT, (uint32_t)(need / TCS_NSLOT) & 1u, abort_flag);
-          if (trace && r < TCS_TRACE_ROUNDS) trace[12 * r + 11] = clock64();
         }
         tail = need + 1;
       }
@@ -273,20 +275,29 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
       head = start + bytes;
       const int sl = r % TCS_NSLOT;
       RoundHdr* H = hdr + sl;
-      const int nt = RD.nt;
-      if (lane < TCS_MAXSLOTS) { H->sN[lane] = 0.f; H->sT[lane] = 0.f; }
-      __syncwarp();
-      TcsTerm tm{};
-      if (lane < nt) {
-        tm = RD.terms[lane];
-        H->sN[tm.slot] = tm.sN;
-        H->sT[tm.slot] = tm.sT;
+      static_assert(TCS_MAXSUB * TCS_MAXSLOTS == 32, "one coefficient pair per lane");
+      H->sub[lane / TCS_MAXSLOTS].sN[lane % TCS_MAXSLOTS] = 0.f;
+      H->sub[lane / TCS_MAXSLOTS].sT[lane % TCS_MAXSLOTS] = 0.f;
+      if (lane < RD.nsub) {
+        const TcsSub U = RD.subs[lane];
+        SubHdr& D = H->sub[lane];
+        D.nk16 = U.nk16;
+        D.dc = U.dc;
+        D.tk = U.tk;
+        D.a_off = U.a_off;
+        D.mask = U.mask;
       }
-      const uint32_t mask = __reduce_or_sync(0xffffffffu, lane < nt ? (1u << tm.slot) : 0u);
+      __syncwarp();
+      if (lane < RD.nt) {
+        const TcsTerm tm = RD.terms[lane];
+        SubHdr& D = H->sub[tm.slot >> 8];
+        D.sN[tm.slot & 255] = tm.sN;
+        D.sT[tm.slot & 255] = tm.sT;
+      }
       if (lane == 0) {
         H->start = start;
-        H->nk16 = RD.nk16;
-        H->mask = mask;
+        H->nsub = RD.nsub;
+        H->ktot = RD.ktot;
       }
       __syncwarp();
       if (lane == 0) {
@@ -333,14 +344,17 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
           tc::fence_after_sync();
           if (trace && r < TCS_TRACE_ROUNDS) trace[12 * r + 1] = clock64();
           const RoundHdr& H = hdr[sl];
-          const int nk16 = H.nk16;
-          const uint32_t base = tc::smem_u32(ring + H.start), SBO = (uint32_t)nk16 * 16;
-          const uint32_t aS = base, xS = base + 2u * rows16 * nk16 * 2u;
-          const uint32_t idesc1 = tc::idesc_bf16(128, 2 * nk16);
+          const uint32_t base = tc::smem_u32(ring + H.start);
           const uint32_t d = tmem + (uint32_t)(r % nd1) * d1w;
-          for (int ks = 0; ks < nk16 / 16; ++ks)
-            tc::mma_bf16(d, tc::sdesc(aS + ks * 256, 128, SBO), tc::sdesc(xS + ks * 256, 128, SBO), idesc1,
-                         ks > 0 ? 1u : 0u);
+          for (int i = 0; i < H.nsub; ++i) {
+            const int nk16 = H.sub[i].nk16;
+            const uint32_t SBO = (uint32_t)nk16 * 16;
+            const uint32_t aS = base + H.sub[i].a_off, xS = aS + 2u * rows16 * nk16 * 2u;
+            const uint32_t idesc1 = tc::idesc_bf16(128, 2 * nk16);
+            for (int ks = 0; ks < nk16 / 16; ++ks)
+              tc::mma_bf16(d + (uint32_t)H.sub[i].dc, tc::sdesc(aS + ks * 256, 128, SBO), tc::sdesc(xS + ks * 256, 128, SBO),
+                           idesc1, ks > 0 ? 1u : 0u);
+          }
           tc::mma_commit(g1 + r % nd1);
           last_bar = (int)(g1 + r % nd1 - bars);
           last_par = (uint32_t)(r / nd1) & 1u;
@@ -354,18 +368,22 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
           tc::fence_after_sync();
           if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 9] = clock64();
           const RoundHdr& H = hdr[sl];
-          const int nk16 = H.nk16;
-          const uint32_t SBO = (uint32_t)nk16 * 16;
-          const uint32_t bS = tc::smem_u32(ring + H.start) + (uint32_t)rows16 * nk16 * 2u;
-          const uint32_t tS = tc::smem_u32(tbuf + b * TCS_TBUF);
+          const uint32_t base = tc::smem_u32(ring + H.start);
+          const uint32_t tS = tc::smem_u32(tbuf + b * TCS_TBUF), SBO_T = (uint32_t)H.ktot * 16;
           const uint32_t idesc2 = tc::idesc_bf16(128, rows16);
-          for (int ks = 0; ks < nk16 / 16; ++ks)
-            tc::mma_bf16(tmem + TCS_D2_COL, tc::sdesc(tS + ks * 256, 128, SBO), tc::sdesc(bS + ks * 256, 128, SBO), idesc2,
-                         (rr > 0 || ks > 0) ? 1u : 0u);
-          tc::mma_commit(empty + sl);
-          tc::mma_commit(g2 + b);
-          last_bar = (int)(g2 + b - bars);
-          last_par = (uint32_t)(rr / 2) & 1u;
+          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 10] = clock64();
+          for (int i = 0; i < H.nsub; ++i) {
+            const int nk16 = H.sub[i].nk16;
+            const uint32_t bS = base + H.sub[i].a_off + (uint32_t)rows16 * nk16 * 2u;
+            const uint32_t t0s = tS + (uint32_t)(H.sub[i].tk >> 3) * 128u;
+            for (int ks = 0; ks < nk16 / 16; ++ks)
+              tc::mma_bf16(tmem + TCS_D2_COL, tc::sdesc(t0s + ks * 256, 128, SBO_T),
+                           tc::sdesc(bS + ks * 256, 128, (uint32_t)nk16 * 16), idesc2, (rr > 0 || i > 0 || ks > 0) ? 1u : 0u);
+          }
+          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 11] = clock64();
+          tc::mma_commit(empty + sl);   // the round's area and its T tile are free again
+          last_bar = (int)(empty + sl - bars);
+          last_par = (uint32_t)(rr / TCS_NSLOT) & 1u;
           if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 5] = clock64();
           ++n2;
           progressed = true;
@@ -399,51 +417,57 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
       const int b = r & 1, sl = r % TCS_NSLOT;
       bool w = tcs_wait(g1 + r % nd1, (uint32_t)(r / nd1) & 1u, abort_flag);
       if (w) w = tcs_wait(full + sl, (uint32_t)(r / TCS_NSLOT) & 1u, abort_flag);   // the header
-      if (w && r >= 2) w = tcs_wait(g2 + b, (uint32_t)((r - 2) / 2) & 1u, abort_flag);
+      if (w && r >= 2)   // T tile b: the GEMM2 of round r - 2 completed
+        w = tcs_wait(empty + (r - 2) % TCS_NSLOT, (uint32_t)((r - 2) / TCS_NSLOT) & 1u, abort_flag);
       ok = __all_sync(0xffffffffu, w);
       if (!ok) break;
       tc::fence_after_sync();
       if (trace && tid == 0 && r < TCS_TRACE_ROUNDS) trace[12 * r + 3] = clock64();
       const RoundHdr& H = hdr[sl];
-      const int nk16 = H.nk16, nc = nk16 / 16;
       unsigned char* T = tbuf + b * TCS_TBUF;
       if (active) {
-        const bool present = myslot >= 0 && ((H.mask >> myslot) & 1u);
-        const float sN = present ? H.sN[myslot] : 0.f, sT = present ? H.sT[myslot] : 0.f;
-        const uint32_t rowoff = (uint32_t)(row >> 3) * (uint32_t)(nk16 * 16) + (uint32_t)(row & 7) * 16u;
+        const uint32_t rowoff = (uint32_t)(row >> 3) * (uint32_t)(H.ktot * 16) + (uint32_t)(row & 7) * 16u;
         const uint32_t dbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(r % nd1) * d1w;
-        constexpr int NH = (TCS_KMAX / 16 + 1) / 2;   // chunks per warp
-        uint32_t xn[NH][16], xt[NH][16];
+        for (int i = 0; i < H.nsub; ++i) {
+          const SubHdr& U = H.sub[i];
+          const int nk16 = U.nk16, nc = nk16 / 16;
+          const bool present = myslot >= 0 && ((U.mask >> myslot) & 1u);
+          const float sN = present ? U.sN[myslot] : 0.f, sT = present ? U.sT[myslot] : 0.f;
+          const uint32_t db = dbase + (uint32_t)U.dc;
+          constexpr int NH = (TCS_KMAX / 16 + 1) / 2;   // chunks per warp and sub-block
+          uint32_t xn[NH][16], xt[NH][16];
 #pragma unroll
-        for (int i = 0; i < NH; ++i) {
-          const int c = 2 * i + half;
-          if (c < nc) {
-            tc::tmem_ld16_nowait(dbase + (uint32_t)(c * 16), xn[i]);
-            tc::tmem_ld16_nowait(dbase + (uint32_t)(nk16 + c * 16), xt[i]);
+          for (int j = 0; j < NH; ++j) {
+            const int c = 2 * j + half;
+            if (c < nc) {
+              tc::tmem_ld16_nowait(db + (uint32_t)(c * 16), xn[j]);
+              tc::tmem_ld16_nowait(db + (uint32_t)(nk16 + c * 16), xt[j]);
+            }
           }
-        }
-        tc::tmem_wait_ld();
+          tc::tmem_wait_ld();
 #pragma unroll
-        for (int i = 0; i < NH; ++i) {
-          const int c = 2 * i + half;
-          if (c >= nc) break;
-          float x[16];
+          for (int j = 0; j < NH; ++j) {
+            const int c = 2 * j + half;
+            if (c >= nc) break;
+            float x[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            asm volatile("" : "+r"(xn[i][j]), "+r"(xt[i][j]));   // keeps every use after the wait
-            x[j] = present ? fmaf(sN, __uint_as_float(xn[i][j]), sT * __uint_as_float(xt[i][j])) : 0.f;
+            for (int e = 0; e < 16; ++e) {
+              asm volatile("" : "+r"(xn[j][e]), "+r"(xt[j][e]));   // keeps every use after the wait
+              x[e] = present ? fmaf(sN, __uint_as_float(xn[j][e]), sT * __uint_as_float(xt[j][e])) : 0.f;
+            }
+            uint4 w0, w1;
+            w0.x = pack_bf16x2(x[0], x[1]);
+            w0.y = pack_bf16x2(x[2], x[3]);
+            w0.z = pack_bf16x2(x[4], x[5]);
+            w0.w = pack_bf16x2(x[6], x[7]);
+            w1.x = pack_bf16x2(x[8], x[9]);
+            w1.y = pack_bf16x2(x[10], x[11]);
+            w1.z = pack_bf16x2(x[12], x[13]);
+            w1.w = pack_bf16x2(x[14], x[15]);
+            const uint32_t k8 = (uint32_t)(U.tk >> 3) + 2u * c;
+            *reinterpret_cast<uint4*>(T + rowoff + k8 * 128u) = w0;
+            *reinterpret_cast<uint4*>(T + rowoff + (k8 + 1) * 128u) = w1;
           }
-          uint4 w0, w1;
-          w0.x = pack_bf16x2(x[0], x[1]);
-          w0.y = pack_bf16x2(x[2], x[3]);
-          w0.z = pack_bf16x2(x[4], x[5]);
-          w0.w = pack_bf16x2(x[6], x[7]);
-          w1.x = pack_bf16x2(x[8], x[9]);
-          w1.y = pack_bf16x2(x[10], x[11]);
-          w1.z = pack_bf16x2(x[12], x[13]);
-          w1.w = pack_bf16x2(x[14], x[15]);
-          *reinterpret_cast<uint4*>(T + rowoff + (uint32_t)(2 * c) * 128u) = w0;
-          *reinterpret_cast<uint4*>(T + rowoff + (uint32_t)(2 * c + 1) * 128u) = w1;
         }
       }
       tc::fence_async_smem();
@@ -454,7 +478,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
     // the last GEMM2, then the diagonal slot blocks of D2 into the output
     if (ok && R > 0) {
       const int rl = R - 1;
-      ok = __all_sync(0xffffffffu, tcs_wait(g2 + (rl & 1), (uint32_t)(rl / 2) & 1u, abort_flag));
+      ok = __all_sync(0xffffffffu, tcs_wait(empty + rl % TCS_NSLOT, (uint32_t)(rl / TCS_NSLOT) & 1u, abort_flag));
     }
     if (ok && R > 0 && active && half == 0) {
       tc::fence_after_sync();
@@ -659,61 +683,96 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
         v[k].push_back(&t);
       }
     }
-    // one round record from (slot, term) pairs of one vector block; split while its merged
-    // copies exceed a record
-    std::function<void(int, const std::vector<std::pair<int, const Term*>>&)> emit =
-        [&](int q, const std::vector<std::pair<int, const Term*>>& st) {
-          const int nk16 = up16((int)xblk[3 * q + 1]);
-          const uint32_t tile = (uint32_t)J.rows16 * nk16 * 2;
-          std::vector<TcsCopy> cp;
-          for (auto& e : st) {
-            const TcsSlot& S = hsl[J.s0 + e.first];
-            const uint32_t rb = (uint32_t)S.row0 * nk16 * 2, sz = (uint32_t)up16(S.n_out) * nk16 * 2;
-            cp.push_back({image(e.second->a), rb, sz, 0, 0});
-            cp.push_back({image(e.second->b), tile + rb, sz, 0, 0});
-          }
-          cp.push_back({xblk[3 * q + 2], 2 * tile, 2u * nk16 * nk16 * 2, 1, 0});
-          std::sort(cp.begin(), cp.end(), [](const TcsCopy& a, const TcsCopy& b) { return a.dst < b.dst; });
-          std::vector<TcsCopy> merged;
-          for (const TcsCopy& c : cp) {   // one copy for images adjacent in the source and the area
-            if (!merged.empty()) {
-              TcsCopy& l = merged.back();
-              if (l.kind == c.kind && l.src + l.bytes / 2 == c.src && l.dst + l.bytes == c.dst) { l.bytes += c.bytes; continue; }
-            }
-            merged.push_back(c);
-          }
-          if ((int)merged.size() > TCS_REC_COPIES) {
-            const size_t h = st.size() / 2;
-            emit(q, std::vector<std::pair<int, const Term*>>(st.begin(), st.begin() + h));
-            emit(q, std::vector<std::pair<int, const Term*>>(st.begin() + h, st.end()));
-            return;
-          }
-          TcsRec R{};
-          R.nk16 = nk16;
-          R.bytes = 2 * tile + 2u * nk16 * nk16 * 2;
-          R.nt = (int)st.size();
-          for (size_t i = 0; i < st.size(); ++i) R.terms[i] = {st[i].first, st[i].second->sN, st[i].second->sT};
-          R.nc = (int)merged.size();
-          R.tx = 0;
-          for (size_t i = 0; i < merged.size(); ++i) { R.copies[i] = merged[i]; R.tx += merged[i].bytes; }
-          hrec.push_back(R);
-          rcost.push_back((double)nk16 / 16 * (std::max(72.0, (double)nk16) + std::max(72.0, J.rows16 / 2.0)) + 300.0);
-          nterms += st.size();
-          ncopies += merged.size();
-        };
+    // units: one vector block and at most one term per slot (the d-th term of every slot);
+    // consecutive units share a round while the round's GEMM1 columns, sub-blocks, terms,
+    // area and copies fit
+    struct Unit { int q, nk16; std::vector<std::pair<int, const Term*>> st; };
+    std::vector<Unit> units;
+    int kmax16 = 16;
     for (auto& kv : byq) {
       size_t depth = 0;
       for (auto& v : kv.second) depth = std::max(depth, v.size());
-      for (size_t d = 0; d < depth; ++d) {   // round d takes the d-th term of every slot
-        std::vector<std::pair<int, const Term*>> st;
+      const int nk16 = up16((int)xblk[3 * kv.first + 1]);
+      kmax16 = std::max(kmax16, nk16);
+      for (size_t d = 0; d < depth; ++d) {
+        Unit u{kv.first, nk16, {}};
         for (int k = 0; k < J.ns; ++k)
-          if (d < kv.second[k].size()) st.push_back({k, kv.second[k][d]});
-        emit(kv.first, st);
+          if (d < kv.second[k].size()) u.st.push_back({k, kv.second[k][d]});
+        units.push_back(u);
       }
     }
+    J.d1w = kmax16 <= 64 ? 128 : 2 * kmax16;
+    const uint32_t max_area = (uint32_t)TCS_MAX_AREA;
+    auto unit_area = [&](const Unit& u) { return (uint32_t)(2 * J.rows16 + 2 * u.nk16) * u.nk16 * 2; };
+    auto unit_copies = [&](const Unit& u, uint32_t a_off, std::vector<TcsCopy>& cp) {
+      const uint32_t tile = (uint32_t)J.rows16 * u.nk16 * 2;
+      for (auto& e : u.st) {
+        const TcsSlot& S = hsl[J.s0 + e.first];
+        const uint32_t rb = (uint32_t)S.row0 * u.nk16 * 2, sz = (uint32_t)up16(S.n_out) * u.nk16 * 2;
+        cp.push_back({image(e.second->a), a_off + rb, sz, 0, 0});
+        cp.push_back({image(e.second->b), a_off + tile + rb, sz, 0, 0});
+      }
+      cp.push_back({xblk[3 * u.q + 2], a_off + 2 * tile, 2u * u.nk16 * u.nk16 * 2, 1, 0});
+    };
+    auto merge = [](std::vector<TcsCopy> cp) {   // one copy for images adjacent in the source and the area
+      std::sort(cp.begin(), cp.end(), [](const TcsCopy& a, const TcsCopy& b) { return a.dst < b.dst; });
+      std::vector<TcsCopy> m;
+      for (const TcsCopy& c : cp) {
+        if (!m.empty()) {
+          TcsCopy& l = m.back();
+          if (l.kind == c.kind && l.src + l.bytes / 2 == c.src && l.dst + l.bytes == c.dst) { l.bytes += c.bytes; continue; }
+        }
+        m.push_back(c);
+      }
+      return m;
+    };
+    size_t ui = 0;
+    while (ui < units.size()) {
+      TcsRec R{};
+      std::vector<TcsCopy> cp;
+      int cols = 0, ktot = 0;
+      uint32_t area = 0;
+      while (ui < units.size() && R.nsub < TCS_MAXSUB) {
+        const Unit& u = units[ui];
+        if (R.nsub > 0 && (cols + 2 * u.nk16 > J.d1w || R.nt + (int)u.st.size() > TCS_REC_TERMS ||
+                           area + unit_area(u) > max_area))
+          break;
+        std::vector<TcsCopy> cp2 = cp;
+        unit_copies(u, area, cp2);
+        std::vector<TcsCopy> m = merge(cp2);
+        if (R.nsub > 0 && (int)m.size() > TCS_REC_COPIES) break;
+        PN_CHECK((int)m.size() <= TCS_REC_COPIES, PNOEOM_ERR_CUDA, "tensor-core sandwich: copies of one vector block");
+        TcsSub& U = R.subs[R.nsub];
+        U.nk16 = (uint16_t)u.nk16;
+        U.dc = (uint16_t)cols;
+        U.tk = (uint16_t)ktot;
+        U.a_off = area;
+        U.mask = 0;
+        for (auto& e : u.st) {
+          R.terms[R.nt++] = {e.first | (R.nsub << 8), e.second->sN, e.second->sT};
+          U.mask |= 1u << e.first;
+        }
+        cp.swap(cp2);
+        cols += 2 * u.nk16;
+        ktot += u.nk16;
+        area += unit_area(u);
+        ++R.nsub;
+        ++ui;
+      }
+      std::vector<TcsCopy> m = merge(cp);
+      R.nc = (int)m.size();
+      R.tx = 0;
+      for (int c = 0; c < R.nc; ++c) { R.copies[c] = m[c]; R.tx += m[c].bytes; }
+      R.bytes = area;
+      R.ktot = ktot;
+      hrec.push_back(R);
+      double cst = 700.0;
+      for (int i = 0; i < R.nsub; ++i) cst += 2.0 * 72.0 * (R.subs[i].nk16 / 16);
+      rcost.push_back(cst);
+      nterms += R.nt;
+      ncopies += R.nc;
+    }
     J.r1 = (int)hrec.size();
-    J.kmax16 = 16;
-    for (int r = J.r0; r < J.r1; ++r) J.kmax16 = std::max(J.kmax16, hrec[r].nk16);
     if (J.r1 > J.r0) hj.push_back(J);
   }
   // enough CTAs for the device (about four per SM with six vectors): a bin's rounds are split
@@ -744,12 +803,11 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
   }
   // every copy and operand lies inside its source and the round's area, every slot and
   // term inside its bin (the kernels index with these values unchecked)
-  const int TCS_RING_HOST = (227 * 1024 - 2 * TCS_ROWS * ((TCS_MAXN + 15) / 16 * 16) * 2 - TCS_NSLOT * TCS_HDR -
-                             16 * (int)sizeof(TcsRec) - 1024) / 1024 * 1024;
   for (auto& jc : jobs_c) {
     const TcsJob& J = jc.second;
     PN_CHECK(J.ns >= 1 && J.ns <= TCS_MAXSLOTS && J.rows16 >= 16 && J.rows16 <= TCS_ROWS && J.rows16 % 16 == 0 &&
-                 J.r1 > J.r0 && J.kmax16 >= 16 && J.kmax16 <= up16(TCS_MAXN) && J.kmax16 % 16 == 0,
+                 J.r1 > J.r0 && J.d1w >= 32 && J.d1w <= 2 * up16(TCS_MAXN) && J.d1w % 16 == 0 &&
+                 2 * J.d1w <= 512 - TCS_ROWS,
              PNOEOM_ERR_CUDA, "tensor-core sandwich: bin shape");
     int rows = 0;
     for (int k = 0; k < J.ns; ++k) {
@@ -760,15 +818,28 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
     PN_CHECK(rows == J.rows16, PNOEOM_ERR_CUDA, "tensor-core sandwich: bin rows");
     for (int r = J.r0; r < J.r1; ++r) {
       const TcsRec& R = hrec[r];
-      PN_CHECK(R.nk16 >= 16 && R.nk16 <= J.kmax16 && R.nk16 % 16 == 0 &&
-                   R.bytes == (uint32_t)(2 * J.rows16 + 2 * R.nk16) * R.nk16 * 2 && 2 * R.bytes <= (uint32_t)TCS_RING_HOST &&
-                   R.nt >= 1 && R.nt <= J.ns && R.nc >= 1 && R.nc <= TCS_REC_COPIES,
+      PN_CHECK(R.nsub >= 1 && R.nsub <= TCS_MAXSUB && R.nt >= 1 && R.nt <= TCS_REC_TERMS && R.nc >= 1 &&
+                   R.nc <= TCS_REC_COPIES && R.bytes <= (uint32_t)TCS_MAX_AREA && R.ktot <= up16(TCS_MAXN),
                PNOEOM_ERR_CUDA, "tensor-core sandwich: round");
-      uint32_t seen = 0, tx = 0;
+      uint32_t area = 0;
+      int cols = 0, ktot = 0;
+      for (int i = 0; i < R.nsub; ++i) {
+        const TcsSub& U = R.subs[i];
+        PN_CHECK(U.nk16 >= 16 && U.nk16 <= up16(TCS_MAXN) && U.nk16 % 16 == 0 && U.a_off == area && U.dc == cols &&
+                     U.tk == ktot,
+                 PNOEOM_ERR_CUDA, "tensor-core sandwich: sub-block");
+        area += (uint32_t)(2 * J.rows16 + 2 * U.nk16) * U.nk16 * 2;
+        cols += 2 * U.nk16;
+        ktot += U.nk16;
+      }
+      PN_CHECK(area == R.bytes && cols <= J.d1w && ktot == R.ktot, PNOEOM_ERR_CUDA, "tensor-core sandwich: round area");
+      uint32_t seen[TCS_MAXSUB] = {0, 0, 0, 0}, tx = 0;
       for (int t = 0; t < R.nt; ++t) {
-        PN_CHECK(R.terms[t].slot >= 0 && R.terms[t].slot < J.ns && !(seen >> R.terms[t].slot & 1u), PNOEOM_ERR_CUDA,
-                 "tensor-core sandwich: term slot");
-        seen |= 1u << R.terms[t].slot;
+        const int sub = R.terms[t].slot >> 8, slot = R.terms[t].slot & 255;
+        PN_CHECK(sub >= 0 && sub < R.nsub && slot >= 0 && slot < J.ns && !(seen[sub] >> slot & 1u) &&
+                     (R.subs[sub].mask >> slot & 1u),
+                 PNOEOM_ERR_CUDA, "tensor-core sandwich: term slot");
+        seen[sub] |= 1u << slot;
       }
       for (int c = 0; c < R.nc; ++c) {
         const TcsCopy& C = R.copies[c];

@@ -56,7 +56,8 @@ struct VProb {
 // blocks are packed into "bins" of at most 128 rows (each block padded to 16 rows: its
 // slot); one CTA evaluates, for one vector, every sandwich term of every block of a bin:
 //   C_s += A_t (sN_t X + sT_t X^T) B_t          (slot s of term t, X = stored vector block q)
-// in rounds that each take one vector block q and at most one term per slot:
+// in rounds of up to TCS_MAXSUB sub-blocks; a sub-block takes one vector block q and at
+// most one term per slot:
 //   GEMM1  D1 = [A_t stacked by slot] [X; X^T]^T     (M = 128, N = 2 nk, K = nk)
 //   T      = sN D1[:, :nk] + sT D1[:, nk:]           per row (slot), zero for slots without a term
 //   GEMM2  D2 += T [B_t^T stacked by slot]^T         (M = 128, N = bin rows, K = nk)
@@ -67,8 +68,10 @@ struct VProb {
 constexpr int TCS_MAXN = 80;             // n_out and nk of terms on this path
 constexpr int TCS_ROWS = 128;            // rows of a bin
 constexpr int TCS_MAXSLOTS = 8;
+constexpr int TCS_MAXSUB = 4;            // vector blocks of a round
 constexpr int TCS_NSLOT = 8;             // rounds in flight (stage barriers / headers)
-constexpr int TCS_HDR = 128;             // bytes of a round header
+constexpr int TCS_HDR = 384;             // bytes of a round header
+constexpr int TCS_MAX_AREA = 80 * 1024;  // bytes of one round's tiles
 constexpr int TCS_CONV_WARPS = 8;        // warps forming T: two per TMEM lane quarter, alternate 16-column chunks
 constexpr int TCS_THREADS = 32 * (TCS_CONV_WARPS + 2);   // + one bulk-copy warp and one MMA-issue warp
 
@@ -77,7 +80,7 @@ struct TcsJob {                          // one bin (CTA x vector)
   int s0, ns;                            // slots [s0, s0 + ns)
   int rows16;                            // rows of the bin (sum of slot rows)
   int sys;
-  int kmax16;                            // largest K of the job's rounds (sizes the TMEM buffers of GEMM1)
+  int d1w;                               // TMEM columns of one GEMM1 buffer (>= every round's sum of 2 nk)
   int pad;
 };
 struct TcsSlot {
@@ -86,8 +89,16 @@ struct TcsSlot {
   int row0;                              // first row of the slot in the bin
 };
 struct TcsTerm {
-  int slot;
+  int slot;                              // slot | (sub-block << 8)
   float sN, sT;
+};
+struct TcsSub {                          // one vector block of a round
+  uint16_t nk16;                         // its K
+  uint16_t dc;                           // GEMM1 columns [dc, dc + 2 nk16) of the round's D1 buffer
+  uint16_t tk;                           // its columns [tk, tk + nk16) of T
+  uint16_t pad;
+  uint32_t a_off;                        // byte offset of its A tile in the round's area (B tile, then X tile follow)
+  uint32_t mask;                         // slots with a term
 };
 struct TcsCopy {                         // bulk copy into the round's stage area
   int64_t src;                           // element offset: image pool (kind 0) or the vector's X images (kind 1)
@@ -96,18 +107,21 @@ struct TcsCopy {                         // bulk copy into the round's stage are
   int kind;
   int pad;
 };
-constexpr int TCS_REC_COPIES = 16;
+constexpr int TCS_REC_COPIES = 20;
+constexpr int TCS_REC_TERMS = TCS_MAXSUB * TCS_MAXSLOTS;
 // One round, fixed size (the copy warp prefetches records many rounds ahead with bulk copies).
 struct TcsRec {
-  uint32_t bytes;                        // area of the round: A tile + B tile + X tile
+  uint32_t bytes;                        // area of the round: per sub-block A tile + B tile + X tile
   uint32_t tx;                           // bytes its copies deliver (slots without a term get none)
-  int nk16;                              // K of the round (vector block rows, rounded up to 16)
-  int nt, nc;                            // terms, copies
-  int pad[3];
-  TcsTerm terms[TCS_MAXSLOTS];
+  int nsub, nt, nc;                      // sub-blocks, terms, copies
+  int ktot;                              // sum of the sub-blocks' nk16 (columns of T)
+  int pad[2];
+  TcsSub subs[TCS_MAXSUB];
+  TcsTerm terms[TCS_REC_TERMS];
   TcsCopy copies[TCS_REC_COPIES];
+  int pad2[16];
 };
-static_assert(sizeof(TcsRec) == 512, "round record");
+static_assert(sizeof(TcsRec) == 1024, "round record");
 
 constexpr int GEMV_KC = 2048;         // K chunk staged in shared memory per GEMV tile
 constexpr int GEMV_ROWS = 32;         // rows of a GEMV tile
