@@ -963,6 +963,15 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   // Phase 2 prologue: Z = FvR^T U_cat (v x sum n_p), read by the E3 products below
   add_dense(G.dp2, DENSE_TILE_TC, 1 << 30, B_WORK, P->work_z, (int)nsum, 0, v, (int)nsum, B_WORK, P->work_fvr, v, 1, v, B_POOL, off_Ucat,
             (int)nsum, 0, 1.0);
+  {   // the same two products, whole
+    std::vector<DProb> g1, g2;
+    add_dense(g1, 1 << 30, 1 << 30, B_WORK, P->work_fvr, v, 0, v, v, B_POOL, off_Ucat, (int)nsum, 0, (int)nsum, B_WORK,
+              P->work_y, v, 0, -1.0);
+    add_dense(g2, 1 << 30, 1 << 30, B_WORK, P->work_z, (int)nsum, 0, v, (int)nsum, B_WORK, P->work_fvr, v, 1, v, B_POOL,
+              off_Ucat, (int)nsum, 0, 1.0);
+    P->prog.h_gfull.clear();
+    if (g1.size() == 1 && g2.size() == 1) P->prog.h_gfull = {g1[0], g2[0]};
+  }
   // Phase 2
   for (int p = 0; p < npairs; ++p) {
     const int nn = (int)nP(p);

@@ -366,6 +366,21 @@ void blas_dgemm_groups(const std::vector<GemmProb<double>>& big, cudaStream_t s)
 }
 }  // namespace
 
+// C = alpha op(A) op(B) + beta C (row-major, single precision storage) for `batch`
+// independent triples at element strides sA, sB, sC (0: shared operand); tf32 selects
+// TF32 tensor-core arithmetic with FP32 accumulation, else plain FP32.
+void blas_sgemm_strided(bool tf32, int ta, int tb, int M, int N, int K, float alpha, const float* A, int lda, long long sA,
+                        const float* B, int ldb, long long sB, float beta, float* C, int ldc, long long sC, int batch,
+                        cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return;
+  cublasHandle_t h = t_blas.get(s);
+  const cublasOperation_t opb = tb ? CUBLAS_OP_T : CUBLAS_OP_N, opa = ta ? CUBLAS_OP_T : CUBLAS_OP_N;
+  const cublasStatus_t st = cublasGemmStridedBatchedEx(
+      h, opb, opa, N, M, K, &alpha, B, CUDA_R_32F, ldb, sB, A, CUDA_R_32F, lda, sA, &beta, C, CUDA_R_32F, ldc, sC, batch,
+      tf32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F_PEDANTIC, CUBLAS_GEMM_DEFAULT);
+  PN_CHECK(st == CUBLAS_STATUS_SUCCESS, PNOEOM_ERR_CUDA, "cuBLAS strided-batched GEMM failed");
+}
+
 template <typename T>
 void grouped_gemm(const std::vector<GemmProb<T>>& probs_in, cudaStream_t s) {
   if (probs_in.empty()) return;

@@ -21,6 +21,11 @@ struct GemmProb {
 // Problems of one call run concurrently: their C regions must not overlap.
 template <typename T>
 void grouped_gemm(const std::vector<GemmProb<T>>& probs, cudaStream_t s);
+// C = alpha op(A) op(B) + beta C (row-major FP32 storage) for `batch` triples at element
+// strides sA, sB, sC (0: shared operand); tf32: TF32 tensor cores, FP32 accumulation.
+void blas_sgemm_strided(bool tf32, int ta, int tb, int M, int N, int K, float alpha, const float* A, int lda, long long sA,
+                        const float* B, int ldb, long long sB, float beta, float* C, int ldc, long long sC, int batch,
+                        cudaStream_t s);
 
 // out[perm-index] = alpha * in + beta * out, where dims_in are the input's
 // dimensions (row-major) and perm[k] = the input axis placed at output axis k.

@@ -59,6 +59,9 @@ struct Program {
   int n_gen2x = 0;
   std::vector<SProb> h_gen2x;
   std::vector<SProb> h_gen1, h_gen2;
+  // the two whole E3 products (FvR = -U_cat Y, Z = FvR^T U_cat) as untiled problems: in the
+  // single-precision sigma of a single system they run as strided-batched library GEMMs
+  std::vector<DProb> h_gfull;
   std::vector<VProb> h_v1, h_v2;
   std::vector<DProb> h_d1, h_d2, h_d3;
   void upload(cudaStream_t s, size_t* fp);
@@ -177,7 +180,7 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
 // (timing hook: if rec != nullptr, rec(cls, launch) wraps each kernel class)
 template <typename T>
 void run_program(const Program& prog, const SysTable& t, const int64_t* out_len, const int64_t* work_len,
-                 cudaStream_t s, pnoeom_pno* timing_owner = nullptr);
+                 cudaStream_t s, pnoeom_pno* timing_owner = nullptr, bool library = false);
 void build_system(pnoeom_ctx* ctx, const pnoeom_system* sys, const pnoeom_opts* opts, cudaStream_t s,
                   pnoeom_pno* P);
 template <typename T>

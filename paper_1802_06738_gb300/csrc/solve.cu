@@ -117,7 +117,7 @@ static void tune_sets(Program& prog, const SysTable& t, cudaStream_t s, double* 
 
 template <typename T>
 void run_program(const Program& prog, const SysTable& t, const int64_t* out_len, const int64_t* work_len,
-                 cudaStream_t s, pnoeom_pno* timing_owner) {
+                 cudaStream_t s, pnoeom_pno* timing_owner, bool library) {
   for (int k = 0; k < t.nsys; ++k) {
     const SysBuf& b = t.s[k];
     if (b.nvec <= 0) continue;
@@ -152,10 +152,36 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     n0 = small(prog.small1);
     run_sandwich<T>(prog.gen1.get(), prog.n_gen1, t, prog.smem_elems, s);
   });
-  timed(4, [&] { run_dense<T>(prog.d1.get(), prog.n_d1, t, DENSE_TILE_TC, s); });
+  // single-precision single-system calls that may use a library (not the no-allocation
+  // entry point): the two whole E3 products as strided-batched GEMMs over the vectors (TF32
+  // tensor cores for the BF16 sigma, FP32 otherwise)
+  const bool whole = library && sizeof(T) == 4 && t.nsys == 1 && prog.h_gfull.size() == 2 && prog.h_gfull[0].tc == 0 &&
+                     prog.h_gfull[1].tc == 0;
+  auto whole_gemm = [&](const DProb& P) {
+    const SysBuf& b = t.s[0];
+    auto at = [&](int buf, int64_t off, long long& stride) -> float* {
+      switch (buf) {
+        case B_POOL: stride = 0; return (float*)b.pool + off;
+        case B_RIN: stride = b.rin_stride; return (float*)b.rin + off;
+        case B_WORK: stride = b.work_stride; return (float*)b.work + off;
+        default: stride = b.sout_stride; return (float*)b.sout + off;
+      }
+    };
+    long long sa, sb, sc;
+    const float* A = at(P.a_buf, P.a_off, sa);
+    const float* Bm = at(P.b_buf, P.b_off, sb);
+    float* C = at(P.c_buf, P.c_off, sc);
+    blas_sgemm_strided(b.pool16 != nullptr, P.ta, P.tb, P.M, P.N, P.K, (float)P.alpha, A, P.lda, sa, Bm, P.ldb, sb, 1.0f,
+                       C, P.ldc, sc, b.nvec, s);
+  };
+  timed(4, [&] {
+    if (whole) whole_gemm(prog.h_gfull[0]);
+    else run_dense<T>(prog.d1.get(), prog.n_d1, t, DENSE_TILE_TC, s);
+  });
   timed(1, [&] { run_gemv<T>(prog.v1.get(), prog.n_v1, t, s); });
   timed(5, [&] {
-    run_dense<T>(prog.d2.get(), prog.n_d2, t, DENSE_TILE_TC, s);
+    if (whole) whole_gemm(prog.h_gfull[1]);
+    else run_dense<T>(prog.d2.get(), prog.n_d2, t, DENSE_TILE_TC, s);
     run_dense<T>(prog.d3.get(), prog.n_d3, t, 32, s);
   });
   // BF16 single-system calls: the phase-2 sandwiches on the tensor cores (blocks above
@@ -178,12 +204,14 @@ void run_program(const Program& prog, const SysTable& t, const int64_t* out_len,
     P->prof_launches[1] += prog.n_v1 > 0;
     P->prof_launches[2] += tcs ? 2 + (prog.n_gen2x > 0) : n2 + (prog.n_gen2 > 0);
     P->prof_launches[3] += prog.n_v2 > 0;
-    P->prof_launches[4] += prog.n_d1 > 0;
-    P->prof_launches[5] += (prog.n_d2 > 0) + (prog.n_d3 > 0);
+    P->prof_launches[4] += whole ? 1 : prog.n_d1 > 0;
+    P->prof_launches[5] += (whole ? 1 : prog.n_d2 > 0) + (prog.n_d3 > 0);
   }
 }
-template void run_program<double>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*);
-template void run_program<float>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*);
+template void run_program<double>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*,
+                                   bool);
+template void run_program<float>(const Program&, const SysTable&, const int64_t*, const int64_t*, cudaStream_t, pnoeom_pno*,
+                                  bool);
 
 template <typename T>
 void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s, bool bf16) {
@@ -202,7 +230,7 @@ void apply_sigma(pnoeom_pno* P, int nvec, const T* r, T* out, cudaStream_t s, bo
     t.s[0].ximg_stride = P->prog.tcs_xstride;
   }
   const int64_t ol = P->L, wl = P->work_len;
-  run_program<T>(P->prog, t, &ol, &wl, s, P);
+  run_program<T>(P->prog, t, &ol, &wl, s, P, true);
 }
 template void apply_sigma<double>(pnoeom_pno*, int, const double*, double*, cudaStream_t, bool);
 template void apply_sigma<float>(pnoeom_pno*, int, const float*, float*, cudaStream_t, bool);
