@@ -944,30 +944,33 @@ __global__ void k_wait_selftest(long long budget, int* out) {
   }
 }
 
-// Dense block times vectors, one (GV_ROWS-row, K-chunk) tile of one block per CTA (split-K,
-// atomic accumulation).  The K chunk of up to R vectors is staged in shared memory (zero
-// beyond the block's K); each warp owns 4 rows and its lanes read 16-byte vectors of
-// consecutive columns, so a warp streams 512 contiguous bytes of every row per step while
-// each staged x vector is reused for 4 rows; the 4 x R partial sums stay in registers over
-// the whole chunk and are reduced across the warp once.  The pool rows must start on
-// 16-byte boundaries (block offsets and leading dimensions are multiples of 8 elements).
-// TA is the pool's element type: the arithmetic type T, or bf16 for the BF16 copy.
+// Dense block times vectors, one (GEMV_ROWS-row, K-chunk) tile of one block per CTA
+// (split-K, atomic accumulation).  The K chunk of up to R vectors is staged in shared
+// memory (zero beyond the block's K); each of the 8 warps owns GEMV_ROWS / 8 rows and its lanes read
+// 16-byte vectors of consecutive columns, two column steps per iteration (16 loads in
+// flight per lane), so each staged x vector is reused for every row of the warp; the partial sums
+// stay in registers over the whole chunk and are reduced across the warp once, by a
+// reduce-scatter over shuffles (each exchange halves the values a lane holds; lane l ends
+// with the sums of flattened (row, vector) indices l * (rows x R / 32) + j).  The pool rows must
+// start on 16-byte boundaries (block offsets and leading dimensions are multiples of 8
+// elements).  TA is the pool's element type: the arithmetic type T, or bf16 for the BF16 copy.
 template <typename TA> struct PoolVec;
 template <> struct PoolVec<float> {
   static constexpr int N = 4;
-  __device__ static void load(const float* p, float (&v)[4]) { ld4(p, v); }
+  __device__ static void cvt(const uint4& q, float (&v)[4]) {
+    v[0] = __uint_as_float(q.x); v[1] = __uint_as_float(q.y); v[2] = __uint_as_float(q.z); v[3] = __uint_as_float(q.w);
+  }
 };
 template <> struct PoolVec<double> {
   static constexpr int N = 2;
-  __device__ static void load(const double* p, double (&v)[2]) {
-    const double2 q = *reinterpret_cast<const double2*>(p);
-    v[0] = q.x; v[1] = q.y;
+  __device__ static void cvt(const uint4& q, double (&v)[2]) {
+    v[0] = __hiloint2double((int)q.y, (int)q.x);
+    v[1] = __hiloint2double((int)q.w, (int)q.z);
   }
 };
 template <> struct PoolVec<__nv_bfloat16> {
   static constexpr int N = 8;
-  __device__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
-    const uint4 q = *reinterpret_cast<const uint4*>(p);
+  __device__ static void cvt(const uint4& q, float (&v)[8]) {
     const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -977,52 +980,67 @@ template <> struct PoolVec<__nv_bfloat16> {
     }
   }
 };
+constexpr int GEMV_WROWS = GEMV_ROWS / 8;   // rows per warp
+
+// One exchange of the warp reduce-scatter over the first N of the lane's sums (N > 1: the
+// lane keeps the upper half when bit sh of its index is set; N == 1: plain pairwise add).
+template <typename T, int NV, int N>
+__device__ __forceinline__ void gemv_rs_step(T (&acc)[NV], int lane, int sh) {
+  if constexpr (N > 1) {
+    const bool up = (lane >> sh) & 1;
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const T send = up ? acc[i] : acc[i + N / 2];
+      const T keep = up ? acc[i + N / 2] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << sh);
+    }
+  } else {
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1 << sh);
+  }
+}
 
 template <typename T, typename TA, int R>
 __device__ __forceinline__ void gemv_tile(const VProb& P, const SysTable& tab, T* xs) {
   constexpr int VEC = PoolVec<TA>::N;
+  constexpr int NV = GEMV_WROWS * R;          // partial sums per lane
+  static_assert(NV % 32 == 0 || NV == 16, "reduce-scatter of 16 or a multiple of 32 sums");
   const int nroots = tab.s[P.sys].nvec;
   const TA* A = (const TA*)(sizeof(TA) == 2 ? tab.s[P.sys].pool16 : tab.s[P.sys].pool) + P.a_off;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kl = P.klen, klp = (kl + VEC - 1) / VEC * VEC;
   const T alpha = (T)P.alpha;
-  const TA* arow[4];
-  bool rv[4];
+  const TA* arow[GEMV_WROWS];
+  bool rv[GEMV_WROWS];
 #pragma unroll
-  for (int rr = 0; rr < 4; ++rr) {
-    const int m = P.m0 + warp * 4 + rr;
-    rv[rr] = m < P.M && warp * 4 + rr < GEMV_ROWS;
+  for (int rr = 0; rr < GEMV_WROWS; ++rr) {
+    const int m = P.m0 + warp * GEMV_WROWS + rr;
+    rv[rr] = m < P.M;
     arow[rr] = A + (int64_t)(rv[rr] ? m : P.m0) * P.lda + P.k0;
   }
   for (int r0 = 0; r0 < nroots; r0 += R) {
     const int nr = min(R, nroots - r0);
     __syncthreads();
-    for (int e = threadIdx.x; e < nr * klp; e += blockDim.x) {
-      const int q = e / klp, kk = e - q * klp;
-      T val = T(0);
-      if (kk < kl) {
-        int xk = P.k0 + kk;
-        if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
-        val = cbuf<T>(tab, P.sys, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
+    for (int q = 0; q < nr; ++q) {
+      const T* xq = cbuf<T>(tab, P.sys, P.x_buf, r0 + q) + P.x_off;
+      for (int kk = threadIdx.x; kk < klp; kk += blockDim.x) {
+        T val = T(0);
+        if (kk < kl) {
+          int xk = P.k0 + kk;
+          if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
+          val = xq[(int64_t)xk * P.x_stride];
+        }
+        xs[q * GEMV_KC + kk] = val;
       }
-      xs[q * GEMV_KC + kk] = val;
     }
     __syncthreads();
-    T acc[4][R];
+    T acc[NV];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr)
+    for (int i = 0; i < NV; ++i) acc[i] = T(0);
+    auto step = [&](int kk, const uint4 (&raw)[GEMV_WROWS]) {
+      T a[GEMV_WROWS][VEC];
 #pragma unroll
-      for (int q = 0; q < R; ++q) acc[rr][q] = T(0);
-    for (int kk = lane * VEC; kk < klp; kk += 32 * VEC) {
-      T a[4][VEC];
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        if (rv[rr]) PoolVec<TA>::load(arow[rr] + kk, a[rr]);
-        else {
-#pragma unroll
-          for (int w = 0; w < VEC; ++w) a[rr][w] = T(0);
-        }
-      }
+      for (int rr = 0; rr < GEMV_WROWS; ++rr) PoolVec<TA>::cvt(raw[rr], a[rr]);
+      // each staged x value is read once and applied to every row of the warp
 #pragma unroll
       for (int q = 0; q < R; ++q) {
         if (q < nr) {
@@ -1031,35 +1049,52 @@ __device__ __forceinline__ void gemv_tile(const VProb& P, const SysTable& tab, T
           for (int w = 0; w < VEC; ++w) {
             const T xv = xq[w];
 #pragma unroll
-            for (int rr = 0; rr < 4; ++rr) acc[rr][q] += a[rr][w] * xv;
+            for (int rr = 0; rr < GEMV_WROWS; ++rr) acc[rr * R + q] += a[rr][w] * xv;
           }
         }
       }
-    }
+    };
+    int kk = lane * VEC;
+    for (; kk + 32 * VEC < klp; kk += 64 * VEC) {   // two column steps per iteration
+      uint4 ra[GEMV_WROWS], rb[GEMV_WROWS];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        T v = acc[rr][q];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        acc[rr][q] = v;
+      for (int rr = 0; rr < GEMV_WROWS; ++rr) {
+        ra[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk) : make_uint4(0u, 0u, 0u, 0u);
+        rb[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk + 32 * VEC) : make_uint4(0u, 0u, 0u, 0u);
       }
-    // lane 4 * q + rr (q < R <= 8) adds the sum of row rr, vector q
+      step(kk, ra);
+      step(kk + 32 * VEC, rb);
+    }
+    if (kk < klp) {
+      uint4 ra[GEMV_WROWS];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr)
+      for (int rr = 0; rr < GEMV_WROWS; ++rr)
+        ra[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk) : make_uint4(0u, 0u, 0u, 0u);
+      step(kk, ra);
+    }
+    // reduce-scatter across the warp: after the exchange at bit s a lane keeps the upper
+    // half of its values when bit s of its lane index is set (16 sums: four exchanges, then
+    // lanes 2l and 2l + 1 add their single values)
+    constexpr int PER = NV >= 32 ? NV / 32 : 1;   // sums a lane ends with
+    gemv_rs_step<T, NV, NV>(acc, lane, 4);
+    gemv_rs_step<T, NV, (NV >= 2 ? NV / 2 : 1)>(acc, lane, 3);
+    gemv_rs_step<T, NV, (NV >= 4 ? NV / 4 : 1)>(acc, lane, 2);
+    gemv_rs_step<T, NV, (NV >= 8 ? NV / 8 : 1)>(acc, lane, 1);
+    gemv_rs_step<T, NV, (NV >= 16 ? NV / 16 : 1)>(acc, lane, 0);
+    const bool writer = NV >= 32 || (lane & (32 / NV - 1)) == 0;
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        if (lane == 4 * q + rr && rv[rr] && q < nr) {
-          const int m = P.m0 + warp * 4 + rr;
-          int cm = m;
-          if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
-          atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[rr][q]);
-        }
+    for (int j = 0; j < PER; ++j) {
+      const int idx = NV >= 32 ? lane * PER + j : lane / (32 / NV), rr = idx / R, q = idx % R;
+      const int m = P.m0 + warp * GEMV_WROWS + rr;
+      if (writer && q < nr && m < P.M) {
+        int cm = m;
+        if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
+        atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[j]);
+      }
+    }
   }
 }
 
-// In FP32 a system whose table entry carries the BF16 pool copy reads its blocks from it.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_gemv(const VProb* __restrict__ probs, const __grid_constant__ SysTable tab) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

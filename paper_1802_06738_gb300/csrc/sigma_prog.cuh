@@ -124,7 +124,7 @@ struct TcsRec {
 static_assert(sizeof(TcsRec) == 1024, "round record");
 
 constexpr int GEMV_KC = 2048;         // K chunk staged in shared memory per GEMV tile
-constexpr int GEMV_ROWS = 32;         // rows of a GEMV tile
+constexpr int GEMV_ROWS = 32;         // rows of a GEMV tile (4 per warp)
 constexpr int POOL_ALIGN = 8;         // GEMV blocks: offsets and leading dimensions are multiples of this
 constexpr int SMALL_DIM = 64;         // sandwich problems with all dims <= this use the shared-memory kernel
 
