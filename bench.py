@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--solves", type=int, default=0, help="repeated Davidson solves for latency percentiles "
                                                           "(0: the workload's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solves", action="store_true", help="skip the Davidson solves (profiling runs of the sigma steps)")
     ap.add_argument("--mode", default="sigma", choices=["sigma", "batched", "serving"],
                     help="sigma: medium-workload sigma throughput (default); batched: many systems in one "
                          "launch sequence; serving: Poisson request stream through the continuous-batching server")
@@ -209,42 +210,61 @@ def nvtx_pop():
         pass
 
 
-def roofline(dom, steps, peaks, dev_peaks, clk):
+# kernel classes that run on the tensor cores, per mixed precision (the rest run on the
+# SIMT pipes or stream dense blocks): the E3 products (cuBLAS, TF32 in the BF16 sigma,
+# the 3xTF32 tile kernel in the FP32 sigma) and, in the BF16 sigma, the sandwich terms
+# (tcgen05 kind::f16 with BF16 operands)
+TENSOR_CLASSES = {"BF16": {"sandwich->sigma": "bf16", "gemm->sigma": "tf32", "gemm->intermediates": "tf32"},
+                  "FP32": {"gemm->sigma": "tf32", "gemm->intermediates": "tf32"}}
+
+
+def roofline(dom, steps, peaks, dev_peaks, clk, mixed):
     """Roofline entry of the dominant kernel class.  The peak is the one of the unit the
-    class runs on, measured on this device: HBM copy bandwidth (MEASURED_PEAKS.json) for
-    the streaming classes, the FP32 FMA rate (pnoeom_measure_peaks) for the SIMT
-    contraction classes and the tcgen05 TF32 rate for the tensor-core GEMM classes;
-    which bound applies is decided by the class's arithmetic intensity against the ridge.
-    `vs_tensor_bf16` gives the same FLOP rate as a fraction of the measured BF16 tensor
-    peak, for the classes that do not run on the tensor cores."""
+    class runs on: the BF16 tensor rate of MEASURED_PEAKS.json (the sustained figure: the
+    class is timed inside a loop of whole sigma calls) for the BF16 tensor-core class, half
+    of it (the nominal TF32:BF16 ratio) for TF32 classes, the FP32 FMA rate measured by
+    pnoeom_measure_peaks for SIMT contraction classes, and the HBM copy bandwidth of
+    MEASURED_PEAKS.json for streaming classes; which bound applies is decided by the class's
+    arithmetic intensity against the ridge.  The device's own tcgen05 BF16 microbenchmark
+    is given beside it."""
     hbm, src = (peaks.get("hbm_gbs"), "of measured (MEASURED_PEAKS.json hbm_gbs)") if peaks.get("hbm_gbs") \
         else (6800.0, "of fallback")
     fp32 = dev_peaks.get("fp32_fma_tflops") or 0.0
-    tf32 = dev_peaks.get("tc_tf32_tflops") or 0.0
-    bf16 = dev_peaks.get("tc_bf16_tflops") or peaks.get("bf16_tflops") or 0.0
+    if peaks.get("bf16_tflops_sustained"):
+        bf16, bsrc = peaks["bf16_tflops_sustained"], "of measured (MEASURED_PEAKS.json bf16_tflops_sustained)"
+    elif peaks.get("bf16_tflops"):
+        bf16, bsrc = peaks["bf16_tflops"], "of measured (MEASURED_PEAKS.json bf16_tflops)"
+    else:
+        bf16, bsrc = 1900.0, "of fallback"
+    kind = TENSOR_CLASSES.get(mixed, {}).get(dom["name"])
     avg_ms = dom["ms"] / steps
     intensity = dom["flops"] / max(dom["bytes"], 1.0)
-    tensor = dom["name"].startswith("gemm")
-    alu = tf32 if tensor else fp32
+    if kind == "bf16":
+        alu, asrc = bf16, bsrc
+    elif kind == "tf32":
+        alu, asrc = bf16 / 2.0, bsrc + " x 1/2 (nominal TF32:BF16 ratio)"
+    else:
+        alu, asrc = fp32, "of measured: FP32 FMA (SIMT) by pnoeom_measure_peaks"
     ridge = alu * 1e12 / (hbm * 1e9) if alu else float("inf")
     common = {"kernel": dom["name"], "algorithmic_bytes_per_call": dom["bytes"], "algorithmic_flops_per_call": dom["flops"],
               "avg_ms_per_call": avg_ms, "launches_per_call": dom["launches"] / steps,
               "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge}
     tflops = dom["flops"] / (avg_ms * 1e-3) / 1e12
     if intensity > ridge:
-        out = {"bound": "tensor" if tensor else "alu", "achieved": tflops, "peak": alu, "unit": "TFLOP/s",
-               "frac": tflops / alu, "peak_source": ("of measured: tcgen05 kind::tf32" if tensor else
-                                                      "of measured: FP32 FMA (SIMT)") + " by pnoeom_measure_peaks", **common}
+        out = {"bound": "tensor" if kind else "alu", "achieved": tflops, "peak": alu, "unit": "TFLOP/s",
+               "frac": tflops / alu, "peak_source": asrc, **common}
     else:
         ach = dom["bytes"] / (avg_ms * 1e-3) / 1e9
         out = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src, **common}
-    if bf16:
-        out["vs_tensor_bf16"] = {"achieved_tflops": tflops, "peak_tflops": bf16, "frac": tflops / bf16,
-                                 "peak_source": "of measured: tcgen05 kind::f16 (BF16) by pnoeom_measure_peaks"}
+    dev_bf16 = dev_peaks.get("tc_bf16_tflops")
+    if dev_bf16:
+        out["vs_device_tcgen05_bf16"] = {"achieved_tflops": tflops, "peak_tflops": dev_bf16, "frac": tflops / dev_bf16,
+                                         "peak_source": "of measured: tcgen05 kind::f16 issue-rate microbenchmark "
+                                                        "(pnoeom_measure_peaks)"}
     return out
 
 
-def ncu_traffic(cls, workload):
+def ncu_traffic(cls, workload, mixed):
     """DRAM bytes per sigma call of kernel class `cls` from the committed ncu summary (a
     line "traffic per call (bytes): <class> = <bytes>"), or None.  The summary records the
     sha256 of the kernel source it was captured with ("kernel source sha256: <hex>"); once
@@ -252,7 +272,8 @@ def ncu_traffic(cls, workload):
     import hashlib
     import re
     f = os.path.join(ROOT, "profiles", f"sigma_traffic_{workload}.md")
-    src = os.path.join(ROOT, "paper_1802_06738_gb300", "csrc", "sigma_kernels.cu")
+    kfile = "sandwich_tc.cu" if (mixed == "BF16" and cls == "sandwich->sigma") else "sigma_kernels.cu"
+    src = os.path.join(ROOT, "paper_1802_06738_gb300", "csrc", kfile)
     if not os.path.exists(f) or not os.path.exists(src):
         return None
     text = open(f).read()
@@ -492,7 +513,7 @@ def main():
     rn_mixed = rn_fp64 = None
     ev_mixed = ev_fp64 = {"fp32": 0, "fp64": 0}
     opts_fp64 = pkg.make_opts(t_pno=w["t_pno"], nroots=nr, precision=pkg.FP64, max_iter=300)
-    for k in range(nsolves):
+    for k in range(0 if args.no_solves else nsolves):
         torch.cuda.synchronize(); t0 = time.perf_counter()
         e_mixed, rn_mixed, it_mixed, conv_m = gp.davidson_solve(opts_mixed, stream=stream)
         torch.cuda.synchronize(); lat_mixed.append(time.perf_counter() - t0)
@@ -584,9 +605,9 @@ def main():
         peaks = json.load(open(pf))
     dom = max(prof, key=lambda d: d["ms"])
     clocks = clk.summary()
-    roof = roofline(dom, k_cls, peaks, dev_peaks, clocks)
+    roof = roofline(dom, k_cls, peaks, dev_peaks, clocks, w["mixed"])
     roof["timing"] = f"class times from a separate loop of {k_cls} calls with CUDA events around each class"
-    roof["traffic"] = ncu_traffic(dom["name"], args.workload)
+    roof["traffic"] = ncu_traffic(dom["name"], args.workload, w["mixed"])
     if roof["traffic"] is not None:
         roof["traffic_per"] = ("call, from the committed ncu summary profiles/sigma_traffic_" + args.workload +
                                ".md (dram__bytes_read.sum + dram__bytes_write.sum)")
@@ -613,7 +634,7 @@ def main():
         gold = json.load(open(gfile))
         golden = {"n_ij_match": bool(np.array_equal(gp.n_ij, gold["n_ij"])),
                   "n_i_match": bool(np.array_equal(gp.n_i, gold["n_i"]))}
-        if "energies" in gold:
+        if "energies" in gold and e_mixed is not None:
             golden.update({"oracle_energies": gold["energies"],
                            "abs_err_mixed_refined": [abs(a - b) for a, b in zip(e_mixed, gold["energies"])],
                            "abs_err_fp64": [abs(a - b) for a, b in zip(e_fp64, gold["energies"])]})
@@ -623,13 +644,30 @@ def main():
         n = ev["fp32"] + ev["fp64"]
         return {"sigma_evals_lowprec": ev["fp32"], "sigma_evals_fp64": ev["fp64"],
                 "sigma_evals_per_s": n / float(np.percentile(xs, 50))}
+    if lat_mixed:
+        solve_section = {"mixed_refined": {**lat(lat_mixed), "iterations": it_mixed, **in_solve(ev_mixed, lat_mixed),
+                                        "energies": list(map(float, e_mixed)),
+                                        "residual_norms": list(map(float, rn_mixed)),
+                                        "unrefined_fp32_phase_energies": list(map(float, e_low)),
+                                        "unrefined_fp32_phase_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low, e_fp64)],
+                                        "unrefined_bf16_phase_energies": list(map(float, e_low16)),
+                                        "unrefined_bf16_phase_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low16, e_fp64)]},
+                      "fp64": {**lat(lat_fp64), "iterations": it_fp64, **in_solve(ev_fp64, lat_fp64),
+                               "energies": list(map(float, e_fp64)), "residual_norms": list(map(float, rn_fp64))},
+                      "max_abs_dE_mixed_vs_fp64": float(np.abs(np.asarray(e_mixed) - np.asarray(e_fp64)).max()),
+                      "pno_build_s": build_s}
+    else:
+        solve_section = {"skipped": "--no-solves (profiling run)", "pno_build_s": build_s}
     gflop_call = sum(d["flops"] for d in prof) / 1e9
     launches_call = sum(d["launches"] for d in prof) / k_cls
     line = {
         "metric": METRIC, "value": value, "unit": "sigma-evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16 blocks, f32 arithmetic" if w["mixed"] == "BF16" else "f32", "data": "synthetic",
+        "dtype": "bf16" if w["mixed"] == "BF16" else "f32", "data": "synthetic",
+        "dtype_detail": ("sandwich terms: BF16 operands on tcgen05 tensor cores, FP32 accumulation; E3 products: "
+                         "TF32 tensor cores; dense blocks: BF16 storage, FP32 arithmetic; vectors FP32")
+        if w["mixed"] == "BF16" else "FP32 SIMT arithmetic; E3 products FP32",
         "config": {"workload": workload_name(args.workload, w), "mixed_precision": w["mixed"],
                    "vec_len": int(L), "n_ij_mean": float(np.mean(gp.n_ij)), "n_ij_max": int(np.max(gp.n_ij)),
                    "nonzero_pairs": int(np.sum(np.asarray(gp.n_ij) > 0)), "n_osv_total": int(np.sum(gp.n_i)),
@@ -638,17 +676,7 @@ def main():
         "fp64_path": {"value": ws * nr * k64 / t_fp64, "unit": "sigma-evals/s", "steps": k64,
                       "ms_per_step": 1e3 * t_fp64 / k64},
         "sigma_max_rel_err_vs_fp64": errs,
-        "solve": {"mixed_refined": {**lat(lat_mixed), "iterations": it_mixed, **in_solve(ev_mixed, lat_mixed),
-                                    "energies": list(map(float, e_mixed)),
-                                    "residual_norms": list(map(float, rn_mixed)),
-                                    "unrefined_fp32_phase_energies": list(map(float, e_low)),
-                                    "unrefined_fp32_phase_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low, e_fp64)],
-                                    "unrefined_bf16_phase_energies": list(map(float, e_low16)),
-                                    "unrefined_bf16_phase_abs_err_vs_fp64": [abs(a - b) for a, b in zip(e_low16, e_fp64)]},
-                  "fp64": {**lat(lat_fp64), "iterations": it_fp64, **in_solve(ev_fp64, lat_fp64),
-                           "energies": list(map(float, e_fp64)), "residual_norms": list(map(float, rn_fp64))},
-                  "max_abs_dE_mixed_vs_fp64": float(np.abs(np.asarray(e_mixed) - np.asarray(e_fp64)).max()),
-                  "pno_build_s": build_s},
+        "solve": solve_section,
         "flop_weighted": {"gflop_per_call": gflop_call, "tflops": gflop_call / (t_mixed / args.steps) / 1e3,
                           "note": "algorithmic FLOPs of all sigma kernel classes per 6-root call / CUDA-event time"},
         "energy_check": golden,

@@ -53,11 +53,20 @@ def test_traffic_reported_only_for_the_captured_kernel_source(tmp_path, monkeypa
     (tmp_path / "profiles" / "sigma_traffic_medium.md").write_text(
         f"traffic per call (bytes): sandwich->sigma = 1234\n\nkernel source sha256: {digest}\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic("sandwich->sigma", "medium") == 1234.0
-    assert bench.ncu_traffic("dense->sigma", "medium") is None
-    assert bench.ncu_traffic("sandwich->sigma", "large") is None     # no capture of that workload
+    assert bench.ncu_traffic("sandwich->sigma", "medium", "FP32") == 1234.0
+    assert bench.ncu_traffic("dense->sigma", "medium", "FP32") is None
+    assert bench.ncu_traffic("sandwich->sigma", "large", "FP32") is None     # no capture of that workload
+    # the BF16 sandwich class is the tensor-core kernel: its own source decides
+    assert bench.ncu_traffic("sandwich->sigma", "medium", "BF16") is None
+    tck = src / "sandwich_tc.cu"
+    tck.write_text("// tensor-core kernel v1\n")
+    (tmp_path / "profiles" / "sigma_traffic_large.md").write_text(
+        "traffic per call (bytes): sandwich->sigma = 99\n\nkernel source sha256: "
+        + hashlib.sha256(tck.read_bytes()).hexdigest() + "\n")
+    assert bench.ncu_traffic("sandwich->sigma", "large", "BF16") == 99.0
     kernel.write_text("// kernel v2\n")
-    assert bench.ncu_traffic("sandwich->sigma", "medium") is None
+    assert bench.ncu_traffic("sandwich->sigma", "medium", "FP32") is None
+    assert bench.ncu_traffic("sandwich->sigma", "large", "BF16") == 99.0
 
 
 def test_reference_arm_prints_the_same_metric(capsys):
@@ -70,3 +79,21 @@ def test_reference_arm_prints_the_same_metric(capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert "unavailable" in line and "o=60" in line["config"]["workload"]
+
+
+def test_roofline_bound_per_precision():
+    """The BF16 sandwich class is tensor-bound against the BF16 peak of MEASURED_PEAKS.json
+    (sustained); in the FP32 sigma the same class is SIMT work against the FP32 FMA peak."""
+    dom = {"name": "sandwich->sigma", "ms": 10.0, "flops": 4e11, "bytes": 1e9, "launches": 2}
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+    dev = {"fp32_fma_tflops": 77.0, "tc_bf16_tflops": 2400.0}
+    r = bench.roofline(dom, 1, peaks, dev, {}, "BF16")
+    assert r["bound"] == "tensor" and r["peak"] == 1700.0 and abs(r["achieved"] - 40.0) < 1e-9
+    assert abs(r["vs_device_tcgen05_bf16"]["frac"] - 40.0 / 2400.0) < 1e-12
+    r = bench.roofline(dom, 1, peaks, dev, {}, "FP32")
+    assert r["bound"] == "alu" and r["peak"] == 77.0
+    g = dict(dom, name="gemm->sigma")
+    assert bench.roofline(g, 1, peaks, dev, {}, "BF16")["peak"] == 850.0
+    h = dict(dom, name="dense->sigma", flops=1e9)
+    r = bench.roofline(h, 1, peaks, dev, {}, "BF16")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
