@@ -332,74 +332,89 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
     // ---- MMA lane: GEMM1 of round n1 as soon as its images landed and its D1 buffer is free
     // (the T of round n1 - nd1 was formed, i.e. GEMM2 of n1 - nd1 was issued); GEMM2 of round
     // n2 as soon as its T was formed; both in round order, whichever is ready first
-    if (lane == 0) {
-      int last_bar = -1;
-      uint32_t last_par = 0;
-      int n1 = 0, n2 = 0;
-      long long t0 = clock64();
-      while (n2 < R) {
-        bool progressed = false;
-        if (n1 < R && n2 > n1 - nd1 && tc::mbar_test_wait(full + n1 % TCS_NSLOT, (uint32_t)(n1 / TCS_NSLOT) & 1u)) {
-          const int r = n1, sl = r % TCS_NSLOT;
-          tc::fence_after_sync();
-          if (trace && r < TCS_TRACE_ROUNDS) trace[12 * r + 1] = clock64();
-          const RoundHdr& H = hdr[sl];
-          const uint32_t base = tc::smem_u32(ring + H.start);
-          const uint32_t d = tmem + (uint32_t)(r % nd1) * d1w;
-          for (int i = 0; i < H.nsub; ++i) {
-            const int nk16 = H.sub[i].nk16;
-            const uint32_t SBO = (uint32_t)nk16 * 16;
-            const uint32_t aS = base + H.sub[i].a_off, xS = aS + 2u * rows16 * nk16 * 2u;
-            const uint32_t idesc1 = tc::idesc_bf16(128, 2 * nk16);
-            for (int ks = 0; ks < nk16 / 16; ++ks)
-              tc::mma_bf16(d + (uint32_t)H.sub[i].dc, tc::sdesc(aS + ks * 256, 128, SBO), tc::sdesc(xS + ks * 256, 128, SBO),
-                           idesc1, ks > 0 ? 1u : 0u);
+    // The whole warp runs the loop (every lane computes the same descriptors, so they stay
+    // warp-uniform) and one elected lane issues the MMAs and commits.
+    const bool leader = tc::elect_one();
+    int last_bar = -1;
+    uint32_t last_par = 0;
+    int n1 = 0, n2 = 0;
+    long long t0 = clock64();
+    while (n2 < R) {
+      bool progressed = false;
+      bool r1 = n1 < R && n2 > n1 - nd1 && tc::mbar_test_wait(full + n1 % TCS_NSLOT, (uint32_t)(n1 / TCS_NSLOT) & 1u);
+      r1 = __shfl_sync(0xffffffffu, r1 ? 1 : 0, 0) != 0;
+      if (r1) {
+        const int r = n1, sl = r % TCS_NSLOT;
+        tc::fence_after_sync();
+        if (trace && leader && r < TCS_TRACE_ROUNDS) trace[12 * r + 1] = clock64();
+        const RoundHdr& H = hdr[sl];
+        const uint32_t base = tc::smem_u32(ring + H.start);
+        const uint32_t d = tmem + (uint32_t)(r % nd1) * d1w;
+        const int nsub = H.nsub;
+        for (int i = 0; i < nsub; ++i) {
+          const int nk16 = H.sub[i].nk16;
+          const uint32_t SBO = (uint32_t)nk16 * 16;
+          const uint32_t aS = base + H.sub[i].a_off, xS = aS + 2u * rows16 * nk16 * 2u;
+          const uint32_t idesc1 = tc::idesc_bf16(128, 2 * nk16);
+          const uint32_t dd = d + (uint32_t)H.sub[i].dc;
+          for (int ks = 0; ks < nk16 / 16; ++ks) {
+            const uint64_t ad = tc::sdesc(aS + ks * 256, 128, SBO), xd = tc::sdesc(xS + ks * 256, 128, SBO);
+            if (leader) tc::mma_bf16(dd, ad, xd, idesc1, ks > 0 ? 1u : 0u);
           }
-          tc::mma_commit(g1 + r % nd1);
-          last_bar = (int)(g1 + r % nd1 - bars);
-          last_par = (uint32_t)(r / nd1) & 1u;
-          if (trace && r < TCS_TRACE_ROUNDS) trace[12 * r + 2] = clock64();
-          ++n1;
-          progressed = true;
         }
-        if (n2 < n1 && tc::mbar_test_wait(tready + (n2 & 1), (uint32_t)(n2 / 2) & 1u)) {
-          const int rr = n2, b = rr & 1, sl = rr % TCS_NSLOT;
-          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 8] = clock64();
-          tc::fence_after_sync();
-          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 9] = clock64();
-          const RoundHdr& H = hdr[sl];
-          const uint32_t base = tc::smem_u32(ring + H.start);
-          const uint32_t tS = tc::smem_u32(tbuf + b * TCS_TBUF), SBO_T = (uint32_t)H.ktot * 16;
-          const uint32_t idesc2 = tc::idesc_bf16(128, rows16);
-          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 10] = clock64();
-          for (int i = 0; i < H.nsub; ++i) {
-            const int nk16 = H.sub[i].nk16;
-            const uint32_t bS = base + H.sub[i].a_off + (uint32_t)rows16 * nk16 * 2u;
-            const uint32_t t0s = tS + (uint32_t)(H.sub[i].tk >> 3) * 128u;
-            for (int ks = 0; ks < nk16 / 16; ++ks)
-              tc::mma_bf16(tmem + TCS_D2_COL, tc::sdesc(t0s + ks * 256, 128, SBO_T),
-                           tc::sdesc(bS + ks * 256, 128, (uint32_t)nk16 * 16), idesc2, (rr > 0 || i > 0 || ks > 0) ? 1u : 0u);
-          }
-          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 11] = clock64();
-          tc::mma_commit(empty + sl);   // the round's area and its T tile are free again
-          last_bar = (int)(empty + sl - bars);
-          last_par = (uint32_t)(rr / TCS_NSLOT) & 1u;
-          if (trace && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 5] = clock64();
-          ++n2;
-          progressed = true;
-        }
-        if (progressed) {
-          t0 = clock64();
-        } else if (*abort_flag) {
-          break;
-        } else if (clock64() - t0 > TCS_WAIT_BUDGET) {
-          *abort_flag = 1;
-          break;
-        }
+        __syncwarp();
+        if (leader) tc::mma_commit(g1 + r % nd1);
+        last_bar = (int)(g1 + r % nd1 - bars);
+        last_par = (uint32_t)(r / nd1) & 1u;
+        if (trace && leader && r < TCS_TRACE_ROUNDS) trace[12 * r + 2] = clock64();
+        ++n1;
+        progressed = true;
       }
-      // the last commit covers every MMA issued before it: until it lands TMEM stays allocated
-      if (last_bar >= 0 && !tcs_drain(bars + last_bar, last_par)) *keep_tmem = 1;
+      bool r2 = n2 < n1 && tc::mbar_test_wait(tready + (n2 & 1), (uint32_t)(n2 / 2) & 1u);
+      r2 = __shfl_sync(0xffffffffu, r2 ? 1 : 0, 0) != 0;
+      if (r2) {
+        const int rr = n2, b = rr & 1, sl = rr % TCS_NSLOT;
+        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 8] = clock64();
+        tc::fence_after_sync();
+        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 9] = clock64();
+        const RoundHdr& H = hdr[sl];
+        const uint32_t base = tc::smem_u32(ring + H.start);
+        const uint32_t tS = tc::smem_u32(tbuf + b * TCS_TBUF), SBO_T = (uint32_t)H.ktot * 16;
+        const uint32_t idesc2 = tc::idesc_bf16(128, rows16);
+        const int nsub = H.nsub;
+        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 10] = clock64();
+        for (int i = 0; i < nsub; ++i) {
+          const int nk16 = H.sub[i].nk16;
+          const uint32_t bS = base + H.sub[i].a_off + (uint32_t)rows16 * nk16 * 2u;
+          const uint32_t t0s = tS + (uint32_t)(H.sub[i].tk >> 3) * 128u;
+          for (int ks = 0; ks < nk16 / 16; ++ks) {
+            const uint64_t td = tc::sdesc(t0s + ks * 256, 128, SBO_T), bd = tc::sdesc(bS + ks * 256, 128, (uint32_t)nk16 * 16);
+            if (leader) tc::mma_bf16(tmem + TCS_D2_COL, td, bd, idesc2, (rr > 0 || i > 0 || ks > 0) ? 1u : 0u);
+          }
+        }
+        __syncwarp();
+        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 11] = clock64();
+        if (leader) tc::mma_commit(empty + sl);   // the round's area and its T tile are free again
+        last_bar = (int)(empty + sl - bars);
+        last_par = (uint32_t)(rr / TCS_NSLOT) & 1u;
+        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 5] = clock64();
+        ++n2;
+        progressed = true;
+      }
+      if (progressed) {
+        t0 = clock64();
+      } else if (*abort_flag) {
+        break;
+      } else if (clock64() - t0 > TCS_WAIT_BUDGET) {
+        *abort_flag = 1;
+        break;
+      }
     }
+    // the last commit covers every MMA issued before it: until it lands TMEM stays allocated
+    bool drained = true;
+    if (leader && last_bar >= 0) drained = tcs_drain(bars + last_bar, last_par);
+    drained = __shfl_sync(0xffffffffu, drained ? 1 : 0, __ffs(__ballot_sync(0xffffffffu, leader)) - 1) != 0;
+    if (!drained && leader) *keep_tmem = 1;
     __syncwarp();
   } else {
     // ---- T-forming warps: T = sN D1[:, :nk] + sT D1[:, nk:] for the rows of this thread's

@@ -102,6 +102,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
   return ok != 0;
 }
 
+// One lane of a converged warp (elect.sync): the lane that issues a warp's tcgen05 work.
+__device__ __forceinline__ bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "elect.sync _|p, 0xffffffff;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(pred));
+  return pred != 0;
+}
+
 // Non-blocking test of the phase of the given parity (never suspends the thread; for
 // loops that poll more than one barrier).
 __device__ __forceinline__ bool mbar_test_wait(uint64_t* mbar, uint32_t parity) {
