@@ -32,6 +32,9 @@ CASES = {
     "mp1_ragged": (6, 30, 90, 11, 1e-6, 4, "mp1"),
     "mp1_tight": (4, 24, 40, 12, 1e-9, 3, "mp1"),
     "empty_pairs": (3, 8, 24, 13, 1e-4, 3, "mp1"),
+    # T_PNO = 0 with v = 96: every pair block (96 PNOs) is above the tensor-core path's limit
+    # of 80 and above the grouped kernel's 64, so every sandwich runs on the generic kernel
+    "wide_t0": (3, 96, 96, 14, 0.0, 2, "mp1"),
 }
 
 
@@ -174,3 +177,29 @@ def test_davidson_mixed_with_refinement(pkg, ctx):
     assert np.abs(e - w).max() < 1e-6
     ev = gp.solve_stats()   # the FP32 phase from the guesses, then the FP64 refinement
     assert ev["fp32"] >= d["nr"] and ev["fp64"] >= 1
+
+
+@pytest.mark.parametrize("case", ["mp1_ragged", "wide_t0"])
+def test_sigma_bf16_error_bound(pkg, ctx, case):
+    """BF16 sigma (tensor-core sandwiches for blocks of at most 80 PNOs, the generic kernel
+    above; BF16 dense blocks) against the oracle: relative error within 2e-2 of the largest
+    element (BF16 keeps 8 significant bits; the operands are rounded once, sums in FP32)."""
+    d = oracle_case(case)
+    gp = _build(pkg, ctx, d)
+    o, v = d["o"], d["v"]
+    rng = np.random.default_rng(9)
+    r1 = rng.standard_normal((o, v))
+    r2 = rng.standard_normal((o, o, v, v)); r2 = 0.5 * (r2 + r2.transpose(1, 0, 3, 2))
+    R = np.array([_pack_gpu(gp, r1, r2)])
+    rt = torch.tensor(R, device="cuda:0", dtype=torch.float32)
+    st = torch.zeros_like(rt)
+    gp.sigma(rt, st, precision=pkg.BF16)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    sp, ps = d["sp"], d["ps"]
+    ref1, ref2 = sp.unpack(ps(sp.pack(r1, r2)))
+    g1, g2 = _unpack_gpu(gp, st.cpu().numpy()[0].astype(np.float64))
+    scale = max(np.abs(ref1).max(), np.abs(ref2).max())
+    err = max(np.abs(g1 - ref1).max(), np.abs(g2 - ref2).max()) / scale
+    assert err < 2e-2, err
+    assert err > 0.0   # the BF16 path really rounds (it is not the FP64 one)
