@@ -56,6 +56,8 @@ def parse():
                                                           "(0: the workload's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solves", action="store_true", help="skip the Davidson solves (profiling runs of the sigma steps)")
+    ap.add_argument("--mixed", default="", choices=["", "BF16", "FP32"],
+                    help="precision of the mixed sigma (default: the workload's own)")
     ap.add_argument("--mode", default="sigma", choices=["sigma", "batched", "serving"],
                     help="sigma: medium-workload sigma throughput (default); batched: many systems in one "
                          "launch sequence; serving: Poisson request stream through the continuous-batching server")
@@ -492,7 +494,9 @@ def main():
     if rank == 0:
         pkg.build()
     barrier(ws)
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.mixed:
+        w["mixed"] = args.mixed
     o, nr = w["o"], w["nroots"]
     MIX = getattr(pkg, w["mixed"])
     nsolves = args.solves if args.solves > 0 else w["solves"]
