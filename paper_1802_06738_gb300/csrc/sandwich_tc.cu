@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(128) k_tcs_make_img(const double* __restrict__
 // term, per-slot coefficients) and the columns of T.
 struct SubHdr {
   int nk16, dc, tk;
-  uint32_t a_off, mask;
+  uint32_t a_off, b_off, x_off, mask;
   float sN[TCS_MAXSLOTS];
   float sT[TCS_MAXSLOTS];
 };
@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
   uint64_t* empty = bars + TCS_NSLOT;        // [NSLOT] the round's GEMM2 completed (its ring area is free)
   uint64_t* g1 = bars + 2 * TCS_NSLOT;       // [TCS_MAXD1] GEMM1 into D1 buffer b completed
   uint64_t* tready = g1 + TCS_MAXD1;         // [2] T tile b formed (one arrival per T-forming thread)
-  uint64_t* dqb = tready + 2;                // [2] half h of the record queue (TCS_DQ / 2 records) landed
+  uint64_t* d1free = tready + 2;             // [TCS_MAXD1] D1 buffer read out by the T-forming warps
+  uint64_t* dqb = d1free + TCS_MAXD1;        // [2] half h of the record queue (TCS_DQ / 2 records) landed
   uint32_t* misc = reinterpret_cast<uint32_t*>(dqb + 2);
   // misc: [0] TMEM base, [1] abort flag, [2] keep-TMEM flag
   volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 1);
@@ -204,6 +205,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
     for (int b = 0; b < 2 * TCS_NSLOT + TCS_MAXD1; ++b) tc::mbar_init(bars + b, 1);
     tc::mbar_init(tready, 32 * TCS_CONV_WARPS);
     tc::mbar_init(tready + 1, 32 * TCS_CONV_WARPS);
+    for (int b = 0; b < TCS_MAXD1; ++b) tc::mbar_init(d1free + b, 32 * TCS_CONV_WARPS);
     tc::mbar_init(dqb, 1);
     tc::mbar_init(dqb + 1, 1);
     *abort_flag = 0;
@@ -285,6 +287,8 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
         D.dc = U.dc;
         D.tk = U.tk;
         D.a_off = U.a_off;
+        D.b_off = U.b_off;
+        D.x_off = U.x_off;
         D.mask = U.mask;
       }
       __syncwarp();
@@ -329,92 +333,81 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
     }
     __syncwarp();
   } else if (warp == TCS_CONV_WARPS + 1) {
-    // ---- MMA lane: GEMM1 of round n1 as soon as its images landed and its D1 buffer is free
-    // (the T of round n1 - nd1 was formed, i.e. GEMM2 of n1 - nd1 was issued); GEMM2 of round
-    // n2 as soon as its T was formed; both in round order, whichever is ready first
-    // The whole warp runs the loop (every lane computes the same descriptors, so they stay
-    // warp-uniform) and one elected lane issues the MMAs and commits.
+    // ---- GEMM1 warp: GEMM1 of round r once its images landed and its D1 buffer was read
+    // out by the T-forming warps (round r - nd1).  The warp runs converged (warp-uniform
+    // descriptors) and one elected lane issues the MMAs and the commit.
     const bool leader = tc::elect_one();
-    int last_bar = -1;
-    uint32_t last_par = 0;
-    int n1 = 0, n2 = 0;
-    long long t0 = clock64();
-    while (n2 < R) {
-      bool progressed = false;
-      bool r1 = n1 < R && n2 > n1 - nd1 && tc::mbar_test_wait(full + n1 % TCS_NSLOT, (uint32_t)(n1 / TCS_NSLOT) & 1u);
-      r1 = __shfl_sync(0xffffffffu, r1 ? 1 : 0, 0) != 0;
-      if (r1) {
-        const int r = n1, sl = r % TCS_NSLOT;
-        tc::fence_after_sync();
-        if (trace && leader && r < TCS_TRACE_ROUNDS) trace[12 * r + 1] = clock64();
-        const RoundHdr& H = hdr[sl];
-        const uint32_t base = tc::smem_u32(ring + H.start);
-        const uint32_t d = tmem + (uint32_t)(r % nd1) * d1w;
-        const int nsub = H.nsub;
-        for (int i = 0; i < nsub; ++i) {
-          const int nk16 = H.sub[i].nk16;
-          const uint32_t SBO = (uint32_t)nk16 * 16;
-          const uint32_t aS = base + H.sub[i].a_off, xS = aS + 2u * rows16 * nk16 * 2u;
-          const uint32_t idesc1 = tc::idesc_bf16(128, 2 * nk16);
-          const uint32_t dd = d + (uint32_t)H.sub[i].dc;
-          for (int ks = 0; ks < nk16 / 16; ++ks) {
-            const uint64_t ad = tc::sdesc(aS + ks * 256, 128, SBO), xd = tc::sdesc(xS + ks * 256, 128, SBO);
-            if (leader) tc::mma_bf16(dd, ad, xd, idesc1, ks > 0 ? 1u : 0u);
-          }
+    int last = -1;
+    bool ok = true;
+    for (int r = 0; r < R; ++r) {
+      const int sl = r % TCS_NSLOT;
+      bool w = tcs_wait(full + sl, (uint32_t)(r / TCS_NSLOT) & 1u, abort_flag);
+      if (w && r >= nd1) w = tcs_wait(d1free + r % nd1, (uint32_t)((r - nd1) / nd1) & 1u, abort_flag);
+      ok = __all_sync(0xffffffffu, w);
+      if (!ok) break;
+      tc::fence_after_sync();
+      if (trace && leader && r < TCS_TRACE_ROUNDS) trace[12 * r + 1] = clock64();
+      const RoundHdr& H = hdr[sl];
+      const uint32_t base = tc::smem_u32(ring + H.start);
+      const uint32_t d = tmem + (uint32_t)(r % nd1) * d1w;
+      const int nsub = H.nsub;
+      for (int i = 0; i < nsub; ++i) {
+        const int nk16 = H.sub[i].nk16;
+        const uint32_t SBO = (uint32_t)nk16 * 16;
+        const uint32_t aS = base + H.sub[i].a_off, xS = base + H.sub[i].x_off;
+        const uint32_t idesc1 = tc::idesc_bf16(128, 2 * nk16);
+        const uint32_t dd = d + (uint32_t)H.sub[i].dc;
+        for (int ks = 0; ks < nk16 / 16; ++ks) {
+          const uint64_t ad = tc::sdesc(aS + ks * 256, 128, SBO), xd = tc::sdesc(xS + ks * 256, 128, SBO);
+          if (leader) tc::mma_bf16(dd, ad, xd, idesc1, ks > 0 ? 1u : 0u);
         }
-        __syncwarp();
-        if (leader) tc::mma_commit(g1 + r % nd1);
-        last_bar = (int)(g1 + r % nd1 - bars);
-        last_par = (uint32_t)(r / nd1) & 1u;
-        if (trace && leader && r < TCS_TRACE_ROUNDS) trace[12 * r + 2] = clock64();
-        ++n1;
-        progressed = true;
       }
-      bool r2 = n2 < n1 && tc::mbar_test_wait(tready + (n2 & 1), (uint32_t)(n2 / 2) & 1u);
-      r2 = __shfl_sync(0xffffffffu, r2 ? 1 : 0, 0) != 0;
-      if (r2) {
-        const int rr = n2, b = rr & 1, sl = rr % TCS_NSLOT;
-        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 8] = clock64();
-        tc::fence_after_sync();
-        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 9] = clock64();
-        const RoundHdr& H = hdr[sl];
-        const uint32_t base = tc::smem_u32(ring + H.start);
-        const uint32_t tS = tc::smem_u32(tbuf + b * TCS_TBUF), SBO_T = (uint32_t)H.ktot * 16;
-        const uint32_t idesc2 = tc::idesc_bf16(128, rows16);
-        const int nsub = H.nsub;
-        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 10] = clock64();
-        for (int i = 0; i < nsub; ++i) {
-          const int nk16 = H.sub[i].nk16;
-          const uint32_t bS = base + H.sub[i].a_off + (uint32_t)rows16 * nk16 * 2u;
-          const uint32_t t0s = tS + (uint32_t)(H.sub[i].tk >> 3) * 128u;
-          for (int ks = 0; ks < nk16 / 16; ++ks) {
-            const uint64_t td = tc::sdesc(t0s + ks * 256, 128, SBO_T), bd = tc::sdesc(bS + ks * 256, 128, (uint32_t)nk16 * 16);
-            if (leader) tc::mma_bf16(tmem + TCS_D2_COL, td, bd, idesc2, (rr > 0 || i > 0 || ks > 0) ? 1u : 0u);
-          }
-        }
-        __syncwarp();
-        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 11] = clock64();
-        if (leader) tc::mma_commit(empty + sl);   // the round's area and its T tile are free again
-        last_bar = (int)(empty + sl - bars);
-        last_par = (uint32_t)(rr / TCS_NSLOT) & 1u;
-        if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 5] = clock64();
-        ++n2;
-        progressed = true;
-      }
-      if (progressed) {
-        t0 = clock64();
-      } else if (*abort_flag) {
-        break;
-      } else if (clock64() - t0 > TCS_WAIT_BUDGET) {
-        *abort_flag = 1;
-        break;
-      }
+      __syncwarp();
+      if (leader) tc::mma_commit(g1 + r % nd1);
+      last = r;
+      if (trace && leader && r < TCS_TRACE_ROUNDS) trace[12 * r + 2] = clock64();
     }
-    // the last commit covers every MMA issued before it: until it lands TMEM stays allocated
+    // the last commit covers every MMA this warp issued: until it lands TMEM stays allocated
     bool drained = true;
-    if (leader && last_bar >= 0) drained = tcs_drain(bars + last_bar, last_par);
-    drained = __shfl_sync(0xffffffffu, drained ? 1 : 0, __ffs(__ballot_sync(0xffffffffu, leader)) - 1) != 0;
-    if (!drained && leader) *keep_tmem = 1;
+    if (leader && last >= 0) drained = tcs_drain(g1 + last % nd1, (uint32_t)(last / nd1) & 1u);
+    if (!__all_sync(0xffffffffu, drained || !leader) && leader) *keep_tmem = 1;
+    __syncwarp();
+  } else if (warp == TCS_CONV_WARPS + 2) {
+    // ---- GEMM2 warp: GEMM2 of round r once its T was formed; its commit frees the round's
+    // ring area and T tile
+    const bool leader = tc::elect_one();
+    int last = -1;
+    bool ok = true;
+    for (int rr = 0; rr < R; ++rr) {
+      const int b = rr & 1, sl = rr % TCS_NSLOT;
+      ok = __all_sync(0xffffffffu, tcs_wait(tready + b, (uint32_t)(rr / 2) & 1u, abort_flag));
+      if (!ok) break;
+      if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 8] = clock64();
+      tc::fence_after_sync();
+      const RoundHdr& H = hdr[sl];
+      const uint32_t base = tc::smem_u32(ring + H.start);
+      const uint32_t tS = tc::smem_u32(tbuf + b * TCS_TBUF), SBO_T = (uint32_t)H.ktot * 16;
+      const uint32_t idesc2 = tc::idesc_bf16(128, rows16);
+      const int nsub = H.nsub;
+      if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 10] = clock64();
+      for (int i = 0; i < nsub; ++i) {
+        const int nk16 = H.sub[i].nk16;
+        const uint32_t bS = base + H.sub[i].b_off;
+        const uint32_t t0s = tS + (uint32_t)(H.sub[i].tk >> 3) * 128u;
+        for (int ks = 0; ks < nk16 / 16; ++ks) {
+          const uint64_t td = tc::sdesc(t0s + ks * 256, 128, SBO_T), bd = tc::sdesc(bS + ks * 256, 128, (uint32_t)nk16 * 16);
+          if (leader) tc::mma_bf16(tmem + TCS_D2_COL, td, bd, idesc2, (rr > 0 || i > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      __syncwarp();
+      if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 11] = clock64();
+      if (leader) tc::mma_commit(empty + sl);   // the round's area and its T tile are free again
+      last = rr;
+      if (trace && leader && rr < TCS_TRACE_ROUNDS) trace[12 * rr + 5] = clock64();
+    }
+    bool drained = true;
+    if (leader && last >= 0) drained = tcs_drain(empty + last % TCS_NSLOT, (uint32_t)(last / TCS_NSLOT) & 1u);
+    if (!__all_sync(0xffffffffu, drained || !leader) && leader) *keep_tmem = 1;
     __syncwarp();
   } else {
     // ---- T-forming warps: T = sN D1[:, :nk] + sT D1[:, nk:] for the rows of this thread's
@@ -488,6 +481,7 @@ __global__ void __launch_bounds__(TCS_THREADS, 1)
       tc::fence_async_smem();
       tc::fence_before_sync();
       if (trace && tid == 0 && r < TCS_TRACE_ROUNDS) trace[12 * r + 4] = clock64();
+      mbar_arrive(d1free + r % nd1);   // this round's D1 buffer has been read out
       mbar_arrive(tready + b);
     }
     // the last GEMM2, then the diagonal slot blocks of D2 into the output
@@ -659,11 +653,15 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
   std::unordered_map<ImgKey, int64_t, ImgKeyHash> images;
   std::vector<int64_t> desc;
   int64_t ipool = 0;
-  auto image = [&](ImgKey k) {
+  auto canon = [&](ImgKey k) {
     if (k.trans && k.ld == k.rows) {
       auto it = s_transpose.find(k.src);
       if (it != s_transpose.end() && it->second.second == k.K) k = ImgKey{it->second.first, k.K, 0, k.rows, k.K};
     }
+    return k;
+  };
+  auto image = [&](ImgKey k) {
+    k = canon(k);
     auto it = images.find(k);
     if (it != images.end()) return it->second;
     const int64_t off = ipool;
@@ -672,20 +670,17 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
     for (int64_t x : {k.src, (int64_t)k.ld, (int64_t)k.trans, (int64_t)k.rows, (int64_t)k.K, off}) desc.push_back(x);
     return off;
   };
+  // units: one vector block and at most one term per slot (the d-th term of every slot)
+  struct Unit { int q, nk16; std::vector<std::pair<int, const Term*>> st; };
   std::vector<TcsJob> hj;
   std::vector<TcsSlot> hsl;
-  std::vector<TcsRec> hrec;
-  std::vector<double> rcost;                 // per record: MMA issue estimate (for splitting and ordering)
-  size_t nterms = 0, ncopies = 0;
-  std::vector<std::pair<int, int>> bin_range;
+  std::vector<std::vector<Unit>> bin_units(bins.size());
   for (size_t bi = 0; bi < bins.size(); ++bi) {
     TcsJob J{};
     J.s0 = (int)hsl.size();
     J.ns = (int)bins[bi].size();
     J.rows16 = bin_rows[bi];
     J.sys = 0;
-    J.r0 = (int)hrec.size();
-    // terms of the bin by vector block, then slot
     std::map<int, std::vector<std::vector<const Term*>>> byq;   // q -> per slot, its terms
     int row0 = 0;
     for (int k = 0; k < J.ns; ++k) {
@@ -698,11 +693,6 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
         v[k].push_back(&t);
       }
     }
-    // units: one vector block and at most one term per slot (the d-th term of every slot);
-    // consecutive units share a round while the round's GEMM1 columns, sub-blocks, terms,
-    // area and copies fit
-    struct Unit { int q, nk16; std::vector<std::pair<int, const Term*>> st; };
-    std::vector<Unit> units;
     int kmax16 = 16;
     for (auto& kv : byq) {
       size_t depth = 0;
@@ -713,73 +703,100 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
         Unit u{kv.first, nk16, {}};
         for (int k = 0; k < J.ns; ++k)
           if (d < kv.second[k].size()) u.st.push_back({k, kv.second[k][d]});
-        units.push_back(u);
+        bin_units[bi].push_back(u);
       }
     }
     J.d1w = kmax16 <= 64 ? 128 : 2 * kmax16;
-    const uint32_t max_area = (uint32_t)TCS_MAX_AREA;
-    auto unit_area = [&](const Unit& u) { return (uint32_t)(2 * J.rows16 + 2 * u.nk16) * u.nk16 * 2; };
-    auto unit_copies = [&](const Unit& u, uint32_t a_off, std::vector<TcsCopy>& cp) {
-      const uint32_t tile = (uint32_t)J.rows16 * u.nk16 * 2;
-      for (auto& e : u.st) {
-        const TcsSlot& S = hsl[J.s0 + e.first];
-        const uint32_t rb = (uint32_t)S.row0 * u.nk16 * 2, sz = (uint32_t)up16(S.n_out) * u.nk16 * 2;
-        cp.push_back({image(e.second->a), a_off + rb, sz, 0, 0});
-        cp.push_back({image(e.second->b), a_off + tile + rb, sz, 0, 0});
+    hj.push_back(J);
+  }
+  // images of the units whose A and B are one image (the occupied ladder: S(ij,kl) on both
+  // sides) first, in unit order: the slots of such a unit, and consecutive units of one bin,
+  // then lie side by side in the pool and reach the round's area in one copy per tile kind
+  for (size_t bi = 0; bi < bins.size(); ++bi)
+    for (const Unit& u : bin_units[bi]) {
+      bool same = true;
+      for (auto& e : u.st) same = same && canon(e.second->a) == canon(e.second->b);
+      if (same)
+        for (auto& e : u.st) image(e.second->a);
+    }
+  // rounds: consecutive units share a round while its GEMM1 columns, sub-blocks, terms,
+  // area and merged copies fit; the area holds the sub-blocks' A tiles, then their B tiles,
+  // then their X tiles, so tiles of consecutive sub-blocks merge into one copy as well
+  std::vector<TcsRec> hrec;
+  std::vector<double> rcost;                 // per record: MMA issue estimate (for splitting and ordering)
+  size_t nterms = 0, ncopies = 0;
+  auto merge = [](std::vector<TcsCopy> cp) {   // one copy for images adjacent in the source and the area
+    std::sort(cp.begin(), cp.end(), [](const TcsCopy& a, const TcsCopy& b) { return a.dst < b.dst; });
+    std::vector<TcsCopy> m;
+    for (const TcsCopy& c : cp) {
+      if (!m.empty()) {
+        TcsCopy& l = m.back();
+        if (l.kind == c.kind && l.src + l.bytes / 2 == c.src && l.dst + l.bytes == c.dst) { l.bytes += c.bytes; continue; }
       }
-      cp.push_back({xblk[3 * u.q + 2], a_off + 2 * tile, 2u * u.nk16 * u.nk16 * 2, 1, 0});
-    };
-    auto merge = [](std::vector<TcsCopy> cp) {   // one copy for images adjacent in the source and the area
-      std::sort(cp.begin(), cp.end(), [](const TcsCopy& a, const TcsCopy& b) { return a.dst < b.dst; });
-      std::vector<TcsCopy> m;
-      for (const TcsCopy& c : cp) {
-        if (!m.empty()) {
-          TcsCopy& l = m.back();
-          if (l.kind == c.kind && l.src + l.bytes / 2 == c.src && l.dst + l.bytes == c.dst) { l.bytes += c.bytes; continue; }
-        }
-        m.push_back(c);
-      }
-      return m;
-    };
-    size_t ui = 0;
-    while (ui < units.size()) {
-      TcsRec R{};
-      std::vector<TcsCopy> cp;
+      m.push_back(c);
+    }
+    return m;
+  };
+  for (size_t bi = 0; bi < bins.size(); ++bi) {
+    TcsJob& J = hj[bi];
+    J.r0 = (int)hrec.size();
+    const std::vector<Unit>& units = bin_units[bi];
+    // layout of a round from its units: sub-block records, merged copies, area bytes
+    auto layout = [&](const std::vector<const Unit*>& us, TcsRec& R) {
+      uint32_t off = 0;
       int cols = 0, ktot = 0;
-      uint32_t area = 0;
-      while (ui < units.size() && R.nsub < TCS_MAXSUB) {
-        const Unit& u = units[ui];
-        if (R.nsub > 0 && (cols + 2 * u.nk16 > J.d1w || R.nt + (int)u.st.size() > TCS_REC_TERMS ||
-                           area + unit_area(u) > max_area))
-          break;
-        std::vector<TcsCopy> cp2 = cp;
-        unit_copies(u, area, cp2);
-        std::vector<TcsCopy> m = merge(cp2);
-        if (R.nsub > 0 && (int)m.size() > TCS_REC_COPIES) break;
-        PN_CHECK((int)m.size() <= TCS_REC_COPIES, PNOEOM_ERR_CUDA, "tensor-core sandwich: copies of one vector block");
-        TcsSub& U = R.subs[R.nsub];
+      R = TcsRec{};
+      R.nsub = (int)us.size();
+      for (size_t i = 0; i < us.size(); ++i) { R.subs[i].a_off = off; off += (uint32_t)J.rows16 * us[i]->nk16 * 2; }
+      for (size_t i = 0; i < us.size(); ++i) { R.subs[i].b_off = off; off += (uint32_t)J.rows16 * us[i]->nk16 * 2; }
+      for (size_t i = 0; i < us.size(); ++i) { R.subs[i].x_off = off; off += 2u * us[i]->nk16 * us[i]->nk16 * 2; }
+      std::vector<TcsCopy> cp;
+      for (size_t i = 0; i < us.size(); ++i) {
+        const Unit& u = *us[i];
+        TcsSub& U = R.subs[i];
         U.nk16 = (uint16_t)u.nk16;
         U.dc = (uint16_t)cols;
         U.tk = (uint16_t)ktot;
-        U.a_off = area;
         U.mask = 0;
         for (auto& e : u.st) {
-          R.terms[R.nt++] = {e.first | (R.nsub << 8), e.second->sN, e.second->sT};
+          const TcsSlot& S = hsl[J.s0 + e.first];
+          const uint32_t rb = (uint32_t)S.row0 * u.nk16 * 2, sz = (uint32_t)up16(S.n_out) * u.nk16 * 2;
+          cp.push_back({image(e.second->a), U.a_off + rb, sz, 0, 0});
+          cp.push_back({image(e.second->b), U.b_off + rb, sz, 0, 0});
+          if (R.nt < TCS_REC_TERMS) R.terms[R.nt] = {e.first | ((int)i << 8), e.second->sN, e.second->sT};
+          ++R.nt;
           U.mask |= 1u << e.first;
         }
-        cp.swap(cp2);
+        cp.push_back({xblk[3 * u.q + 2], U.x_off, 2u * u.nk16 * u.nk16 * 2, 1, 0});
         cols += 2 * u.nk16;
         ktot += u.nk16;
-        area += unit_area(u);
-        ++R.nsub;
-        ++ui;
       }
-      std::vector<TcsCopy> m = merge(cp);
+      const std::vector<TcsCopy> m = merge(cp);
       R.nc = (int)m.size();
       R.tx = 0;
-      for (int c = 0; c < R.nc; ++c) { R.copies[c] = m[c]; R.tx += m[c].bytes; }
-      R.bytes = area;
+      for (int c = 0; c < R.nc && c < TCS_REC_COPIES; ++c) { R.copies[c] = m[c]; R.tx += m[c].bytes; }
+      R.bytes = off;
       R.ktot = ktot;
+      return cols;
+    };
+    auto fits = [&](const TcsRec& R, int cols) {
+      return cols <= J.d1w && R.nt <= TCS_REC_TERMS && R.bytes <= (uint32_t)TCS_MAX_AREA && R.nc <= TCS_REC_COPIES;
+    };
+    size_t ui = 0;
+    while (ui < units.size()) {
+      std::vector<const Unit*> us{&units[ui]};
+      TcsRec R;
+      int cols = layout(us, R);
+      PN_CHECK(fits(R, cols), PNOEOM_ERR_CUDA, "tensor-core sandwich: a vector block does not fit a round");
+      ++ui;
+      while (ui < units.size() && (int)us.size() < TCS_MAXSUB) {
+        us.push_back(&units[ui]);
+        TcsRec R2;
+        const int cols2 = layout(us, R2);
+        if (!fits(R2, cols2)) { us.pop_back(); break; }
+        R = R2;
+        ++ui;
+      }
       hrec.push_back(R);
       double cst = 700.0;
       for (int i = 0; i < R.nsub; ++i) cst += 2.0 * 72.0 * (R.subs[i].nk16 / 16);
@@ -788,7 +805,12 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
       ncopies += R.nc;
     }
     J.r1 = (int)hrec.size();
-    if (J.r1 > J.r0) hj.push_back(J);
+  }
+  {   // drop bins without rounds
+    std::vector<TcsJob> keep;
+    for (const TcsJob& J : hj)
+      if (J.r1 > J.r0) keep.push_back(J);
+    hj.swap(keep);
   }
   // enough CTAs for the device (about four per SM with six vectors): a bin's rounds are split
   // into contiguous ranges of similar cost, each a job whose D2 is added to the output
@@ -843,9 +865,17 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
         PN_CHECK(U.nk16 >= 16 && U.nk16 <= up16(TCS_MAXN) && U.nk16 % 16 == 0 && U.a_off == area && U.dc == cols &&
                      U.tk == ktot,
                  PNOEOM_ERR_CUDA, "tensor-core sandwich: sub-block");
-        area += (uint32_t)(2 * J.rows16 + 2 * U.nk16) * U.nk16 * 2;
+        area += (uint32_t)J.rows16 * U.nk16 * 2;
         cols += 2 * U.nk16;
         ktot += U.nk16;
+      }
+      for (int i = 0; i < R.nsub; ++i) {
+        PN_CHECK(R.subs[i].b_off == area, PNOEOM_ERR_CUDA, "tensor-core sandwich: B tile");
+        area += (uint32_t)J.rows16 * R.subs[i].nk16 * 2;
+      }
+      for (int i = 0; i < R.nsub; ++i) {
+        PN_CHECK(R.subs[i].x_off == area, PNOEOM_ERR_CUDA, "tensor-core sandwich: X tile");
+        area += 2u * R.subs[i].nk16 * R.subs[i].nk16 * 2;
       }
       PN_CHECK(area == R.bytes && cols <= J.d1w && ktot == R.ktot, PNOEOM_ERR_CUDA, "tensor-core sandwich: round area");
       uint32_t seen[TCS_MAXSUB] = {0, 0, 0, 0}, tx = 0;

@@ -73,7 +73,7 @@ constexpr int TCS_NSLOT = 8;             // rounds in flight (stage barriers / h
 constexpr int TCS_HDR = 384;             // bytes of a round header
 constexpr int TCS_MAX_AREA = 80 * 1024;  // bytes of one round's tiles
 constexpr int TCS_CONV_WARPS = 8;        // warps forming T: two per TMEM lane quarter, alternate 16-column chunks
-constexpr int TCS_THREADS = 32 * (TCS_CONV_WARPS + 2);   // + one bulk-copy warp and one MMA-issue warp
+constexpr int TCS_THREADS = 32 * (TCS_CONV_WARPS + 3);   // + a bulk-copy warp and two MMA-issue warps
 
 struct TcsJob {                          // one bin (CTA x vector)
   int r0, r1;                            // round records [r0, r1) (a bin's rounds may be split over jobs)
@@ -97,7 +97,7 @@ struct TcsSub {                          // one vector block of a round
   uint16_t dc;                           // GEMM1 columns [dc, dc + 2 nk16) of the round's D1 buffer
   uint16_t tk;                           // its columns [tk, tk + nk16) of T
   uint16_t pad;
-  uint32_t a_off;                        // byte offset of its A tile in the round's area (B tile, then X tile follow)
+  uint32_t a_off, b_off, x_off;          // byte offsets of its A, B and X tiles in the round's area
   uint32_t mask;                         // slots with a term
 };
 struct TcsCopy {                         // bulk copy into the round's stage area
@@ -111,7 +111,7 @@ constexpr int TCS_REC_COPIES = 20;
 constexpr int TCS_REC_TERMS = TCS_MAXSUB * TCS_MAXSLOTS;
 // One round, fixed size (the copy warp prefetches records many rounds ahead with bulk copies).
 struct TcsRec {
-  uint32_t bytes;                        // area of the round: per sub-block A tile + B tile + X tile
+  uint32_t bytes;                        // area of the round: the A tiles, then the B tiles, then the X tiles
   uint32_t tx;                           // bytes its copies deliver (slots without a term get none)
   int nsub, nt, nc;                      // sub-blocks, terms, copies
   int ktot;                              // sum of the sub-blocks' nk16 (columns of T)
@@ -119,7 +119,7 @@ struct TcsRec {
   TcsSub subs[TCS_MAXSUB];
   TcsTerm terms[TCS_REC_TERMS];
   TcsCopy copies[TCS_REC_COPIES];
-  int pad2[16];
+  int pad2[8];
 };
 static_assert(sizeof(TcsRec) == 1024, "round record");
 
