@@ -63,3 +63,60 @@ def test_noalloc_rejects_oversized_request(built):
                                  0, None)
     assert rc == pkg.ERR_UNSUPPORTED
     assert b"scratch" in pkg.lib().pnoeom_last_error()
+
+
+def _live_bytes(pkg):
+    b = ctypes.c_longlong()
+    assert pkg.lib().pnoeom_alloc_live_bytes(ctypes.byref(b)) == pkg.OK
+    return b.value
+
+
+def test_noalloc_allocates_nothing(built):
+    """On a fresh handle whose sigma() scratch was sized for one vector, a sigma_noalloc
+    call with more vectors leaves the library's allocator untouched and matches sigma()."""
+    pkg, ctx, _ = built
+    s = make_system(4, 16, 48, 21)
+    fresh = pkg.PNO(ctx, s["eps"], s["B"], 4, opts=pkg.make_opts(t_pno=1e-6, nroots=3))
+    rng = np.random.default_rng(23)
+    one = torch.tensor(rng.standard_normal((1, fresh.length)), dtype=torch.float32, device="cuda:0")
+    fresh.sigma(one, torch.zeros_like(one), precision=pkg.FP32)   # loads the kernels; scratch for 1 vector
+    torch.cuda.synchronize()
+    r = torch.tensor(rng.standard_normal((4, fresh.length)), dtype=torch.float32, device="cuda:0")
+    out = torch.full_like(r, float("nan"))
+    before = _live_bytes(pkg)
+    assert _call_noalloc(pkg, ctx, fresh, r, out, pkg.FP32) == pkg.OK, pkg.lib().pnoeom_last_error()
+    torch.cuda.synchronize()
+    assert _live_bytes(pkg) == before
+    ref = torch.zeros_like(r)
+    fresh.sigma(r, ref, precision=pkg.FP32)     # sigma() now grows its scratch to 4 vectors
+    torch.cuda.synchronize()
+    assert _live_bytes(pkg) > before
+    a, b = ref.double().cpu().numpy(), out.double().cpu().numpy()
+    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
+
+
+def test_noalloc_under_stream_capture(built):
+    """After the first call, sigma_noalloc can be captured into a CUDA graph: the replay
+    reads the vectors present at replay time and matches sigma()."""
+    pkg, ctx, gp = built
+    rng = np.random.default_rng(29)
+    r = torch.tensor(rng.standard_normal((3, gp.length)), dtype=torch.float32, device="cuda:0")
+    out = torch.zeros_like(r)
+    assert _call_noalloc(pkg, ctx, gp, r, out, pkg.FP32) == pkg.OK     # first call before any capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+        rc = pkg.lib().sigma_noalloc(ctx.h, gp.h, 3, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                     pkg.FP32, ctypes.c_void_p(side.cuda_stream))
+    assert rc == pkg.OK, pkg.lib().pnoeom_last_error()
+    r.copy_(torch.tensor(rng.standard_normal((3, gp.length)), dtype=torch.float32))
+    out.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    ref = torch.zeros_like(r)
+    gp.sigma(r, ref, precision=pkg.FP32)
+    torch.cuda.synchronize()
+    a, b = ref.double().cpu().numpy(), out.double().cpu().numpy()
+    assert np.all(np.isfinite(b))
+    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
