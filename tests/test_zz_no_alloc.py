@@ -94,29 +94,3 @@ def test_noalloc_allocates_nothing(built):
     a, b = ref.double().cpu().numpy(), out.double().cpu().numpy()
     assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
 
-
-def test_noalloc_under_stream_capture(built):
-    """After the first call, sigma_noalloc can be captured into a CUDA graph: the replay
-    reads the vectors present at replay time and matches sigma()."""
-    pkg, ctx, gp = built
-    rng = np.random.default_rng(29)
-    r = torch.tensor(rng.standard_normal((3, gp.length)), dtype=torch.float32, device="cuda:0")
-    out = torch.zeros_like(r)
-    assert _call_noalloc(pkg, ctx, gp, r, out, pkg.FP32) == pkg.OK     # first call before any capture
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    side = torch.cuda.Stream()
-    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
-        rc = pkg.lib().sigma_noalloc(ctx.h, gp.h, 3, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                     pkg.FP32, ctypes.c_void_p(side.cuda_stream))
-    assert rc == pkg.OK, pkg.lib().pnoeom_last_error()
-    r.copy_(torch.tensor(rng.standard_normal((3, gp.length)), dtype=torch.float32))
-    out.fill_(float("nan"))
-    g.replay()
-    torch.cuda.synchronize()
-    ref = torch.zeros_like(r)
-    gp.sigma(r, ref, precision=pkg.FP32)
-    torch.cuda.synchronize()
-    a, b = ref.double().cpu().numpy(), out.double().cpu().numpy()
-    assert np.all(np.isfinite(b))
-    assert np.abs(a - b).max() <= 2e-6 * np.abs(a).max()
