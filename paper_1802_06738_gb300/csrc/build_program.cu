@@ -906,14 +906,18 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
   auto add_gemv = [&](std::vector<VProb>& L_, int64_t aoff, int M, int K, int lda, int xbuf, int64_t xoff, int xs, int xvn,
                       int cbuf, int64_t coff, int cs, int cvn, double al) {
     if (M <= 0 || K <= 0 || al == 0.0) return;
-    for (int m0 = 0; m0 < M; m0 += GEMV_ROWS)
+    // one row group per tile: a warp streams its rows once, so tiles with more groups
+    // would serialise their load latencies (measured slower at the medium workload)
+    const int groups = 1;
+    for (int m0 = 0; m0 < M; m0 += groups * GEMV_ROWS)
       for (int k0 = 0; k0 < K; k0 += GEMV_KC) {
         VProb q{};
         q.a_off = aoff; q.x_off = xoff; q.c_off = coff;
         q.x_buf = xbuf; q.c_buf = cbuf;
         q.M = M; q.K = K; q.lda = lda;
         q.x_stride = xs; q.c_stride = cs; q.xvec_n = xvn; q.cvec_n = cvn;
-        q.m0 = m0; q.k0 = k0; q.klen = std::min(GEMV_KC, K - k0); q.alpha = al;
+        q.m0 = m0; q.mlen = std::min(groups * GEMV_ROWS, M - m0);
+        q.k0 = k0; q.klen = std::min(GEMV_KC, K - k0); q.alpha = al;
         L_.push_back(q);
       }
   };
@@ -1083,7 +1087,7 @@ void build_program(pnoeom_pno* P, cudaStream_t s, const double* Fd, DV& dBoo, DV
       std::set<std::pair<int64_t, int64_t>> vec_blocks;
       double pe = 0, fl = 0;
       for (const VProb& q : Lst) {
-        const int rows = std::min(GEMV_ROWS, q.M - q.m0);
+        const int rows = q.mlen;
         pe += (double)rows * q.klen;
         fl += 2.0 * rows * q.klen;
         vec_blocks.insert({q.x_off + ((int64_t)q.x_buf << 40), (int64_t)q.K * q.x_stride});

@@ -944,9 +944,12 @@ __global__ void k_wait_selftest(long long budget, int* out) {
   }
 }
 
-// Dense block times vectors, one (GEMV_ROWS-row, K-chunk) tile of one block per CTA
+// Dense block times vectors, one (row range, K-chunk) tile of one block per CTA
 // (split-K, atomic accumulation).  The K chunk of up to R vectors is staged in shared
-// memory (zero beyond the block's K); each of the 8 warps owns GEMV_ROWS / 8 rows and its lanes read
+// memory once per tile (zero beyond the block's K; each thread issues eight loads before it
+// stores them); the tile's rows are taken in groups of GEMV_ROWS against it (the program
+// builder makes one group per tile).  In a group each of the 8 warps owns
+// GEMV_ROWS / 8 rows and its lanes read
 // 16-byte vectors of consecutive columns, two column steps per iteration (16 loads in
 // flight per lane), so each staged x vector is reused for every row of the warp; the partial sums
 // stay in registers over the whole chunk and are reduced across the warp once, by a
@@ -1003,40 +1006,45 @@ template <typename T, typename TA, int R>
 __device__ __forceinline__ void gemv_tile(const VProb& P, const SysTable& tab, T* xs) {
   constexpr int VEC = PoolVec<TA>::N;
   constexpr int NV = GEMV_WROWS * R;          // partial sums per lane
+  constexpr int SL = 8;                       // staged x loads in flight per thread
   static_assert(NV % 32 == 0 || NV == 16, "reduce-scatter of 16 or a multiple of 32 sums");
   const int nroots = tab.s[P.sys].nvec;
   const TA* A = (const TA*)(sizeof(TA) == 2 ? tab.s[P.sys].pool16 : tab.s[P.sys].pool) + P.a_off;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int kl = P.klen, klp = (kl + VEC - 1) / VEC * VEC;
   const T alpha = (T)P.alpha;
-  const TA* arow[GEMV_WROWS];
-  bool rv[GEMV_WROWS];
-#pragma unroll
-  for (int rr = 0; rr < GEMV_WROWS; ++rr) {
-    const int m = P.m0 + warp * GEMV_WROWS + rr;
-    rv[rr] = m < P.M;
-    arow[rr] = A + (int64_t)(rv[rr] ? m : P.m0) * P.lda + P.k0;
-  }
   for (int r0 = 0; r0 < nroots; r0 += R) {
     const int nr = min(R, nroots - r0);
     __syncthreads();
-    for (int q = 0; q < nr; ++q) {
-      const T* xq = cbuf<T>(tab, P.sys, P.x_buf, r0 + q) + P.x_off;
-      for (int kk = threadIdx.x; kk < klp; kk += blockDim.x) {
-        T val = T(0);
-        if (kk < kl) {
-          int xk = P.k0 + kk;
-          if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
-          val = xq[(int64_t)xk * P.x_stride];
+    // stage the K chunk of nr vectors: each thread issues SL independent loads before
+    // it stores any of them
+    const int tot = nr * klp;
+    for (int base = threadIdx.x; base < tot; base += SL * blockDim.x) {
+      T val[SL];
+#pragma unroll
+      for (int u = 0; u < SL; ++u) {
+        const int idx = base + u * blockDim.x;
+        val[u] = T(0);
+        if (idx < tot) {
+          const int q = idx / klp, kk = idx - q * klp;
+          if (kk < kl) {
+            int xk = P.k0 + kk;
+            if (P.xvec_n > 0) xk = (xk % P.xvec_n) * P.xvec_n + xk / P.xvec_n;
+            val[u] = cbuf<T>(tab, P.sys, P.x_buf, r0 + q)[P.x_off + (int64_t)xk * P.x_stride];
+          }
         }
-        xs[q * GEMV_KC + kk] = val;
+      }
+#pragma unroll
+      for (int u = 0; u < SL; ++u) {
+        const int idx = base + u * blockDim.x;
+        if (idx < tot) {
+          const int q = idx / klp;
+          xs[q * GEMV_KC + (idx - q * klp)] = val[u];
+        }
       }
     }
     __syncthreads();
-    T acc[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) acc[i] = T(0);
-    auto step = [&](int kk, const uint4 (&raw)[GEMV_WROWS]) {
+    auto step = [&](int kk, const uint4 (&raw)[GEMV_WROWS], T (&acc)[NV]) {
       T a[GEMV_WROWS][VEC];
 #pragma unroll
       for (int rr = 0; rr < GEMV_WROWS; ++rr) PoolVec<TA>::cvt(raw[rr], a[rr]);
@@ -1054,42 +1062,56 @@ __device__ __forceinline__ void gemv_tile(const VProb& P, const SysTable& tab, T
         }
       }
     };
-    int kk = lane * VEC;
-    for (; kk + 32 * VEC < klp; kk += 64 * VEC) {   // two column steps per iteration
-      uint4 ra[GEMV_WROWS], rb[GEMV_WROWS];
+    // row groups of the tile, all against the staged chunk; a warp skips a group in
+    // which it has no rows (no barrier inside this loop)
+    for (int g0 = warp * GEMV_WROWS; g0 < P.mlen; g0 += GEMV_ROWS) {
+      const TA* arow[GEMV_WROWS];
+      bool rv[GEMV_WROWS];
 #pragma unroll
       for (int rr = 0; rr < GEMV_WROWS; ++rr) {
-        ra[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk) : make_uint4(0u, 0u, 0u, 0u);
-        rb[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk + 32 * VEC) : make_uint4(0u, 0u, 0u, 0u);
+        rv[rr] = g0 + rr < P.mlen;
+        arow[rr] = A + (int64_t)(P.m0 + (rv[rr] ? g0 + rr : 0)) * P.lda + P.k0;
       }
-      step(kk, ra);
-      step(kk + 32 * VEC, rb);
-    }
-    if (kk < klp) {
-      uint4 ra[GEMV_WROWS];
+      T acc[NV];
 #pragma unroll
-      for (int rr = 0; rr < GEMV_WROWS; ++rr)
-        ra[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk) : make_uint4(0u, 0u, 0u, 0u);
-      step(kk, ra);
-    }
-    // reduce-scatter across the warp: after the exchange at bit s a lane keeps the upper
-    // half of its values when bit s of its lane index is set (16 sums: four exchanges, then
-    // lanes 2l and 2l + 1 add their single values)
-    constexpr int PER = NV >= 32 ? NV / 32 : 1;   // sums a lane ends with
-    gemv_rs_step<T, NV, NV>(acc, lane, 4);
-    gemv_rs_step<T, NV, (NV >= 2 ? NV / 2 : 1)>(acc, lane, 3);
-    gemv_rs_step<T, NV, (NV >= 4 ? NV / 4 : 1)>(acc, lane, 2);
-    gemv_rs_step<T, NV, (NV >= 8 ? NV / 8 : 1)>(acc, lane, 1);
-    gemv_rs_step<T, NV, (NV >= 16 ? NV / 16 : 1)>(acc, lane, 0);
-    const bool writer = NV >= 32 || (lane & (32 / NV - 1)) == 0;
+      for (int i = 0; i < NV; ++i) acc[i] = T(0);
+      int kk = lane * VEC;
+      for (; kk + 32 * VEC < klp; kk += 64 * VEC) {   // two column steps per iteration
+        uint4 ra[GEMV_WROWS], rb[GEMV_WROWS];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-      const int idx = NV >= 32 ? lane * PER + j : lane / (32 / NV), rr = idx / R, q = idx % R;
-      const int m = P.m0 + warp * GEMV_WROWS + rr;
-      if (writer && q < nr && m < P.M) {
-        int cm = m;
-        if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
-        atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[j]);
+        for (int rr = 0; rr < GEMV_WROWS; ++rr) {
+          ra[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk) : make_uint4(0u, 0u, 0u, 0u);
+          rb[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk + 32 * VEC) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        step(kk, ra, acc);
+        step(kk + 32 * VEC, rb, acc);
+      }
+      if (kk < klp) {
+        uint4 ra[GEMV_WROWS];
+#pragma unroll
+        for (int rr = 0; rr < GEMV_WROWS; ++rr)
+          ra[rr] = rv[rr] ? *reinterpret_cast<const uint4*>(arow[rr] + kk) : make_uint4(0u, 0u, 0u, 0u);
+        step(kk, ra, acc);
+      }
+      // reduce-scatter across the warp: after the exchange at bit s a lane keeps the upper
+      // half of its values when bit s of its lane index is set (16 sums: four exchanges, then
+      // lanes 2l and 2l + 1 add their single values)
+      constexpr int PER = NV >= 32 ? NV / 32 : 1;   // sums a lane ends with
+      gemv_rs_step<T, NV, NV>(acc, lane, 4);
+      gemv_rs_step<T, NV, (NV >= 2 ? NV / 2 : 1)>(acc, lane, 3);
+      gemv_rs_step<T, NV, (NV >= 4 ? NV / 4 : 1)>(acc, lane, 2);
+      gemv_rs_step<T, NV, (NV >= 8 ? NV / 8 : 1)>(acc, lane, 1);
+      gemv_rs_step<T, NV, (NV >= 16 ? NV / 16 : 1)>(acc, lane, 0);
+      const bool writer = NV >= 32 || (lane & (32 / NV - 1)) == 0;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int idx = NV >= 32 ? lane * PER + j : lane / (32 / NV), rr = idx / R, q = idx % R;
+        if (writer && q < nr && g0 + rr < P.mlen) {
+          const int m = P.m0 + g0 + rr;
+          int cm = m;
+          if (P.cvec_n > 0) cm = (m % P.cvec_n) * P.cvec_n + m / P.cvec_n;
+          atomicAdd(mbuf<T>(tab, P.sys, P.c_buf, r0 + q) + P.c_off + (int64_t)cm * P.c_stride, alpha * acc[j]);
+        }
       }
     }
   }

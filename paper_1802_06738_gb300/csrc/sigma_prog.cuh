@@ -47,7 +47,7 @@ struct VProb {
   int lda;
   int x_stride, c_stride;             // element strides of x and c
   int xvec_n, cvec_n;                 // > 0: vectorised n x n block read / written transposed
-  int m0;                             // row tile origin (tiles of 64 rows)
+  int m0, mlen;                       // rows m0 .. m0 + mlen - 1 of this tile (GEMV_ROWS-row groups)
   int k0, klen;                       // K chunk of this tile (split-K; klen <= GEMV_KC)
   double alpha;
 };
@@ -124,7 +124,7 @@ struct TcsRec {
 static_assert(sizeof(TcsRec) == 1024, "round record");
 
 constexpr int GEMV_KC = 2048;         // K chunk staged in shared memory per GEMV tile
-constexpr int GEMV_ROWS = 32;         // rows of a GEMV tile (4 per warp)
+constexpr int GEMV_ROWS = 32;         // rows of one GEMV row group (4 per warp)
 constexpr int POOL_ALIGN = 8;         // GEMV blocks: offsets and leading dimensions are multiples of this
 constexpr int SMALL_DIM = 64;         // sandwich problems with all dims <= this use the shared-memory kernel
 

@@ -12,8 +12,9 @@ Usage: python tests/golden/make_golden.py medium   (about two hours on 8 cores)
        python tests/golden/make_golden.py large --pno-only
            (PNO/OSV counts and CIS energies of the large workload, ~10 minutes)
        python tests/golden/make_golden.py large --sigma-samples
-           (per-pair oracle sigma of the blockwise trial vector for sampled pair blocks and
-            singles rows of the large workload, added to its fixture; ~30 minutes)
+           (per-pair oracle sigma of the blockwise trial vector: seeded entries of every
+            non-empty pair block and singles row of the large workload, added to its
+            fixture)
        python tests/golden/make_golden.py medium --sigma-only
            (recomputes only the sigma fields of an existing fixture, ~2 minutes)
 """
@@ -79,12 +80,12 @@ def trial_r2_block(v, i, j, seed=321):
     return x if i <= j else x.T
 
 
-def sigma_samples(name, npairs_sample=8):
-    """Sigma of the blockwise trial vector for a sample of pair blocks and singles, by the
-    per-pair oracle (oracle.pno_direct), in the canonical basis: SIGMA_SAMPLES seeded
-    entries of each sampled pair block and the whole sampled singles rows.  The sample
-    takes pairs of every size class (sorted by n_ij, evenly spaced) and three occupied
-    orbitals with OSVs."""
+def sigma_samples(name, npairs_whole=8, per_pair=8, per_row=16):
+    """Sigma of the blockwise trial vector by the per-pair oracle (oracle.pno_direct), in
+    the canonical basis, for every non-empty pair block and every singles row with OSVs:
+      * npairs_whole pairs of every size class (sorted by n_ij, evenly spaced) keep
+        SIGMA_SAMPLES seeded entries each, every other non-empty pair per_pair entries;
+      * three occupied orbitals keep their whole singles row, the others per_row entries."""
     from oracle.pno_direct import PNOSigmaDirect
     w = WORKLOADS[name]
     o, v = w["o"], w["v"]
@@ -106,26 +107,29 @@ def sigma_samples(name, npairs_sample=8):
         if sp.n_ij[p]:
             U = sp.U[i, j]
             vec[sp.off_ij[p]:sp.off_ij[p + 1]] = (U.T @ trial_r2_block(v, i, j) @ U).ravel()
-    nz = [p for p in np.argsort(sp.n_ij, kind="stable") if sp.n_ij[p] > 0]
-    pick = sorted({int(nz[int(round(k * (len(nz) - 1) / (npairs_sample - 1)))]) for k in range(npairs_sample)})
+    nz = [int(p) for p in np.argsort(sp.n_ij, kind="stable") if sp.n_ij[p] > 0]
+    whole = {nz[int(round(k * (len(nz) - 1) / (npairs_whole - 1)))] for k in range(npairs_whole)}
     occ = [i for i in range(o) if sp.n_i[i] > 0]
-    occ_pick = sorted({occ[0], occ[len(occ) // 2], occ[-1]})
-    sig = o2(vec, pairs=pick, singles=occ_pick)
-    print(f"sigma samples {time.time() - t0:.0f} s", flush=True)
+    occ_whole = {occ[0], occ[len(occ) // 2], occ[-1]}
+    sig = o2(vec, pairs=sorted(nz), singles=occ)
+    print(f"sigma of {len(nz)} pair blocks and {len(occ)} singles rows {time.time() - t0:.0f} s", flush=True)
     rng = np.random.default_rng(7)
     smp, s1 = {}, {}
-    for p in pick:
+    for p in sorted(nz):
         i, j = sp.pairs[p]
         U = sp.U[i, j]
         blk = U @ sig[sp.off_ij[p]:sp.off_ij[p + 1]].reshape(sp.n_ij[p], sp.n_ij[p]) @ U.T
-        pos = rng.integers(0, v, size=(SIGMA_SAMPLES, 2))
+        pos = rng.integers(0, v, size=(SIGMA_SAMPLES if p in whole else per_pair, 2))
         smp[f"{i},{j}"] = [[int(a), int(b), float(blk[a, b])] for a, b in pos]
-    for i in occ_pick:
-        s1[str(i)] = (sp.Ui[i] @ sig[sp.off_i[i]:sp.off_i[i + 1]]).tolist()
+    for i in occ:
+        row = sp.Ui[i] @ sig[sp.off_i[i]:sp.off_i[i + 1]]
+        cols = np.arange(v) if i in occ_whole else rng.integers(0, v, size=per_row)
+        s1[str(i)] = [[int(a), float(row[a])] for a in cols]
     path = os.path.join(HERE, f"oracle_{name}.json")
     out = json.load(open(path)) if os.path.exists(path) else {}
     out.update({"sigma_trial": "blockwise (make_golden.trial_r1 / trial_r2_block, seed 321)",
-                "sigma_pair_samples": smp, "sigma_singles_rows": s1, "sigma_seconds": time.time() - t0})
+                "sigma_pair_samples": smp, "sigma_singles_samples": s1, "sigma_seconds": time.time() - t0})
+    out.pop("sigma_singles_rows", None)
     json.dump(out, open(path, "w"))
     print(f"wrote sigma samples to {path}: {time.time() - t0:.0f} s", flush=True)
 
