@@ -80,14 +80,15 @@ def trial_r2_block(v, i, j, seed=321):
     return x if i <= j else x.T
 
 
-def sigma_samples(name, npairs_whole=8, per_pair=8, per_row=16):
+def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None):
     """Sigma of the blockwise trial vector by the per-pair oracle (oracle.pno_direct), in
     the canonical basis, for every non-empty pair block and every singles row with OSVs:
       * npairs_whole pairs of every size class (sorted by n_ij, evenly spaced) keep
         SIGMA_SAMPLES seeded entries each, every other non-empty pair per_pair entries;
-      * three occupied orbitals keep their whole singles row, the others per_row entries."""
+      * three occupied orbitals keep their whole singles row, the others per_row entries.
+    w: a workload dict (o, v, naux, nroots, t_pno, seed); the ground state is MP1 unless
+    t2 is given.  Returns the fixture fields."""
     from oracle.pno_direct import PNOSigmaDirect
-    w = WORKLOADS[name]
     o, v = w["o"], w["v"]
     t0 = time.time()
     s = make_system(o, v, w["naux"], w["seed"])
@@ -95,7 +96,8 @@ def sigma_samples(name, npairs_whole=8, per_pair=8, per_row=16):
     sp = pno.PNOSpace(eps, B, o, w["nroots"], w["t_pno"])
     sp.D = None                                               # densities not needed any more
     print(f"PNO spaces {time.time() - t0:.0f} s", flush=True)
-    t2 = ccsd.mp1_t2(eps, B, o)
+    if t2 is None:
+        t2 = ccsd.mp1_t2(eps, B, o)
     h = hm.hcore_from_fock(eps, B, o)
     o2 = PNOSigmaDirect(None, t2, h, B, o, sp)
     print(f"O2 setup {time.time() - t0:.0f} s", flush=True)
@@ -125,13 +127,19 @@ def sigma_samples(name, npairs_whole=8, per_pair=8, per_row=16):
         row = sp.Ui[i] @ sig[sp.off_i[i]:sp.off_i[i + 1]]
         cols = np.arange(v) if i in occ_whole else rng.integers(0, v, size=per_row)
         s1[str(i)] = [[int(a), float(row[a])] for a in cols]
+    return {"sigma_trial": "blockwise (make_golden.trial_r1 / trial_r2_block, seed 321)",
+            "sigma_pair_samples": smp, "sigma_singles_samples": s1, "sigma_seconds": time.time() - t0}
+
+
+def sigma_samples(name):
+    """Add the sigma samples of the blockwise trial vector to the workload's fixture."""
     path = os.path.join(HERE, f"oracle_{name}.json")
+    fields = sigma_sample_fields(WORKLOADS[name])
     out = json.load(open(path)) if os.path.exists(path) else {}
-    out.update({"sigma_trial": "blockwise (make_golden.trial_r1 / trial_r2_block, seed 321)",
-                "sigma_pair_samples": smp, "sigma_singles_samples": s1, "sigma_seconds": time.time() - t0})
+    out.update(fields)
     out.pop("sigma_singles_rows", None)
     json.dump(out, open(path, "w"))
-    print(f"wrote sigma samples to {path}: {time.time() - t0:.0f} s", flush=True)
+    print(f"wrote sigma samples to {path}: {fields['sigma_seconds']:.0f} s", flush=True)
 
 
 def pno_only(name):
