@@ -3,19 +3,24 @@ T_CutPNO = 1e-7, MP1 T2, seed 3; the BF16 sigma with FP64 refinement of Sec. 2's
 Davidson, the configuration the benchmark times).
 
 Oracle results come from tests/golden/oracle_large.json (written by
-tests/golden/make_golden.py large --pno-only, which calls only oracle/):
+tests/golden/make_golden.py large --pno-only and large --sigma-samples, which call
+only oracle/):
   * the PNO/OSV counts (compared exactly) and the six CIS energies;
-the oracle's sigma and Davidson energies are not available at this size, so the
-rest is checked through properties that hold at any size:
+  * sigma of the blockwise trial vector from the per-pair oracle (O2): seeded entries of
+    every non-empty pair block and every singles row, in the canonical basis;
+the oracle's Davidson energies are not available at this size, so the rest is checked
+through properties that hold at any size:
   * sigma is linear (FP64, to rounding);
   * the FP32 and BF16 sigma agree with the FP64 one within the bounds their
     number formats give;
   * the BF16 + FP64-refinement solve reaches the FP64 solve's energies (|dE| <= 1e-5 Eh,
     the pass bar of this workload) and every refined residual is below res_tol.
-The build takes a few minutes; the module builds once.
+The build takes a few minutes; the module builds once.  The file is named so that pytest
+collects it after the other GPU tests (except the allocation-free entry point's).
 """
 import json
 import os
+import sys
 
 import numpy as np
 import pytest
@@ -87,3 +92,45 @@ def test_large_bf16_refined_energies_match_fp64(large):
     # lowest excitation energies above zero and below the CIS ones plus a few eV
     assert np.all(e > 0) and np.all(np.diff(e) >= -1e-12)
     assert ctx.device_status() == 0
+
+
+# Tolerances relative to the largest sampled |sigma|.  FP64: both sides are exact up to
+# rounding for the same PNO/OSV spaces, but at this size both take the CIS roots from
+# iterative eigensolvers (the library's block Davidson stops at residual 1e-11 Eh, about
+# 5e-9 in the vectors for root gaps of 2e-3 Eh), so the spaces may differ by small
+# rotations in directions whose occupations lie near T_CutPNO; such a rotation of angle t
+# moves a sampled entry by about t times the trial vector's component in that direction.
+# 1e-5 allows t up to about 1e-4 and still fails a dropped or mis-signed term.  FP32 and
+# BF16: the bounds of the precision test above.
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-5), ("FP32", 1e-5), ("BF16", 2e-2)])
+def test_large_sigma_matches_oracle_samples(large, prec, tol):
+    pkg, _, gp, gold = large
+    if "sigma_pair_samples" not in gold:
+        pytest.skip("oracle_large.json has no sigma samples")
+    sys.path.insert(0, os.path.join(HERE, "golden"))
+    from make_golden import trial_r1, trial_r2_block
+    from tests.sigma_samples import blockwise_vector, sampled_entries
+    if "vec" not in _trial:
+        bases = {}
+
+        def basis(k):
+            if k not in bases:
+                bases[k] = gp.basis(k)[0]
+            return bases[k]
+        _trial["basis"] = basis
+        _trial["vec"] = blockwise_vector(gp, basis, trial_r1(gp.o, gp.v), trial_r2_block)
+    basis, vec = _trial["basis"], _trial["vec"]
+    dt = torch.float64 if prec == "FP64" else torch.float32   # BF16 sigma takes float vectors
+    rt = torch.tensor(vec[None, :], dtype=dt, device="cuda:0")
+    st = torch.zeros_like(rt)
+    gp.sigma(rt, st, precision=getattr(pkg, prec))
+    torch.cuda.synchronize()
+    got, ref = sampled_entries(gp, basis, st.double().cpu().numpy()[0], gold["sigma_pair_samples"],
+                               gold["sigma_singles_samples"])
+    assert len(ref) >= len(gold["sigma_pair_samples"])
+    scale = np.abs(ref).max()
+    err = np.abs(got - ref).max() / scale
+    assert err <= tol, (prec, err)
+
+
+_trial = {}
