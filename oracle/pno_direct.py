@@ -49,7 +49,7 @@ class PNOSigmaDirect:
         self.Boo = np.ascontiguousarray(Bd[:, :o, :o])
         self.Bov = np.ascontiguousarray(Bd[:, :o, o:])
         self.Bvo = np.ascontiguousarray(Bd[:, o:, :o])
-        self.Bvv = Bd[:, o:, o:]
+        self.Bvv = np.ascontiguousarray(Bd[:, o:, o:])
         nq = self.Bov.shape[0]
         self.t = t2
         self.u = np.multiply(t2, 2.0)
@@ -112,14 +112,25 @@ class PNOSigmaDirect:
             self._cache[key] = f.reshape(o * v, -1)
         return self._cache[key]
 
+    def _kiac(self, k, i):
+        """(ki|ac) = sum_Q B^Q_ki B^Q_ac (v x v), kept for the rest of the sigma call.  One
+        pass over B_vv gives it for every occupied index of the requested output blocks."""
+        key = ("kiac", k, i)
+        if key not in self._cache:
+            occ = sorted(set(self._occ) | {i})
+            blk = np.tensordot(self.Boo[:, k, occ], self.Bvv, axes=(0, 0))
+            for n_, x in enumerate(occ):
+                self._cache[("kiac", k, x)] = blk[n_]
+        return self._cache[key]
+
     def _MC(self, i, j, k):
         """U(i,j)^T Wc[k,i] U(k,j), Wc[k,i,a,c] = (ki|ac) - 1/2 sum_{l,d} t[l,i,a,d] (kd|lc)."""
-        kiac = e("Q,Qac->ac", self.Boo[:, k, i], self.Bvv)
+        kiac = self._kiac(k, i)
         return self.U(i, j).T @ kiac @ self.U(k, j) - 0.5 * self._rf("TU", i, j).T @ self._rf("GU", k, j)
 
     def _MD(self, i, j, k):
         """U(i,j)^T Wd[.,i,k,.] U(j,k), Wd[a,i,k,c] = 2 (ai|kc) - (ki|ac) + 1/2 sum u[i,l,a,d] L[l,d,k,c]."""
-        X = 2.0 * e("Qa,Qc->ac", self.Bvo[:, :, i], self.Bov[:, k, :]) - e("Q,Qac->ac", self.Boo[:, k, i], self.Bvv)
+        X = 2.0 * e("Qa,Qc->ac", self.Bvo[:, :, i], self.Bov[:, k, :]) - self._kiac(k, i)
         return self.U(i, j).T @ X @ self.U(j, k) + 0.5 * self._rf("UU", i, j).T @ self._rf("LU", k, j)
 
     def _MZ(self, k, i, j):
@@ -139,8 +150,15 @@ class PNOSigmaDirect:
         self._cache = {}
         pairs = range(len(sp.pairs)) if pairs is None else pairs
         singles = range(o) if singles is None else singles
+        self._occ = sorted({x for p in pairs if sp.n_ij[p] for x in sp.pairs[p]})
         out = np.zeros(sp.length)
         r1 = [sp.Ui[i] @ vec[sp.off_i[i]:sp.off_i[i + 1]] for i in range(o)]
+        # R1-dependent v x v global of the ordered-pair R1 terms:
+        # Lam[b,c] = sum_{m,d} (2 (bc|md) - (bd|mc)) r_m,d
+        rho = sum(e("Qd,d->Q", self.Bov[:, m, :], r1[m]) for m in range(o))
+        self._Lam = 2.0 * e("Qbc,Q->bc", self.Bvv, rho)
+        for m in range(o):
+            self._Lam -= e("Qbd,d,Qc->bc", self.Bvv, r1[m], self.Bov[:, m, :])
         # R-dependent globals: FvR = -sum_kl U ur(k,l) U^T G^{lk},  FoR[k,j] = sum_l <U^T X_k U, ur(l,j)>
         # with ur = 2 R - R^T, G^{lk}[d,c] = (ld|kc), X_k[c,d] = (kd|lc)
         FvR = np.zeros((v, v))
@@ -261,12 +279,9 @@ class PNOSigmaDirect:
         C += -0.5 * e("QcA,Qkd,d,kcB->AB", BUt, self.Bov, r1[x], ut + ty)
         # - sum U[a,A] (ac|kd) r_y,d tx[k,c,B]
         C += -e("QcA,Qkd,d,kcB->AB", BUt, self.Bov, r1[y], tx)
-        # U^T t[x,y] Lam^T U, Lam[b,c] = sum_{m,d} (2 (bc|md) - (bd|mc)) r_m,d
-        rho = sum(e("Qd,d->Q", self.Bov[:, m, :], r1[m]) for m in range(o))
-        Lam = 2.0 * e("Qbc,Q->bc", self.Bvv, rho)
-        for m in range(o):
-            Lam -= e("Qbd,d,Qc->bc", self.Bvv, r1[m], self.Bov[:, m, :])
-        C += Up.T @ t[x, y] @ Lam.T @ Up
+        # U^T t[x,y] Lam^T U, Lam[b,c] = sum_{m,d} (2 (bc|md) - (bd|mc)) r_m,d (formed once
+        # per sigma call)
+        C += Up.T @ t[x, y] @ self._Lam.T @ Up
         # - sum_k gam[k] U^T t[x,k] U, gam[k] = sum_{m,d} (2 (ky|md) - (kd|my)) r_m,d
         for k in range(o):
             gam = sum(2.0 * self.g_ooov[k, y, m] @ r1[m] - self.g_ovoo[k, :, m, y] @ r1[m] for m in range(o))

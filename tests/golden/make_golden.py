@@ -12,9 +12,11 @@ Usage: python tests/golden/make_golden.py medium   (about two hours on 8 cores)
        python tests/golden/make_golden.py large --pno-only
            (PNO/OSV counts and CIS energies of the large workload, ~10 minutes)
        python tests/golden/make_golden.py large --sigma-samples
-           (per-pair oracle sigma of the blockwise trial vector: seeded entries of every
-            non-empty pair block and singles row of the large workload, added to its
-            fixture)
+           (per-pair oracle sigma of the blockwise trial vector: seeded entries of 16 pair
+            blocks of every size class and of every singles row of the large workload,
+            added to its fixture)
+       python tests/golden/make_golden.py medium --sigma-samples --out=oracle_medium_blockwise.json
+           (the same for the medium workload, in a file of its own)
        python tests/golden/make_golden.py medium --sigma-only
            (recomputes only the sigma fields of an existing fixture, ~2 minutes)
 """
@@ -80,9 +82,10 @@ def trial_r2_block(v, i, j, seed=321):
     return x if i <= j else x.T
 
 
-def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None):
+def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None, all_pairs=True):
     """Sigma of the blockwise trial vector by the per-pair oracle (oracle.pno_direct), in
-    the canonical basis, for every non-empty pair block and every singles row with OSVs:
+    the canonical basis, for every non-empty pair block (or, with all_pairs=False, only the
+    npairs_whole pairs below) and every singles row with OSVs:
       * npairs_whole pairs of every size class (sorted by n_ij, evenly spaced) keep
         SIGMA_SAMPLES seeded entries each, every other non-empty pair per_pair entries;
       * three occupied orbitals keep their whole singles row, the others per_row entries.
@@ -113,11 +116,12 @@ def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None):
     whole = {nz[int(round(k * (len(nz) - 1) / (npairs_whole - 1)))] for k in range(npairs_whole)}
     occ = [i for i in range(o) if sp.n_i[i] > 0]
     occ_whole = {occ[0], occ[len(occ) // 2], occ[-1]}
-    sig = o2(vec, pairs=sorted(nz), singles=occ)
-    print(f"sigma of {len(nz)} pair blocks and {len(occ)} singles rows {time.time() - t0:.0f} s", flush=True)
+    out_pairs = sorted(nz) if all_pairs else sorted(whole)
+    sig = o2(vec, pairs=out_pairs, singles=occ)
+    print(f"sigma of {len(out_pairs)} pair blocks and {len(occ)} singles rows {time.time() - t0:.0f} s", flush=True)
     rng = np.random.default_rng(7)
     smp, s1 = {}, {}
-    for p in sorted(nz):
+    for p in out_pairs:
         i, j = sp.pairs[p]
         U = sp.U[i, j]
         blk = U @ sig[sp.off_ij[p]:sp.off_ij[p + 1]].reshape(sp.n_ij[p], sp.n_ij[p]) @ U.T
@@ -131,10 +135,15 @@ def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None):
             "sigma_pair_samples": smp, "sigma_singles_samples": s1, "sigma_seconds": time.time() - t0}
 
 
-def sigma_samples(name):
-    """Add the sigma samples of the blockwise trial vector to the workload's fixture."""
-    path = os.path.join(HERE, f"oracle_{name}.json")
-    fields = sigma_sample_fields(WORKLOADS[name])
+def sigma_samples(name, out=None):
+    """Add the sigma samples of the blockwise trial vector to the workload's fixture (or to
+    the fixture file `out` in this folder)."""
+    path = os.path.join(HERE, out or f"oracle_{name}.json")
+    if name == "large":   # O2 takes about a minute per pair block here: 16 blocks of every size class
+        fields = sigma_sample_fields(WORKLOADS[name], npairs_whole=16, all_pairs=False)
+    else:
+        fields = sigma_sample_fields(WORKLOADS[name])
+    fields.update({"workload": name, **{k: WORKLOADS[name][k] for k in ("o", "v", "naux", "nroots", "t_pno", "seed")}})
     out = json.load(open(path)) if os.path.exists(path) else {}
     out.update(fields)
     out.pop("sigma_singles_rows", None)
@@ -205,6 +214,7 @@ if __name__ == "__main__":
     if "--pno-only" in sys.argv:
         pno_only(args[0])
     elif "--sigma-samples" in sys.argv:
-        sigma_samples(args[0])
+        outs = [a.split("=", 1)[1] for a in sys.argv[1:] if a.startswith("--out=")]
+        sigma_samples(args[0], outs[0] if outs else None)
     else:
         main(args[0] if args else "small", sigma_only="--sigma-only" in sys.argv)
