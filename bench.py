@@ -45,7 +45,7 @@ METRIC = "PNO-EOM-CCSD \u03c3-evals/s & solve p50/p99, mixed vs FP64 GPU path, |
 ORACLE_WORKLOADS = ("small", "medium")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
@@ -64,8 +64,12 @@ def parse():
     ap.add_argument("--nsys", type=int, default=16, help="batched: number of systems (sample of the 64-system workload)")
     ap.add_argument("--omax", type=int, default=14, help="batched/serving: cap on o of the sampled systems")
     ap.add_argument("--nreq", type=int, default=40, help="serving: number of requests")
-    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
-    return ap.parse_args()
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second of the stream")
+    ap.add_argument("--arms", default="mixed", help="serving: comma-separated arms to run on the same stream, "
+                                                    "'mixed' and/or 'fp64' (the plain FP64 GPU path)")
+    ap.add_argument("--serve-mixed", default="FP32", choices=["FP32", "BF16"],
+                    help="serving: sigma precision of the mixed arm (FP64 refinement follows)")
+    return ap.parse_args(argv)
 
 
 def dist_setup():
@@ -412,63 +416,92 @@ def run_batched(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, ws, rank, local):
-    """Poisson request stream through the continuous-batching server."""
+def serving_stream(nreq, omax, rate, seed=5, n=600):
+    """The requests the serving mode submits: the first `nreq` requests with o <= omax of
+    the 600-request Poisson stream, each at its own arrival time in that stream (so with
+    omax >= 40 and nreq = 600 it is the whole stream; a filter thins it, and the offered
+    rate is what remains)."""
+    from synthetic import poisson_requests
+    return [r for r in poisson_requests(n, rate, seed) if r["o"] <= omax][:nreq]
+
+
+def serve_arm(pkg, ctx, reqs, systems, precision, refine):
+    """One pass of the request stream through a fresh server; per-request times and stats."""
     import numpy as np
+    srv = pkg.Server(ctx, hbm_budget_bytes=200 << 30, max_active=32)
+    t0 = time.perf_counter()
+    ids = []
+    for k, r in enumerate(reqs):
+        delay = r["t"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        opts = pkg.make_opts(t_pno=r["t_pno"], nroots=r["nroots"], precision=precision, refine_fp64=refine)
+        ids.append(srv.submit(systems[k]["eps"], systems[k]["B"], r["o"], opts))
+    for rid in ids:
+        srv.wait(rid, 3600.0)
+    wall = time.perf_counter() - t0
+    res = [srv.poll(rid) for rid in ids]
+    st = srv.stats()
+    srv.close()
+    tm = np.array([x["times"] for x in res])
+    pct = lambda a: {"p50_s": float(np.percentile(a, 50)), "p99_s": float(np.percentile(a, 99))}
+    sev = sum(x["sigma_evals"] for x in res)
+    return {"wall_s": wall, "sigma_evals": sev, "sigma_evals_per_s": sev / wall,
+            "latency": pct(tm[:, 3] - tm[:, 0]), "queueing": pct(tm[:, 1] - tm[:, 0]),
+            "build": pct(tm[:, 2] - tm[:, 1]), "solve": pct(tm[:, 3] - tm[:, 2]),
+            "achieved_rate_per_s": len(reqs) / wall,
+            "completed": sum(1 for x in res if x["status"] == pkg.DONE), "server": st}
+
+
+def run_serving(args, ws, rank, local):
+    """Poisson request stream through the continuous-batching server, once per arm."""
     import torch
     import paper_1802_06738_gb300 as pkg
-    from synthetic import make_system, poisson_requests
+    from synthetic import make_system
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     if rank == 0:
         pkg.build()
     barrier(ws)
-    reqs = [r for r in poisson_requests(600, args.rate, 5) if r["o"] <= args.omax][: args.nreq]
-    # rescale arrival times to keep the stream's rate after the size filter
-    gaps = np.random.default_rng(50).exponential(1.0 / args.rate, size=len(reqs))
-    arrivals = np.cumsum(gaps)
+    reqs = serving_stream(args.nreq, args.omax, args.rate)
     systems = [make_system(r["o"], r["v"], r["naux"], r["seed"] + 1000 * rank) for r in reqs]
     ctx = pkg.Context(local)
-    srv = pkg.Server(ctx, hbm_budget_bytes=200 << 30, max_active=32)
-    barrier(ws)
+    arms = [a.strip() for a in args.arms.split(",") if a.strip()]
+    mixed = getattr(pkg, args.serve_mixed)
+    out = {}
     with Clocks(local) as clk:
         clk.wait_first()
         tw0 = time.time()
-        t0 = time.perf_counter()
-        ids = []
-        for k, r in enumerate(reqs):
-            delay = arrivals[k] - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            opts = pkg.make_opts(t_pno=r["t_pno"], nroots=r["nroots"], precision=pkg.FP32, refine_fp64=1)
-            ids.append(srv.submit(systems[k]["eps"], systems[k]["B"], r["o"], opts))
-        for rid in ids:
-            srv.wait(rid, 3600.0)
-        wall = time.perf_counter() - t0
+        for arm in arms:
+            barrier(ws)
+            if arm == "mixed":
+                out[arm] = serve_arm(pkg, ctx, reqs, systems, mixed, 1)
+            elif arm == "fp64":
+                out[arm] = serve_arm(pkg, ctx, reqs, systems, pkg.FP64, 0)
+            else:
+                raise SystemExit(f"unknown serving arm {arm!r}")
+            out[arm]["wall_s"] = max_over_ranks(out[arm]["wall_s"], ws, dev)
         clk.mark(tw0, time.time())
-    res = [srv.poll(rid) for rid in ids]
-    st = srv.stats()
-    srv.close()
-    lat = np.array([x["times"][3] - x["times"][0] for x in res])
-    queue = np.array([x["times"][1] - x["times"][0] for x in res])
-    build = np.array([x["times"][2] - x["times"][1] for x in res])
-    solve = np.array([x["times"][3] - x["times"][2] for x in res])
-    done = sum(1 for x in res if x["status"] == pkg.DONE)
-    sev = sum(x["sigma_evals"] for x in res)
-    wall = max_over_ranks(wall, ws, dev)
     if rank != 0:
         return
-    pct = lambda a: {"p50_s": float(np.percentile(a, 50)), "p99_s": float(np.percentile(a, 99))}
-    line = {"metric": "served PNO-EOM-CCSD solves: latency p50/p99 and sigma-evals/s (mixed FP32 sigma + FP64 refinement)",
-            "value": ws * sev / wall, "unit": "sigma-evals/s", "n_gpus": ws, "steps": len(reqs), "warmup": 0,
-            "ms_per_step": 1e3 * wall / len(reqs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serving sample: {len(reqs)} requests of the Poisson stream (o <= {args.omax}), "
-                                   f"rate {args.rate}/s, v=10o, naux=3v, roots in {{3,6,10}}, T_PNO in {{1e-6,1e-7}}",
+    head = out[arms[0]]
+    span = reqs[-1]["t"] if reqs else 0.0
+    line = {"metric": f"served PNO-EOM-CCSD solves: latency p50/p99 and sigma-evals/s ({arms[0]} arm"
+                      + (f": {args.serve_mixed} sigma + FP64 refinement)" if arms[0] == "mixed" else ": FP64 sigma)"),
+            "value": ws * head["sigma_evals"] / head["wall_s"], "unit": "sigma-evals/s", "n_gpus": ws,
+            "steps": len(reqs), "warmup": 0, "ms_per_step": 1e3 * head["wall_s"] / max(len(reqs), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if arms[0] == "fp64" else args.serve_mixed.lower(), "data": "synthetic",
+            "config": {"workload": f"serving: {len(reqs)} requests of the 600-request Poisson stream (o <= {args.omax}) "
+                                   f"at their own arrival times, stream rate {args.rate}/s, v=10o, naux=3v, "
+                                   "roots in {3,6,10}, T_PNO in {1e-6,1e-7}",
                        "o_values": [r["o"] for r in reqs]},
-            "latency": pct(lat), "queueing": pct(queue), "build": pct(build), "solve": pct(solve),
-            "offered_rate_per_s": args.rate, "achieved_rate_per_s": len(reqs) / wall, "completed": done,
-            "server": st, "clocks": clk.summary(), "gpu_launches": None, "cpu_baseline": None}
+            "offered_rate_per_s": len(reqs) / span if span > 0 else None,
+            "arms": out, "clocks": clk.summary(), "gpu_launches": None, "cpu_baseline": None}
+    if "mixed" in out and "fp64" in out:
+        line["fp64_over_mixed"] = {"p50": out["fp64"]["latency"]["p50_s"] / out["mixed"]["latency"]["p50_s"],
+                                   "p99": out["fp64"]["latency"]["p99_s"] / out["mixed"]["latency"]["p99_s"],
+                                   "sigma_evals_per_s": out["fp64"]["sigma_evals_per_s"] / out["mixed"]["sigma_evals_per_s"]}
     print(json.dumps(line), flush=True)
 
 

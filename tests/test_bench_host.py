@@ -1,7 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the clock summary keeps only the
 nvidia-smi samples inside the timed region and reads the throttle reasons, and the DRAM
 traffic figure is reported only while the kernel source matches the hash recorded with
-the ncu capture."""
+the ncu capture; the serving stream keeps its own arrival times."""
 import hashlib
 import os
 import sys
@@ -97,3 +97,22 @@ def test_roofline_bound_per_precision():
     h = dict(dom, name="dense->sigma", flops=1e9)
     r = bench.roofline(h, 1, peaks, dev, {}, "BF16")
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+
+
+def test_serving_stream_keeps_the_streams_own_arrival_times():
+    """The serving mode submits requests of the 600-request Poisson stream at their own
+    arrival times: unfiltered it is the whole stream; a cap on o thins it without
+    re-drawing the arrivals."""
+    from synthetic import poisson_requests
+    whole = poisson_requests(600, 20.0, 5)
+    assert bench.serving_stream(600, 40, 20.0) == whole
+    thin = bench.serving_stream(40, 14, 20.0)
+    assert len(thin) == 40 and all(r["o"] <= 14 for r in thin)
+    assert all(r in whole for r in thin)
+    ts = [r["t"] for r in thin]
+    assert all(a < b for a, b in zip(ts, ts[1:]))
+
+
+def test_serving_arms_option():
+    args = bench.parse(["--mode", "serving", "--arms", "mixed,fp64", "--omax", "40", "--nreq", "600"])
+    assert args.arms.split(",") == ["mixed", "fp64"] and args.serve_mixed == "FP32"
