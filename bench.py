@@ -270,6 +270,34 @@ def roofline(dom, steps, peaks, dev_peaks, clk, mixed):
     return out
 
 
+def fp64_roofline(prof, steps, peaks, dev_peaks):
+    """Roofline entry of the dominant class of the FP64 sigma: the cuBLAS DGEMM rate
+    measured by pnoeom_measure_peaks for the library-GEMM classes, the DFMA rate it
+    measures for the other contraction classes, the HBM copy bandwidth of
+    MEASURED_PEAKS.json for streaming classes (intensity against the ridge decides)."""
+    dom = max(prof, key=lambda d: d["ms"])
+    hbm, src = (peaks.get("hbm_gbs"), "of measured (MEASURED_PEAKS.json hbm_gbs)") if peaks.get("hbm_gbs") \
+        else (6800.0, "of fallback")
+    if dom["name"].startswith("gemm") and dev_peaks.get("cublas_dgemm_tflops"):
+        alu, asrc = dev_peaks["cublas_dgemm_tflops"], "of measured: cuBLAS DGEMM by pnoeom_measure_peaks"
+    else:
+        alu, asrc = dev_peaks.get("fp64_fma_tflops") or 0.0, "of measured: FP64 FMA (SIMT) by pnoeom_measure_peaks"
+    avg_ms = dom["ms"] / steps
+    if avg_ms <= 0:
+        return {"unavailable": "no class time was recorded"}
+    intensity = dom["flops"] / max(dom["bytes"], 1.0)
+    ridge = alu * 1e12 / (hbm * 1e9) if alu else float("inf")
+    common = {"kernel": dom["name"], "algorithmic_bytes_per_call": dom["bytes"],
+              "algorithmic_flops_per_call": dom["flops"], "avg_ms_per_call": avg_ms,
+              "intensity_flop_per_byte": intensity, "ridge_flop_per_byte": ridge}
+    if intensity > ridge:
+        tf = dom["flops"] / (avg_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": tf, "peak": alu, "unit": "TFLOP/s", "frac": tf / alu,
+                "peak_source": asrc, **common}
+    ach = dom["bytes"] / (avg_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "peak_source": src, **common}
+
+
 def ncu_traffic(cls, workload, mixed):
     """DRAM bytes per sigma call of kernel class `cls` from the committed ncu summary (a
     line "traffic per call (bytes): <class> = <bytes>"), or None.  The summary records the
@@ -607,6 +635,18 @@ def main():
     ev1.record()
     torch.cuda.synchronize()
     t_fp64 = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, ws, dev)
+    # per-class times of the FP64 sigma, in a loop of their own (outside the timed region)
+    k64c = 3
+    try:
+        gp.set_timing(True)
+        for _ in range(k64c):
+            gp.sigma(R64, S64, precision=pkg.FP64, stream=stream)
+        torch.cuda.synchronize()
+        prof64, prof64_err = gp.sigma_timing(nr, pkg.FP64), None
+    except Exception as ex:    # reported in the line; the headline does not depend on it
+        prof64, prof64_err = None, str(ex)
+    finally:
+        gp.set_timing(False)
 
     # end to end through the C ABI: host vectors in pinned memory, copies inside the timed region
     Rh = R32.cpu().pin_memory()
@@ -711,7 +751,8 @@ def main():
                    "parallelism": f"replicas x{ws}", "l2": "operator pool larger than L2 (no flush)",
                    "device_footprint_bytes": int(gp.footprint)},
         "fp64_path": {"value": ws * nr * k64 / t_fp64, "unit": "sigma-evals/s", "steps": k64,
-                      "ms_per_step": 1e3 * t_fp64 / k64},
+                      "ms_per_step": 1e3 * t_fp64 / k64, "kernels": prof64,
+                      "roofline": fp64_roofline(prof64, k64c, peaks, dev_peaks) if prof64 else {"unavailable": prof64_err}},
         "sigma_max_rel_err_vs_fp64": errs,
         "solve": solve_section,
         "flop_weighted": {"gflop_per_call": gflop_call, "tflops": gflop_call / (t_mixed / args.steps) / 1e3,

@@ -136,10 +136,12 @@ int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, cons
       PN_CUDA(cudaEventElapsedTime(&x, e.second.first, e.second.second));
       t += x; ++n;   // n: sigma calls recorded
     }
-    // element sizes: vectors 8 (FP64) or 4 bytes; operator blocks likewise, except the dense
-    // GEMV blocks of the BF16 sigma (classes 1 and 3), read as 2-byte BF16
+    // element sizes: vectors 8 (FP64) or 4 bytes; operator blocks likewise, except in the
+    // BF16 sigma the dense GEMV blocks (classes 1 and 3) and the operator images of the
+    // tensor-core sandwich terms (class 2), read as 2-byte BF16 (blocks above that path's
+    // size limit read the FP32 pool instead; the benchmark workloads have none)
     const double es = precision == PNOEOM_FP64 ? 8.0 : 4.0;
-    const double ep = precision == PNOEOM_BF16 && (k == 1 || k == 3) ? 2.0 : es;
+    const double ep = precision == PNOEOM_BF16 && (k == 1 || k == 2 || k == 3) ? 2.0 : es;
     if (name) *name = names[k];
     if (launches) *launches = pno->prof_launches[k];
     if (ms) *ms = t;

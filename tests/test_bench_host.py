@@ -116,3 +116,18 @@ def test_serving_stream_keeps_the_streams_own_arrival_times():
 def test_serving_arms_option():
     args = bench.parse(["--mode", "serving", "--arms", "mixed,fp64", "--omax", "40", "--nreq", "600"])
     assert args.arms.split(",") == ["mixed", "fp64"] and args.serve_mixed == "FP32"
+
+
+def test_fp64_roofline_picks_the_unit_of_the_dominant_class():
+    peaks = {"hbm_gbs": 6784.5}
+    dev = {"fp64_fma_tflops": 1.06, "cublas_dgemm_tflops": 1.10}
+    sw = {"name": "sandwich->sigma", "launches": 3, "ms": 30.0, "bytes": 1e9, "flops": 1e11}
+    dn = {"name": "dense->sigma", "launches": 3, "ms": 3.0, "bytes": 1e9, "flops": 1e8}   # below the ridge
+    r = bench.fp64_roofline([sw, dn], 3, peaks, dev)
+    assert r["kernel"] == "sandwich->sigma" and r["bound"] == "alu" and r["peak"] == 1.06
+    assert abs(r["achieved"] - 1e11 / 10e-3 / 1e12) < 1e-12
+    r = bench.fp64_roofline([dict(sw, ms=1.0), dict(dn, ms=60.0)], 3, peaks, dev)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and abs(r["frac"] - (1e9 / 20e-3 / 1e9) / 6784.5) < 1e-12
+    g = {"name": "gemm->sigma", "launches": 3, "ms": 90.0, "bytes": 1e8, "flops": 1e12}
+    assert bench.fp64_roofline([g, sw], 3, peaks, dev)["peak"] == 1.10
+    assert "unavailable" in bench.fp64_roofline([dict(sw, ms=0.0)], 3, peaks, dev)
