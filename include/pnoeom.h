@@ -359,8 +359,9 @@ int pnoeom_small_eig(int n, const double* A, double* wr, double* wi, double* VR)
  * in ms, the algorithmic bytes one sigma call's launches of that class move
  * for nvec vectors (operator blocks
  * read once, vector blocks read and written once per vector, at the element
- * size of `precision`: 8 bytes for PNOEOM_FP64, 4 otherwise, and 2 for the dense
- * GEMV blocks of PNOEOM_BF16, classes 1 and 3) and their flops.  Any pointer may be NULL.  Blocks
+ * size of `precision`: 8 bytes for PNOEOM_FP64, 4 otherwise, and 2 in PNOEOM_BF16 for
+ * the dense GEMV blocks, classes 1 and 3, and the tensor-core operator images of class 2)
+ * and their flops.  Any pointer may be NULL.  Blocks
  * until the recorded events complete. */
 int pno_set_timing(pnoeom_pno* pno, int enable);
 int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, const char** name, int* launches,
