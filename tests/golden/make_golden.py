@@ -131,7 +131,8 @@ def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None, all_
         row = sp.Ui[i] @ sig[sp.off_i[i]:sp.off_i[i + 1]]
         cols = np.arange(v) if i in occ_whole else rng.integers(0, v, size=per_row)
         s1[str(i)] = [[int(a), float(row[a])] for a in cols]
-    return {"sigma_trial": "blockwise (make_golden.trial_r1 / trial_r2_block, seed 321)",
+    return {"n_ij": sp.n_ij.tolist(), "n_i": sp.n_i.tolist(),
+            "sigma_trial": "blockwise (make_golden.trial_r1 / trial_r2_block, seed 321)",
             "sigma_pair_samples": smp, "sigma_singles_samples": s1, "sigma_seconds": time.time() - t0}
 
 
