@@ -623,6 +623,12 @@ def main():
     torch.cuda.synchronize()
     prof = gp.sigma_timing(nr, MIX)
     gp.set_timing(False)
+    tc_exec = None     # executed MMA flops of the tensor-core sandwich kernel per call
+    if w["mixed"] == "BF16":
+        try:
+            tc_exec = gp.tc_mma_flops() * nr
+        except Exception:
+            tc_exec = None
 
     # FP64 sigma steps
     k64 = max(3, args.steps // 4)
@@ -684,6 +690,11 @@ def main():
     clocks = clk.summary()
     roof = roofline(dom, k_cls, peaks, dev_peaks, clocks, w["mixed"])
     roof["timing"] = f"class times from a separate loop of {k_cls} calls with CUDA events around each class"
+    if tc_exec and dom["name"] == "sandwich->sigma" and roof.get("avg_ms_per_call"):
+        ex_tf = tc_exec / (roof["avg_ms_per_call"] * 1e-3) / 1e12
+        roof["executed_mma"] = {"flops_per_call": tc_exec, "over_algorithmic": tc_exec / max(dom["flops"], 1.0),
+                                "tflops": ex_tf, "frac_of_peak": ex_tf / roof["peak"] if roof.get("unit") == "TFLOP/s" else None,
+                                "note": "2 M N K over every MMA the kernel issues, padding included (pno_tc_mma_flops)"}
     roof["traffic"] = ncu_traffic(dom["name"], args.workload, w["mixed"])
     if roof["traffic"] is not None:
         roof["traffic_per"] = ("call, from the committed ncu summary profiles/sigma_traffic_" + args.workload +

@@ -367,6 +367,14 @@ int pno_set_timing(pnoeom_pno* pno, int enable);
 int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, const char** name, int* launches,
                      double* ms, double* bytes, double* flops);
 
+/* Executed tensor-core work of the BF16 sigma's sandwich terms (Sec. 2 ring, Fock and
+ * occupied-ladder terms on the tcgen05 path), per vector: 2 M N K summed over every MMA
+ * the kernel issues, padding included (bins of 128 rows, K rounded up to 16, both X and
+ * X^T in the first product, the whole bin width in the second).  Set by pno_build; 0 when
+ * the system has no term on that path.  Compare with the algorithmic flops of class 2 of
+ * pno_sigma_timing.  per_vector: host double.  Errors: PNOEOM_ERR_INVALID_ARG for NULL. */
+int pno_tc_mma_flops(const pnoeom_pno* pno, double* per_vector);
+
 /* Autotuner record: pno_build times every launch of the output-grouped
  * small-block kernel (one per size bucket and phase) for every candidate
  * (group size x vectors per CTA) on nroots_sa FP32 vectors, and each launch

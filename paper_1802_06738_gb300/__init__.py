@@ -56,7 +56,7 @@ _lib = None
 EXPORTS = ["pnoeom_create", "pnoeom_destroy", "pnoeom_last_error", "pno_build", "pno_destroy",
            "pno_query", "pno_get_basis", "sigma", "davidson_solve", "pno_get_eigenvectors",
            "pno_get_cis", "pno_get_occupations", "pno_get_cis_vectors", "pnoeom_small_eig", "pno_build_seconds",
-           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info",
+           "pno_set_timing", "pno_sigma_timing", "sigma_noalloc", "pno_autotune_info", "pno_tc_mma_flops",
            "pnoeom_batch_create", "pnoeom_batch_destroy", "pnoeom_batch_sigma", "pnoeom_batch_solve",
            "pnoeom_server_create", "pnoeom_server_destroy", "pnoeom_server_submit", "pnoeom_server_poll",
            "pnoeom_server_wait", "pnoeom_server_stats", "pnoeom_gemm_tf32x3", "pnoeom_device_status",
@@ -82,6 +82,7 @@ def lib():
         L.sigma.argtypes = [vp, vp, i, vp, vp, i, vp]
         L.sigma_noalloc.argtypes = [vp, vp, i, vp, vp, i, vp]
         L.pno_autotune_info.argtypes = [vp, i, ip, ip, dp, ip]
+        L.pno_tc_mma_flops.argtypes = [vp, dp]
         L.pnoeom_batch_create.argtypes = [vp, ctypes.POINTER(vp), i, vp, ctypes.POINTER(vp)]
         L.pnoeom_batch_destroy.argtypes = [vp]; L.pnoeom_batch_destroy.restype = None
         L.pnoeom_batch_sigma.argtypes = [vp, vp, ip, ctypes.POINTER(vp), ctypes.POINTER(vp), i, vp]
@@ -306,6 +307,12 @@ class PNO:
                                           ctypes.byref(by), ctypes.byref(fl)))
             out.append(dict(name=nm.value.decode(), launches=n.value, ms=ms.value, bytes=by.value, flops=fl.value))
         return out
+
+    def tc_mma_flops(self):
+        """Executed MMA flops of the tensor-core sandwich kernel per vector (padding included)."""
+        x = ctypes.c_double()
+        _check(lib().pno_tc_mma_flops(self.h, ctypes.byref(x)))
+        return x.value
 
     def solve_stats(self):
         """dict(fp32, fp64): sigma evaluations of the last davidson_solve, by precision."""

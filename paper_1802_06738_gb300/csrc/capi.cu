@@ -150,6 +150,13 @@ int pno_sigma_timing(const pnoeom_pno* pno, int k, int nvec, int precision, cons
   });
 }
 
+int pno_tc_mma_flops(const pnoeom_pno* pno, double* per_vector) {
+  return guard([&] {
+    PN_CHECK(pno && per_vector, PNOEOM_ERR_INVALID_ARG, "NULL argument");
+    *per_vector = pno->prog.tcs_mma_flops;
+  });
+}
+
 int pno_query(const pnoeom_pno* pno, int* npairs, const int** n_ij, const int** n_i, size_t* vec_len,
               size_t* footprint_bytes) {
   return guard([&] {

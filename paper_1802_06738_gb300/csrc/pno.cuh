@@ -55,6 +55,7 @@ struct Program {
   DBuf<int64_t> tcs_xblk;
   int n_tcs_jobs = 0, n_tcs_xblk = 0;
   int64_t tcs_xstride = 0;         // elements of one vector's X images
+  double tcs_mma_flops = 0;        // flops of every MMA k_sandwich_tc issues for one vector (2 M N K)
   DBuf<SProb> gen2x;
   int n_gen2x = 0;
   std::vector<SProb> h_gen2x;

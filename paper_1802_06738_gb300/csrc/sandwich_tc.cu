@@ -724,6 +724,7 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
   // then their X tiles, so tiles of consecutive sub-blocks merge into one copy as well
   std::vector<TcsRec> hrec;
   std::vector<double> rcost;                 // per record: MMA issue estimate (for splitting and ordering)
+  double mma_flops = 0;                      // executed MMA flops of one vector
   size_t nterms = 0, ncopies = 0;
   auto merge = [](std::vector<TcsCopy> cp) {   // one copy for images adjacent in the source and the area
     std::sort(cp.begin(), cp.end(), [](const TcsCopy& a, const TcsCopy& b) { return a.dst < b.dst; });
@@ -798,6 +799,8 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
         ++ui;
       }
       hrec.push_back(R);
+      for (int i = 0; i < R.nsub; ++i)   // GEMM1: M = 128, N = 2 nk16, K = nk16; GEMM2: M = 128, N = rows16, K = nk16
+        mma_flops += 2.0 * 128.0 * R.subs[i].nk16 * (2.0 * R.subs[i].nk16 + J.rows16);
       double cst = 700.0;
       for (int i = 0; i < R.nsub; ++i) cst += 2.0 * 72.0 * (R.subs[i].nk16 / 16);
       rcost.push_back(cst);
@@ -900,8 +903,8 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
   if (std::getenv("PNOEOM_LOG_TIMING"))
     std::fprintf(stderr,
                  "[pnoeom] tensor-core sandwich: %zu bins (%zu blocks) in %zu jobs, %zu rounds, %zu terms, %zu copies, "
-                 "%.1f MB images, %zu problems on the generic kernel\n",
-                 hj.size(), hsl.size(), jobs_c.size(), hrec.size(), nterms, ncopies, ipool * 2e-6, rest.size());
+                 "%.1f MB images, %zu problems on the generic kernel, %.3g MMA flops per vector\n",
+                 hj.size(), hsl.size(), jobs_c.size(), hrec.size(), nterms, ncopies, ipool * 2e-6, rest.size(), mma_flops);
   // heaviest jobs first
   std::stable_sort(jobs_c.begin(), jobs_c.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
   std::vector<TcsJob> hjs;
@@ -910,6 +913,7 @@ void build_tcs(pnoeom_pno* P, const std::vector<SProb>& sp2,
   PR.n_tcs_jobs = (int)hjs.size();
   PR.n_tcs_xblk = (int)(xblk.size() / 3);
   PR.tcs_xstride = std::max<int64_t>(xs, 256);
+  PR.tcs_mma_flops = mma_flops;
   PR.tcs_jobs.alloc(std::max<size_t>(1, hjs.size()), fp); PR.tcs_jobs.upload(hjs.data(), hjs.size(), s);
   PR.tcs_slots.alloc(std::max<size_t>(1, hsl.size()), fp); PR.tcs_slots.upload(hsl.data(), hsl.size(), s);
   PR.tcs_recs.alloc(std::max<size_t>(1, hrec.size()), fp); PR.tcs_recs.upload(hrec.data(), hrec.size(), s);
