@@ -98,11 +98,12 @@ def test_large_bf16_refined_energies_match_fp64(large):
 # rounding for the same PNO/OSV spaces, but at this size both take the CIS roots from
 # iterative eigensolvers (the library's block Davidson stops at residual 1e-11 Eh, about
 # 5e-9 in the vectors for root gaps of 2e-3 Eh), so the spaces may differ by small
-# rotations in directions whose occupations lie near T_CutPNO; such a rotation of angle t
-# moves a sampled entry by about t times the trial vector's component in that direction.
-# 1e-5 allows t up to about 1e-4 and still fails a dropped or mis-signed term.  FP32 and
-# BF16: the bounds of the precision test above.
-@pytest.mark.parametrize("prec,tol", [("FP64", 1e-5), ("FP32", 1e-5), ("BF16", 2e-2)])
+# rotations in directions whose occupations lie near T_CutPNO.  On the medium workload a
+# random 5e-9 change of the CIS vectors moved the oracle's sampled entries by 9e-9 of the
+# largest; 1e-6 leaves two orders of magnitude for this system's closer occupations and
+# still fails a dropped or mis-signed term.  FP32 and BF16: the bounds of the precision
+# test above.
+@pytest.mark.parametrize("prec,tol", [("FP64", 1e-6), ("FP32", 1e-5), ("BF16", 2e-2)])
 def test_large_sigma_matches_oracle_samples(large, prec, tol):
     pkg, _, gp, gold = large
     if "sigma_pair_samples" not in gold:
