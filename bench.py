@@ -334,9 +334,11 @@ def workload_name(name, w):
 
 
 def oracle_unavailable(name):
-    return (f"the FP64 oracle's sigma for the {name} workload needs its canonical three- and four-virtual "
-            "intermediates (about 100 GB for the v^3 o integrals at o=60, v=600) and an 11-minute PNO "
-            "construction on 8 host cores before the first sigma, so no bounded sample of it fits this run")
+    return (f"the FP64 oracle's canonical sigma for the {name} workload needs its three- and four-virtual "
+            "intermediates (about 100 GB for the v^3 o integrals at o=60, v=600); its per-pair sigma (O2) avoids "
+            "them but needs the oracle's PNO construction (11 to 70 minutes on 8 host cores) and its setup "
+            "before the first sample, and then about two minutes per pair block, so no bounded sample of it "
+            "fits this run")
 
 
 def run_reference(args, ws, rank):
