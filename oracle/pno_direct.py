@@ -49,7 +49,6 @@ class PNOSigmaDirect:
         self.Boo = np.ascontiguousarray(Bd[:, :o, :o])
         self.Bov = np.ascontiguousarray(Bd[:, :o, o:])
         self.Bvo = np.ascontiguousarray(Bd[:, o:, :o])
-        self.Bvv = np.ascontiguousarray(Bd[:, o:, o:])
         nq = self.Bov.shape[0]
         self.t = t2
         self.u = np.multiply(t2, 2.0)
@@ -68,14 +67,25 @@ class PNOSigmaDirect:
         self.W = e("Qki,Qlj->kilj", self.Boo, self.Boo)
         for k in range(o):
             self.W[k] += e("ijcd,cld->ilj", t, g[k])                  # sum_cd t^{cd}_{ij} (kc|ld)
-        self.FvvI = self.Fvv - e("klbd,ldkc->bc", u, g)
-        self.FooI = self.Foo + e("ljcd,kdlc->kj", u, g)
-        self.Xv = self.Fvv - e("klac,kdlc->ad", u, g)
-        self.Xo = self.Foo + e("kicd,mdkc->mi", u, g)
+        # FvvI = Fvv - sum u[k,l,b,d] (ld|kc),  FooI = Foo + sum u[l,j,c,d] (kd|lc),
+        # Xv = Fvv - sum u[k,l,a,c] (kd|lc),     Xo = Foo + sum u[k,i,c,d] (md|kc):
+        # the outer occupied index summed one slice at a time (whole-array contractions
+        # would copy u and (kc|ld), 10 GB each at o = 60, v = 600)
+        self.FvvI, self.FooI = self.Fvv.copy(), self.Foo.copy()
+        self.Xv, self.Xo = self.Fvv.copy(), self.Foo.copy()
+        for k in range(o):
+            gk = np.ascontiguousarray(g[:, :, k, :])                   # (ld|kc) at [l,d,c]
+            self.FvvI -= e("lbd,ldc->bc", u[k], gk)
+            self.FooI += e("jcd,mdc->mj", u[k], gk)                    # l = k here
+            self.Xv -= e("lac,dlc->ad", u[k], g[k])
+            self.Xo += e("icd,mdc->mi", u[k], gk)
         self.g_ooov = e("Qki,Qlc->kilc", self.Boo, self.Bov)          # (ki|lc)
         self.g_ovoo = e("Qkc,Qlj->kclj", self.Bov, self.Boo)          # (kc|lj)
         self.g_oovo = e("Qki,Qbj->kibj", self.Boo, self.Bvo)          # (ki|bj)
         self.g_vooo = e("Qai,Qkj->aikj", self.Bvo, self.Boo)          # (ai|kj)
+        # B^Q_ab, stored contiguous (after the o^2 v^2 contractions above, whose temporaries
+        # are the host-memory peak of this setup)
+        self.Bvv = np.ascontiguousarray(Bd[:, o:, o:])
 
     # -- bases -----------------------------------------------------------------------
     def U(self, x, y):
@@ -175,6 +185,9 @@ class PNOSigmaDirect:
                     FoR[m, l] += np.sum((Ukl.T @ g[m, :, k, :].T @ Ukl) * ur)
         for p in pairs:
             if sp.n_ij[p]:
+                # the (ov x n) ring factors of one output block are dropped before the next
+                # (at o = 60, v = 600 those of a few blocks fill the host memory)
+                self._cache = {key: x for key, x in self._cache.items() if key[0] == "kiac"}
                 out[sp.off_ij[p]:sp.off_ij[p + 1]] = self._pair_block(vec, p, r1, FvR, FoR).ravel()
         for i in singles:
             if sp.n_i[i]:
