@@ -728,7 +728,8 @@ def main():
             golden.update({"oracle_energies": gold["energies"],
                            "abs_err_mixed_refined": [abs(a - b) for a, b in zip(e_mixed, gold["energies"])],
                            "abs_err_fp64": [abs(a - b) for a, b in zip(e_fp64, gold["energies"])]})
-    lat = lambda xs: {"p50_s": float(np.percentile(xs, 50)), "p99_s": float(np.percentile(xs, 99)), "n": len(xs)}
+    lat = lambda xs: {"p50_s": float(np.percentile(xs, 50)), "p99_s": float(np.percentile(xs, 99)), "n": len(xs),
+                      **({"note": f"percentiles of {len(xs)} solves: the p99 is their maximum"} if len(xs) < 100 else {})}
 
     def in_solve(ev, xs):   # sigma-evals of one whole solve (setup excluded) and their rate
         n = ev["fp32"] + ev["fp64"]
