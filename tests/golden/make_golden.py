@@ -103,6 +103,7 @@ def sigma_sample_fields(w, npairs_whole=8, per_pair=8, per_row=16, t2=None, all_
         t2 = ccsd.mp1_t2(eps, B, o)
     h = hm.hcore_from_fock(eps, B, o)
     o2 = PNOSigmaDirect(None, t2, h, B, o, sp)
+    del s, B                                                  # O2 keeps its own blocks of B
     print(f"O2 setup {time.time() - t0:.0f} s", flush=True)
     r1 = trial_r1(o, v)
     vec = np.zeros(sp.length)
