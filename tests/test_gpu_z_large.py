@@ -7,7 +7,8 @@ tests/golden/make_golden.py large --pno-only and large --sigma-samples, which ca
 only oracle/):
   * the PNO/OSV counts (compared exactly) and the six CIS energies;
   * sigma of the blockwise trial vector from the per-pair oracle (O2): seeded entries of
-    every non-empty pair block and every singles row, in the canonical basis;
+    16 pair blocks of every size class and of every singles row, in the canonical basis
+    (the test skips while the fixture holds none);
 the oracle's Davidson energies are not available at this size, so the rest is checked
 through properties that hold at any size:
   * sigma is linear (FP64, to rounding);
